@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark: extrapolated GBS macro-steps of 2D acoustics on one GB300.
+
+Workload (one "step" = one macro-step of the whole hot path): periodic 2048^2
+grid, 6th-order centred FD, kappa and rho = 1 + 16 seeded Gaussians, Gaussian
+pressure pulse (sigma 20 cells), GBS_{8,6} (order 8, 11 sequences, 143
+grid-point updates per point per macro-step), FP32 state with FP64 combine,
+H = 0.8 x the stability limit.  Metric: grid-point updates per second
+(Gpt-updates/s), one update = one point advanced by one FE or LF step of one
+sequence.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl gbs|reference]
+
+Under torchrun each rank advances its own independent problem (replicas: the
+single-problem path has no exchange step); value = all ranks' updates / the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on the host
+cores, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to L2 err 1e-6: fused FP32 vs plain FP64 GBS; Gpt-updates/s; % HBM peak"
+UNIT = "Gpt-updates/s"
+N_GRID = 2048
+FD_ORDER = 6
+SIGMA = 20.0
+N_GAUSS = 16
+H_FRACTION = 0.8
+
+
+def workload_desc(n=N_GRID):
+    return (f"2D acoustics {n}x{n} periodic, 6th-order FD, GBS_8,6 (11 sequences, 143 updates/pt), "
+            f"FP32 state + FP64 combine, H = {H_FRACTION} x stability limit")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_macro_step_timing(side, n_steps=1):
+    """Time the FP64 oracle for n_steps macro-steps on a side x side grid of the same recipe."""
+    from fractions import Fraction
+
+    from oracle import gbs as OG
+    from oracle import mol as OM
+    from oracle import weights as OW
+    from paper_1907_11771_gb300 import inputs
+    from paper_1907_11771_gb300 import schemes as S
+    sc = S.GBS_8_6
+    steps, c = OW.scheme_weights(sc.order, list(sc.steps_dep), list(sc.steps_free),
+                                 [Fraction(t) for t in sc.c_free_text])
+    c = OW.to_fp64(c)
+    y0, kappa, rho = inputs.acoustic_problem((side, side), 0, N_GAUSS, SIGMA * side / N_GRID)
+    b = 1.0 / rho
+    f = lambda v: OM.rhs_acoustic(v, kappa, b, [1.0, 1.0], FD_ORDER)
+    H = 0.5  # any stable step: the cost does not depend on H
+    t0 = time.perf_counter()
+    y = y0
+    for _ in range(n_steps):
+        y = OG.gbs_macro_step(f, y, H, steps, c)
+    dt = time.perf_counter() - t0
+    return dt, sc.updates_per_point * side * side * n_steps
+
+
+def pick_oracle_side(budget_s):
+    """Largest side (multiple of 64, 128..2048) whose one oracle macro-step fits budget_s.
+
+    Calibrated on one right-hand side of a 512^2 grid; larger grids fall out of
+    cache and run slower per point, hence the safety factor."""
+    from oracle import mol as OM
+    import numpy as np
+    side = 512
+    y = np.random.default_rng(0).standard_normal((3, side, side))
+    k = np.ones((side, side))
+    OM.rhs_acoustic(y, k, k, [1.0, 1.0], FD_ORDER)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        OM.rhs_acoustic(y, k, k, [1.0, 1.0], FD_ORDER)
+    t_rhs = (time.perf_counter() - t0) / 2
+    per_pt = t_rhs / (side * side) * 1.15 * 1.8     # GBS updates on top; out-of-cache slowdown
+    pts = budget_s / (143 * per_pt)
+    s = int((pts ** 0.5) // 64 * 64)
+    return max(128, min(N_GRID, s))
+
+
+def cpu_baseline(budget_s=20.0):
+    side = pick_oracle_side(budget_s)
+    dt, upd = oracle_macro_step_timing(side)
+    return {"value": upd / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 macro-step of GBS_8,6 on a {side}x{side} grid of the same recipe "
+                      f"({upd} updates, {dt:.1f} s, numpy FP64, single-threaded)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    budget = 100.0 / max(1, args.steps + args.warmup)
+    side = pick_oracle_side(budget)
+    for _ in range(args.warmup):
+        oracle_macro_step_timing(side)
+    total_t, total_u, per = 0.0, 0, []
+    for _ in range(args.steps):
+        dt, upd = oracle_macro_step_timing(side)
+        total_t += dt
+        total_u += upd
+        per.append(dt)
+    v = total_u / total_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(side).replace("FP32 state + FP64 combine", "FP64 CPU oracle"),
+                       "grid": [side, side]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 1 macro-step of GBS_8,6 on a {side}x{side} grid of the "
+                                       f"same recipe (the full {N_GRID}^2 grid does not fit the time budget)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1907_11771_gb300 import binding as B
+    from paper_1907_11771_gb300 import build as Bld
+    from paper_1907_11771_gb300 import inputs
+    from paper_1907_11771_gb300 import schemes as S
+    from paper_1907_11771_gb300.solver import GBSSolver
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    Bld.build()
+
+    n = args.grid
+    y0, kappa, rho = inputs.acoustic_problem((n, n), rank, N_GAUSS, SIGMA * n / N_GRID)
+    tk = torch.tensor(kappa.astype(np.float32).ravel(), device="cuda")
+    tr = torch.tensor(rho.astype(np.float32).ravel(), device="cuda")
+    sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=FD_ORDER,
+                    precision=B.GBS_F32_STATE_F64_COMBINE, kappa=tk, rho=tr)
+    sol.set_scheme(S.GBS_8_6)
+    kernel = {"auto": B.GBS_KERNEL_AUTO, "plain": B.GBS_KERNEL_PLAIN, "fused": B.GBS_KERNEL_FUSED}[args.kernel]
+    sol.set_option("kernel", kernel)
+    H = H_FRACTION * sol.stability_limit()[0]
+    y = torch.tensor(y0.astype(np.float32).ravel(), device="cuda")
+    upd_per_step = S.GBS_8_6.updates_per_point * n * n
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sol.step(y, y, H, 1)
+    torch.cuda.synchronize()
+    barrier()
+    l0 = sol.kernel_launches
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            sol.step(y, y, H, 1)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = sol.kernel_launches - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * upd_per_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # dominant-kernel roofline: CUDA events recorded by the library around each launch
+    sol.set_option("time_kernels", 1)
+    sol.kernel_time()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        sol.step(y, y, H, 1)
+    nl, kms, kbytes = sol.kernel_time()
+    sol.set_option("time_kernels", 0)
+    peak, peak_kind = peaks()
+    achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "leap-frog step (k_lf)",
+            "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
+            "avg_launch_ms": kms / nl if nl else None}
+
+    # end to end through the C ABI with host buffers: H2D + macro-step + D2H per step
+    hbuf = torch.empty(y.numel(), dtype=torch.float32, pin_memory=True)
+    hbuf.copy_(y.cpu())
+    hout = torch.empty_like(hbuf)
+    sol.step_host(hbuf, hout, H, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.step_host(hbuf, hout, H, 1)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": ws * upd_per_step * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": y.numel() * 4}
+
+    sol.sync()
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_desc(n), "grid": [n, n], "scheme": "GBS_8,6",
+                           "updates_per_step_per_gpu": upd_per_step, "combine_dtype": "f64",
+                           "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{ws}"},
+                "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    sol.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def sol_kernel_is_fused(sol, B):
+    try:
+        return sol.uses_fused()
+    except Exception:
+        return False
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
+    ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gbs":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

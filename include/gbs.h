@@ -1,0 +1,216 @@
+/*
+ * gbs.h -- C ABI of the GB300 (sm_103a) extrapolated-GBS time stepper.
+ *
+ * Method: Ellison & Fornberg, "A parallel-in-time approach for wave-type PDEs"
+ * (arXiv 1907.11771).  An ODE y' = f(y) from a method-of-lines wave system is
+ * advanced over sections of length H.  Each section is one extrapolated GBS
+ * macro-step (Sec. 2.1 eq. "GBS", Sec. 3.2, Sec. 3.5):
+ *
+ *   for every sequence k with even step count N_k and h_k = H / N_k
+ *     y_1 = y_0 + h_k f(y_0)                                  Forward Euler
+ *     y_(n+1) = y_(n-1) + 2 h_k f(y_n),  n = 1..N_k            leap-frog
+ *     y*_k = (y_(N_k-1) + 2 y_(N_k) + y_(N_k+1)) / 4          averaging
+ *   y(t + H) = sum_k c_k y*_k                                 extrapolation
+ *
+ * f(y_0) is evaluated once and shared by all sequences (Sec. 3.5).  The
+ * weights c satisfy the order constraints sum_k c_k h_k^(2j) = [j == 0],
+ * j < p/2 (Sec. 3.2 eq. "vander"); with more sequences than constraints the
+ * free weights are given and the dependent ones follow from
+ * c_dep = V_dep^-1 (b - V_free c_free) (Sec. 3.6 eq. "cdep_computation").
+ *
+ * Conventions for every entry point
+ *  - All functions return a gbs_status; none aborts, throws or prints.  The
+ *    text of the last failure of a handle is returned by gbs_last_error().
+ *  - Device pointers are CUDA device (or managed) addresses on the current
+ *    device; the caller owns them and keeps them alive while work that uses
+ *    them is in flight.  The library owns only its workspace.
+ *  - State layout ("SoA"): for each problem of the batch, in batch order,
+ *    fields [F][nz][ny][nx] contiguous with x fastest; the batch is the
+ *    concatenation of the problems.  F = 2 (u, v) for the 1D wave system and
+ *    F = 1 + ndim (p, u_x, u_y[, u_z]) for acoustics.  Media arrays (kappa,
+ *    rho) and gradients use [nz][ny][nx] per problem, concatenated likewise.
+ *  - Element type of states and media: float for GBS_F32_STATE_F64_COMBINE,
+ *    double for GBS_F64.  Gradients are always double.
+ *  - Work is enqueued asynchronously on the stream given to gbs_create.
+ *    Device-side failures are latched and reported by gbs_sync().
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBS_ABI_VERSION 1
+#define GBS_MAX_SLOTS 8    /* weight slots per handle                       */
+#define GBS_MAX_SEQ 16     /* sequences per scheme (m)                       */
+#define GBS_MAX_STEPS 64   /* largest step count N_k                         */
+
+typedef struct gbs_ctx* gbs_handle; /* opaque; created by gbs_create, freed by gbs_destroy */
+
+typedef enum {
+  GBS_OK = 0,
+  GBS_ERR_INVALID = 1,   /* bad argument: null pointer, size, enum, step counts */
+  GBS_ERR_ORDER = 2,     /* weights violate the order constraints               */
+  GBS_ERR_UNSTABLE = 3,  /* H beyond the scheme's stability limit (checked only
+                            when requested)                                     */
+  GBS_ERR_CUDA = 4,      /* a CUDA runtime call failed                          */
+  GBS_ERR_NOMEM = 5,     /* workspace allocation failed                         */
+  GBS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up                  */
+  GBS_ERR_NONFINITE = 7, /* a NaN/Inf was found where finite values are needed  */
+  GBS_ERR_STATE = 8      /* call out of order (e.g. stepping before weights set) */
+} gbs_status;
+
+enum { GBS_WAVE1D = 1, GBS_ACOUSTIC = 2 };                /* gbs_problem.system    */
+enum { GBS_F32_STATE_F64_COMBINE = 0, GBS_F64 = 1 };       /* gbs_problem.precision */
+enum { GBS_KERNEL_AUTO = 0, GBS_KERNEL_PLAIN = 1, GBS_KERNEL_FUSED = 2 }; /* gbs_set_option */
+
+/* Problem description.  All problems of a batch share system, ndim, fd_order
+ * and precision; each has its own grid and spacing. */
+typedef struct {
+  int system;             /* GBS_WAVE1D (u_t = v_x, v_t = u_x) or GBS_ACOUSTIC
+                             (p_t = -kappa div u, u_t = -grad p / rho)          */
+  int ndim;               /* 1 for GBS_WAVE1D; 1, 2 or 3 for GBS_ACOUSTIC        */
+  int fd_order;           /* 4 or 6: periodic centred finite differences         */
+  int precision;          /* GBS_F32_STATE_F64_COMBINE or GBS_F64                */
+  int batch;              /* number of independent problems, >= 1               */
+  int enable_adjoint;     /* nonzero: reserve workspace for gbs_adjoint_step     */
+  const int64_t* shape;   /* host, batch x 3: (nx, ny, nz), unused dims = 1      */
+  const double* dx;       /* host, batch x 3 grid spacings (unused dims ignored) */
+} gbs_problem;
+
+/* Bytes of device workspace gbs_create would allocate for `pb` when schemes
+ * with up to `max_steps` steps per sequence are used (0 on invalid input). */
+size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps);
+
+/* Number of scalars in one state buffer of `pb` (sum over problems of F * points). */
+size_t gbs_state_elems(const gbs_problem* pb);
+
+/* Create a handle.  kappa and rho are device arrays (media layout, state
+ * element type) for GBS_ACOUSTIC and must be NULL for GBS_WAVE1D.  The library
+ * keeps the kappa pointer (it is read by every step) and precomputes
+ * b = 1/rho into its workspace.  `cuda_stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  All workspace is allocated here, none later, except
+ * the adjoint level store sized in gbs_set_weights.
+ * Errors: GBS_ERR_INVALID (bad description or pointers), GBS_ERR_NOMEM,
+ * GBS_ERR_CUDA; *out is NULL on error. */
+gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
+                      void* cuda_stream, gbs_handle* out);
+
+/* Replace the media (same layout rules as gbs_create); recomputes b = 1/rho. */
+gbs_status gbs_set_media(gbs_handle h, const void* kappa, const void* rho);
+
+/* Define the scheme of weight slot `slot` (0 <= slot < GBS_MAX_SLOTS).
+ * order_p: even order of accuracy p; n_dep must equal p/2.  steps_dep /
+ * steps_free: host arrays of distinct even step counts in [2, GBS_MAX_STEPS],
+ * n_dep + n_free <= GBS_MAX_SEQ.  c_free: host array of the n_free free
+ * weights (taken as exact binary values); may be NULL when n_free == 0.
+ * c_full: optional host array of all n_dep + n_free weights (dependent
+ * first); when given it is validated and used as is, otherwise the dependent
+ * weights are solved from Sec. 3.6 eq. "cdep_computation" in double-double
+ * arithmetic (Bjorck-Pereyra for the dual Vandermonde system) and rounded to
+ * FP64.  Either way the rounded weights must satisfy every order constraint
+ * to within 64 ulp of sum_k |c_k| h_k^(2j), else GBS_ERR_ORDER.  The order
+ * of summation in the combine is dependent weights first, then free ones.
+ * Also computes the scheme's imaginary stability boundary (Sec. 2.2). */
+gbs_status gbs_set_weights(gbs_handle h, int slot, int order_p, int n_dep, const int* steps_dep,
+                           int n_free, const int* steps_free, const double* c_free,
+                           const double* c_full);
+
+/* Read back a slot: *m sequences, steps[m] and FP64 weights c[m] (host arrays
+ * of at least GBS_MAX_SEQ entries, each may be NULL), and *isb = the
+ * imaginary stability boundary of R(xi) = sum_k c_k P_k(xi), found by a dense
+ * scan of |R(iy)| - 1 > 1e-12 refined by bisection (may be NULL). */
+gbs_status gbs_get_weights(gbs_handle h, int slot, int* m, int* steps, double* c, double* isb);
+
+/* Batched problems: host array slot_per_problem[batch] selects each
+ * problem's weight slot (default: all use slot 0). */
+gbs_status gbs_assign_slots(gbs_handle h, const int* slot_per_problem);
+
+/* Largest stable H per problem as ISB(slot) / rho_hat, where rho_hat =
+ * max(sqrt(kappa b)) * sqrt(sum_d (s_max / dx_d)^2) bounds the spectral
+ * radius of the acoustic operator (s_max = max |stencil symbol|; for the 1D
+ * wave system kappa b = 1).  H_max: host array of `batch` doubles. */
+gbs_status gbs_stability_limit(gbs_handle h, double* H_max);
+
+/* Advance every problem by n_macro macro-steps of size H (Sec. 2.1 / 3.2):
+ * y_out = (macro-step)^n_macro (y_in).  y_in, y_out: device state buffers;
+ * y_in == y_out is allowed, other overlap is not.  n_macro == 0 copies.
+ * Asynchronous; allocates nothing.  Errors: GBS_ERR_INVALID, GBS_ERR_STATE
+ * (a used slot has no weights), GBS_ERR_CUDA (launch failure). */
+gbs_status gbs_step(gbs_handle h, const void* y_in, void* y_out, double H, int n_macro);
+
+/* As gbs_step with one H per problem (host array of `batch` doubles). */
+gbs_status gbs_step_batch(gbs_handle h, const void* y_in, void* y_out, const double* H,
+                          int n_macro);
+
+/* End-to-end variant: y_in and y_out are HOST buffers (pinned or pageable).
+ * Copies in, steps on the device, copies out and waits for completion. */
+gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, double H,
+                         int n_macro);
+
+/* Discrete adjoint of ONE macro-step (the exact transpose of the forward
+ * steps above; not in the paper).  With y_out = M(kappa) y_in:
+ *   lam_in = M^T lam_out + S^T r
+ *   grad_kappa += d< lam_out, M(kappa) y_in > / d kappa     (pointwise)
+ * y_in: device state at the START of the macro-step.  lam_out: device
+ * adjoint state at its end.  lam_in: device output (may equal lam_out).
+ * grad_kappa: device double array (media layout), accumulated.  S^T r adds
+ * rcv_resid[i] to field 0 at flat point index rcv_idx[i] (device arrays;
+ * indices per problem 0, i.e. batch must be 1 when n_rcv > 0); n_rcv may be 0.
+ * Requires enable_adjoint and GBS_ACOUSTIC. */
+gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out, void* lam_in,
+                            double* grad_kappa, double H, const int64_t* rcv_idx, int n_rcv,
+                            const void* rcv_resid);
+
+/* Receiver misfit helper: resid[i] = y_field0[rcv_idx[i]] - data[i] (device
+ * arrays, state element type) and, if J is non-NULL (device double), adds
+ * 0.5 * sum_i resid[i]^2 to *J with a warp-shuffle reduction. */
+gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n_rcv,
+                      const void* data, void* resid, double* J);
+
+/* Norms over a whole state buffer, accumulated in FP64 with warp-shuffle and
+ * block reductions in a fixed order: out[0] = sum (a - b)^2,
+ * out[1] = sum b^2, out[2] = max |a - b|, out[3] = number of non-finite
+ * entries of a.  `b` may be NULL (treated as zero).  out: host array of 4
+ * doubles; the call waits for the result. */
+gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
+
+/* Tuning options: "kernel" = GBS_KERNEL_*, "graph" = 0/1 (CUDA-graph replay
+ * of a macro-step), "check_stability" = 0/1 (gbs_step returns
+ * GBS_ERR_UNSTABLE when H exceeds gbs_stability_limit), "time_kernels" = 0/1
+ * (record CUDA events around every launch of the dominant kernel -- the
+ * leap-frog step kernel, or the time-blocked pass kernel -- on the handle's
+ * stream; graph replay is bypassed while it is on).  gbs_get_option also
+ * answers "kernel_in_use" (the GBS_KERNEL_* value gbs_step would run now).
+ * Unknown names: GBS_ERR_INVALID. */
+gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value);
+gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value);
+
+/* Launch count and summed device time (ms, CUDA events) of the dominant
+ * kernel since the previous call, recorded while "time_kernels" is on; also
+ * reports the algorithmic bytes those launches move (*bytes, may be NULL), the
+ * per-launch figure being the unit cost of the kernel times the grid-point
+ * updates it performs.  Waits for the stream; resets the counters. */
+gbs_status gbs_kernel_time(gbs_handle h, int64_t* launches, double* total_ms, double* bytes);
+
+/* Wait for the handle's stream and report a latched device-side error. */
+gbs_status gbs_sync(gbs_handle h);
+
+/* Free the workspace and the handle (NULL is accepted). */
+gbs_status gbs_destroy(gbs_handle h);
+
+/* Last error message of `h` ("" if none); for h == NULL, the last error of a
+ * failed gbs_create on this thread.  Valid until the next call on h. */
+const char* gbs_last_error(gbs_handle h);
+
+/* Number of GPU kernels this handle has launched (for launch accounting). */
+int64_t gbs_kernel_launches(gbs_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBS_H */

@@ -1,0 +1,862 @@
+// C ABI of the GBS library: handle life cycle, validation, scheme set-up
+// (weights, order constraints, stability boundary), workspace, and the
+// dispatch of macro-steps (with CUDA-graph replay) and adjoint steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbs_dd.h"
+#include "gbs_internal.h"
+
+namespace gbs {
+int fused_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err_flag,
+                     void* scratch, int64_t scratch_bytes);
+bool fused_supported(const StepPlan& p);
+int64_t fused_scratch_bytes(const StepPlan& p);
+}  // namespace gbs
+
+using namespace gbs;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Slot {
+  bool set = false;
+  int order = 0;
+  int m = 0;
+  int steps[GBS_MAX_SEQ] = {0};
+  double c[GBS_MAX_SEQ] = {0};
+  double isb = 0;
+};
+
+struct GraphEntry {
+  const void* yi = nullptr;
+  void* yo = nullptr;
+  int kernel = 0;
+  uint64_t version = 0;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+}  // namespace
+
+struct gbs_ctx {
+  // problem
+  int system = 0, ndim = 0, order = 0, R = 0, f64 = 0, batch = 0, F = 0, adjoint = 0;
+  size_t esz = 4;                         // state element size
+  std::vector<ProbDev> probs;
+  int64_t state_elems = 0, media_elems = 0, total_blocks = 0;
+  std::vector<double> cmax;               // per problem max sqrt(kappa b)
+  // media
+  const void* kappa = nullptr;
+  void* b = nullptr;
+  // slots
+  Slot slots[GBS_MAX_SLOTS];
+  std::vector<int> slot_of;
+  // device tables
+  ProbDev* d_probs = nullptr;
+  SlotDev* d_slots = nullptr;
+  double* d_H = nullptr;
+  std::vector<double> cur_H;
+  int* d_err = nullptr;
+  double* d_red = nullptr;                // norm partials (4 * kNormBlocks) + 4 results
+  double* d_cmax = nullptr;
+  // workspace
+  void* f0 = nullptr;
+  void* L0 = nullptr;
+  void* L1 = nullptr;
+  double* acc = nullptr;
+  void* stage = nullptr;
+  void* levels = nullptr;
+  int levels_steps = 0;
+  void* mu0 = nullptr;
+  void* mu1 = nullptr;
+  void* mu_shared = nullptr;
+  void* fused_scratch = nullptr;
+  int64_t fused_scratch_bytes = 0;
+  // execution
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  int opt_kernel = GBS_KERNEL_AUTO;
+  int opt_graph = 1;
+  int opt_check_stability = 0;
+  int opt_time_kernels = 0;
+  std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
+  std::vector<double> tev_bytes;
+  int tev_used = 0;
+  std::vector<int64_t> active_pts;        // points updated by plain step (k, n)
+  uint64_t sched_version = 1;
+  std::vector<GraphEntry> graphs;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+gbs_status fail(gbs_ctx* h, gbs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return st;
+}
+
+#define CK(h, call)                                                                                 \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail((h), GBS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int fields_of(int system, int ndim) { return system == GBS_WAVE1D ? 2 : 1 + ndim; }
+
+double symbol_max(int R) {
+  // max over theta of |sum_j a_j 2 sin(j theta)| -- sampled densely, then refined
+  auto s = [R](double t) {
+    return R == 2 ? (2.0 * (2.0 / 3.0) * std::sin(t) - 2.0 * (1.0 / 12.0) * std::sin(2 * t))
+                  : (2.0 * 0.75 * std::sin(t) - 2.0 * 0.15 * std::sin(2 * t) + 2.0 * (1.0 / 60.0) * std::sin(3 * t));
+  };
+  double best = 0, bt = 0;
+  const int n = 20000;
+  for (int i = 0; i <= n; ++i) {
+    const double t = M_PI * i / n;
+    if (std::fabs(s(t)) > best) best = std::fabs(s(t)), bt = t;
+  }
+  double lo = std::max(0.0, bt - M_PI / n), hi = std::min(M_PI, bt + M_PI / n);
+  for (int it = 0; it < 200; ++it) {
+    const double m1 = lo + (hi - lo) / 3, m2 = hi - (hi - lo) / 3;
+    if (std::fabs(s(m1)) < std::fabs(s(m2))) lo = m1;
+    else hi = m2;
+  }
+  return std::fabs(s(0.5 * (lo + hi)));
+}
+
+gbs_status validate_problem(const gbs_problem* pb, gbs_ctx* h) {
+  if (!pb) return fail(h, GBS_ERR_INVALID, "problem description is NULL");
+  if (pb->system != GBS_WAVE1D && pb->system != GBS_ACOUSTIC)
+    return fail(h, GBS_ERR_INVALID, "system must be GBS_WAVE1D or GBS_ACOUSTIC");
+  if (pb->system == GBS_WAVE1D && pb->ndim != 1) return fail(h, GBS_ERR_INVALID, "GBS_WAVE1D needs ndim == 1");
+  if (pb->ndim < 1 || pb->ndim > 3) return fail(h, GBS_ERR_INVALID, "ndim must be 1, 2 or 3");
+  if (pb->fd_order != 4 && pb->fd_order != 6) return fail(h, GBS_ERR_INVALID, "fd_order must be 4 or 6");
+  if (pb->precision != GBS_F32_STATE_F64_COMBINE && pb->precision != GBS_F64)
+    return fail(h, GBS_ERR_INVALID, "unknown precision");
+  if (pb->batch < 1) return fail(h, GBS_ERR_INVALID, "batch must be >= 1");
+  if (!pb->shape || !pb->dx) return fail(h, GBS_ERR_INVALID, "shape and dx arrays are required");
+  if (pb->enable_adjoint && pb->system != GBS_ACOUSTIC)
+    return fail(h, GBS_ERR_INVALID, "the adjoint is provided for GBS_ACOUSTIC only");
+  const int R = pb->fd_order / 2;
+  for (int p = 0; p < pb->batch; ++p) {
+    for (int d = 0; d < 3; ++d) {
+      const int64_t n = pb->shape[3 * p + d];
+      if (d < pb->ndim) {
+        if (n < R || n > (int64_t(1) << 30))
+          return fail(h, GBS_ERR_INVALID, "problem %d: size %lld along dim %d outside [%d, 2^30]", p, (long long)n, d, R);
+        const double dx = pb->dx[3 * p + d];
+        if (!(dx > 0) || !std::isfinite(dx)) return fail(h, GBS_ERR_INVALID, "problem %d: dx[%d] must be > 0", p, d);
+      } else if (n != 1) {
+        return fail(h, GBS_ERR_INVALID, "problem %d: unused dim %d must have size 1", p, d);
+      }
+    }
+  }
+  return GBS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+gbs_status dalloc(gbs_ctx* h, T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return GBS_OK;
+  if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, GBS_ERR_NOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  return GBS_OK;
+}
+
+void free_graphs(gbs_ctx* h) {
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+void free_all(gbs_ctx* h) {
+  free_graphs(h);
+  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
+                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->fused_scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+  h->tev.clear();
+}
+
+struct Sizes {
+  int64_t state_elems = 0, media_elems = 0;
+};
+
+Sizes sizes_of(const gbs_problem* pb) {
+  Sizes s;
+  const int F = fields_of(pb->system, pb->ndim);
+  for (int p = 0; p < pb->batch; ++p) {
+    const int64_t pts = pb->shape[3 * p] * pb->shape[3 * p + 1] * pb->shape[3 * p + 2];
+    s.state_elems += F * pts;
+    s.media_elems += pts;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Scheme set-up
+// ---------------------------------------------------------------------------
+
+// Dual Vandermonde system sum_i z_i x_i^j = r_j (j = 0..n) by Bjorck-Pereyra, in dd.
+void bjorck_pereyra_dual(const std::vector<dd>& x, std::vector<dd>& b) {
+  const int n = (int)x.size() - 1;
+  for (int k = 0; k < n; ++k)
+    for (int i = n; i > k; --i) b[i] = b[i] - x[k] * b[i - 1];
+  for (int k = n - 1; k >= 0; --k) {
+    for (int i = k + 1; i <= n; ++i) b[i] = b[i] / (x[i] - x[i - k - 1]);
+    for (int i = k; i < n; ++i) b[i] = b[i] - b[i + 1];
+  }
+}
+
+dd inv_sq(int n) { return dd_from(1.0) / dd_from(double(n) * double(n)); }
+
+// |R(iy)|^2 - 1 for the scheme; R = sum_k c_k P_k(iy), P_k from the GBS recurrence on y' = lambda y.
+double abs2_minus_one(const Slot& s, double y) {
+  std::complex<double> R = 0;
+  for (int k = 0; k < s.m; ++k) {
+    const int N = s.steps[k];
+    const std::complex<double> z(0.0, y / N);
+    std::complex<double> y_prev = 1.0, y_cur = 1.0 + z;  // y_0, y_1 (Forward Euler)
+    std::complex<double> y_before = y_prev;
+    for (int j = 1; j <= N; ++j) {                        // leap-frog
+      const std::complex<double> y_next = y_prev + 2.0 * z * y_cur;
+      y_before = y_prev;
+      y_prev = y_cur;
+      y_cur = y_next;
+    }
+    // y_before = y_(N-1), y_prev = y_N, y_cur = y_(N+1)
+    R += s.c[k] * (y_before + 2.0 * y_prev + y_cur) * 0.25;
+  }
+  return std::norm(R) - 1.0;
+}
+
+double scan_isb(const Slot& s) {
+  int nmax = 0;
+  for (int k = 0; k < s.m; ++k) nmax = std::max(nmax, s.steps[k]);
+  const double ymax = 1.5 * (nmax + 1);  // ISB_n <= 1 for explicit methods
+  const double dy = 1e-3;
+  const double tol = 1e-12;
+  double prev = 0.0;
+  for (double y = dy; y <= ymax; y += dy) {
+    if (abs2_minus_one(s, y) > tol) {
+      double lo = prev, hi = y;
+      for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (abs2_minus_one(s, mid) > tol) hi = mid;
+        else lo = mid;
+      }
+      return lo;
+    }
+    prev = y;
+  }
+  return ymax;
+}
+
+gbs_status upload_slots(gbs_ctx* h) {
+  SlotDev sd[GBS_MAX_SLOTS];
+  std::memset(sd, 0, sizeof sd);
+  for (int i = 0; i < GBS_MAX_SLOTS; ++i) {
+    sd[i].m = h->slots[i].m;
+    for (int k = 0; k < h->slots[i].m; ++k) {
+      sd[i].steps[k] = h->slots[i].steps[k];
+      sd[i].c[k] = h->slots[i].c[k];
+    }
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(h->d_slots, sd, sizeof sd, cudaMemcpyHostToDevice));
+  for (int p = 0; p < h->batch; ++p) h->probs[p].slot = h->slot_of[p];
+  CK(h, cudaMemcpy(h->d_probs, h->probs.data(), sizeof(ProbDev) * h->batch, cudaMemcpyHostToDevice));
+  ++h->sched_version;
+  return GBS_OK;
+}
+
+gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
+  std::memset(p, 0, sizeof *p);
+  p->system = h->system;
+  p->ndim = h->ndim;
+  p->R = h->R;
+  p->f64 = h->f64;
+  p->F = h->F;
+  p->batch = h->batch;
+  p->probs = h->d_probs;
+  p->slots = h->d_slots;
+  p->H = h->d_H;
+  p->total_blocks = h->total_blocks;
+  p->state_elems = h->state_elems;
+  p->kappa = h->kappa;
+  p->b = h->b;
+  p->f0 = h->f0;
+  p->L0 = h->L0;
+  p->L1 = h->L1;
+  p->acc = h->acc;
+  h->active_pts.assign((size_t)GBS_MAX_SEQ * (GBS_MAX_STEPS + 1), 0);
+  for (int q = 0; q < h->batch; ++q) {
+    const Slot& s = h->slots[h->slot_of[q]];
+    if (!s.set) return fail(h, GBS_ERR_STATE, "problem %d uses weight slot %d which has no weights", q, h->slot_of[q]);
+    p->max_m = std::max(p->max_m, s.m);
+    for (int k = 0; k < s.m; ++k) {
+      p->max_steps_k[k] = std::max(p->max_steps_k[k], s.steps[k]);
+      for (int n = 1; n <= s.steps[k]; ++n) h->active_pts[k * (GBS_MAX_STEPS + 1) + n] += h->probs[q].pts;
+    }
+  }
+  p->active_pts = h->active_pts.data();
+  // plain leap-frog step: read y_(n-1) and y_n, write y_(n+1) (F fields each), read the media
+  p->unit_bytes = (double)h->esz * (3.0 * h->F + (h->system == GBS_ACOUSTIC ? 2.0 : 0.0));
+  if (h->opt_time_kernels) {
+    p->tev = h->tev.data();
+    p->tev_bytes = h->tev_bytes.data();
+    p->tev_cap = (int)h->tev.size() / 2;
+    p->tev_used = &h->tev_used;
+  }
+  return GBS_OK;
+}
+
+gbs_status set_H(gbs_ctx* h, const double* H) {
+  bool same = (int)h->cur_H.size() == h->batch;
+  for (int p = 0; p < h->batch; ++p) {
+    if (!(H[p] > 0) || !std::isfinite(H[p])) return fail(h, GBS_ERR_INVALID, "H[%d] must be finite and > 0", p);
+    if (same && h->cur_H[p] != H[p]) same = false;
+  }
+  if (same) return GBS_OK;
+  h->cur_H.assign(H, H + h->batch);
+  // pageable source: the call returns once the values are staged, so cur_H may change afterwards
+  CK(h, cudaMemcpyAsync(h->d_H, h->cur_H.data(), sizeof(double) * h->batch, cudaMemcpyHostToDevice, h->stream));
+  return GBS_OK;
+}
+
+bool use_fused(gbs_ctx* h, const StepPlan& p) {
+  if (h->opt_kernel == GBS_KERNEL_PLAIN) return false;
+  return fused_supported(p);
+}
+
+// Enqueue one macro-step on stream s (no graph).  Returns launches or -1.
+int enqueue_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo, cudaStream_t s, int kernel) {
+  if (kernel == GBS_KERNEL_FUSED)
+    return fused_macro_step(p, yi, yo, s, h->d_err, h->fused_scratch, h->fused_scratch_bytes);
+  return plain_macro_step(p, yi, yo, s);
+}
+
+gbs_status run_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo) {
+  const int kernel = use_fused(h, p) ? GBS_KERNEL_FUSED : GBS_KERNEL_PLAIN;
+  if (!h->opt_graph || h->opt_time_kernels) {
+    const int n = enqueue_macro(h, p, yi, yo, h->stream, kernel);
+    if (n < 0) return fail(h, GBS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->launches += n;
+    return GBS_OK;
+  }
+  GraphEntry* ge = nullptr;
+  for (auto& g : h->graphs)
+    if (g.yi == yi && g.yo == yo && g.kernel == kernel && g.version == h->sched_version) ge = &g;
+  if (!ge) {
+    if (h->graphs.size() >= 4) {
+      cudaGraphExecDestroy(h->graphs.front().exec);
+      h->graphs.erase(h->graphs.begin());
+    }
+    GraphEntry g;
+    g.yi = yi;
+    g.yo = yo;
+    g.kernel = kernel;
+    g.version = h->sched_version;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const int n = enqueue_macro(h, p, yi, yo, h->cap, kernel);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (n < 0 || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(h, GBS_ERR_CUDA, "graph capture of the macro-step failed");
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return fail(h, GBS_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e2));
+    g.launches = n;
+    h->graphs.push_back(g);
+    ge = &h->graphs.back();
+  }
+  CK(h, cudaGraphLaunch(ge->exec, h->stream));
+  h->launches += ge->launches;
+  return GBS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public entry points
+// ===========================================================================
+
+extern "C" {
+
+size_t gbs_state_elems(const gbs_problem* pb) {
+  if (validate_problem(pb, nullptr) != GBS_OK) return 0;
+  return (size_t)sizes_of(pb).state_elems;
+}
+
+size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps) {
+  if (validate_problem(pb, nullptr) != GBS_OK || max_steps < 0) return 0;
+  const Sizes s = sizes_of(pb);
+  const size_t esz = pb->precision == GBS_F64 ? 8 : 4;
+  size_t bytes = 0;
+  bytes += 4 * s.state_elems * esz;       // f0, L0, L1, stage
+  bytes += 8 * s.state_elems;             // acc
+  bytes += s.media_elems * esz;           // b
+  if (pb->enable_adjoint) bytes += (size_t)(max_steps + 2 + 3) * s.state_elems * esz;
+  bytes += sizeof(ProbDev) * pb->batch + sizeof(SlotDev) * GBS_MAX_SLOTS + 8 * pb->batch * 2 +
+           8 * (4 * kNormBlocks + 4) + 64;
+  return bytes;
+}
+
+gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho, void* cuda_stream,
+                      gbs_handle* out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, GBS_ERR_INVALID, "out pointer is NULL");
+  *out = nullptr;
+  gbs_status st = validate_problem(pb, nullptr);
+  if (st != GBS_OK) return st;
+  if (pb->system == GBS_WAVE1D && (kappa || rho))
+    return fail(nullptr, GBS_ERR_INVALID, "GBS_WAVE1D takes no media (kappa and rho must be NULL)");
+  if (pb->system == GBS_ACOUSTIC && (!is_device_ptr(kappa) || !is_device_ptr(rho)))
+    return fail(nullptr, GBS_ERR_INVALID, "kappa and rho must be device pointers");
+  gbs_ctx* h = new gbs_ctx();
+  h->system = pb->system;
+  h->ndim = pb->ndim;
+  h->order = pb->fd_order;
+  h->R = pb->fd_order / 2;
+  h->f64 = pb->precision == GBS_F64;
+  h->esz = h->f64 ? 8 : 4;
+  h->batch = pb->batch;
+  h->F = fields_of(pb->system, pb->ndim);
+  h->adjoint = pb->enable_adjoint != 0;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->slot_of.assign(h->batch, 0);
+  h->probs.resize(h->batch);
+  int64_t soff = 0, moff = 0, blk = 0;
+  for (int p = 0; p < h->batch; ++p) {
+    ProbDev& q = h->probs[p];
+    std::memset(&q, 0, sizeof q);
+    for (int d = 0; d < 3; ++d) {
+      q.n[d] = (int)pb->shape[3 * p + d];
+      q.inv_dx[d] = d < h->ndim ? 1.0 / pb->dx[3 * p + d] : 0.0;
+    }
+    q.pts = (int64_t)q.n[0] * q.n[1] * q.n[2];
+    q.state_off = soff;
+    q.media_off = moff;
+    q.blk_begin = blk;
+    soff += h->F * q.pts;
+    moff += q.pts;
+    blk += (q.pts + kPlainBlock - 1) / kPlainBlock;
+  }
+  h->state_elems = soff;
+  h->media_elems = moff;
+  h->total_blocks = blk;
+  if (blk > 0x7fffffff) {
+    delete h;
+    return fail(nullptr, GBS_ERR_INVALID, "problem too large for one launch grid");
+  }
+  auto bail = [&](gbs_status s) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return s;
+  };
+  const size_t E = (size_t)h->state_elems, P = (size_t)h->media_elems;
+  if ((st = dalloc(h, &h->d_probs, sizeof(ProbDev) * h->batch)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_slots, sizeof(SlotDev) * GBS_MAX_SLOTS)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_H, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_err, 64)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_red, sizeof(double) * (4 * kNormBlocks + 4))) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_cmax, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->f0, E * h->esz)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->L0, E * h->esz)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->L1, E * h->esz)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->acc, E * sizeof(double))) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->stage, E * h->esz)) != GBS_OK) return bail(st);
+  if (h->system == GBS_ACOUSTIC && (st = dalloc(h, &h->b, P * h->esz)) != GBS_OK) return bail(st);
+  if (h->adjoint) {
+    if ((st = dalloc(h, &h->mu0, E * h->esz)) != GBS_OK) return bail(st);
+    if ((st = dalloc(h, &h->mu1, E * h->esz)) != GBS_OK) return bail(st);
+    if ((st = dalloc(h, &h->mu_shared, E * h->esz)) != GBS_OK) return bail(st);
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    fail(h, GBS_ERR_CUDA, "cudaStreamCreate failed");
+    return bail(GBS_ERR_CUDA);
+  }
+  if (cudaMemset(h->d_err, 0, 64) != cudaSuccess || cudaMemset(h->d_slots, 0, sizeof(SlotDev) * GBS_MAX_SLOTS) != cudaSuccess ||
+      cudaMemcpy(h->d_probs, h->probs.data(), sizeof(ProbDev) * h->batch, cudaMemcpyHostToDevice) != cudaSuccess) {
+    fail(h, GBS_ERR_CUDA, "workspace initialisation failed");
+    return bail(GBS_ERR_CUDA);
+  }
+  h->cmax.assign(h->batch, 1.0);
+  *out = h;
+  if (h->system == GBS_ACOUSTIC) {
+    st = gbs_set_media(h, kappa, rho);
+    if (st != GBS_OK) {
+      g_create_error = h->err;
+      *out = nullptr;
+      free_all(h);
+      delete h;
+      return st;
+    }
+  }
+  return GBS_OK;
+}
+
+gbs_status gbs_set_media(gbs_handle h, const void* kappa, const void* rho) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (h->system != GBS_ACOUSTIC) return fail(h, GBS_ERR_INVALID, "media apply to GBS_ACOUSTIC only");
+  if (!is_device_ptr(kappa) || !is_device_ptr(rho)) return fail(h, GBS_ERR_INVALID, "kappa and rho must be device pointers");
+  h->kappa = kappa;
+  if (prep_media(h->f64, rho, h->b, h->media_elems, h->stream) < 0)
+    return fail(h, GBS_ERR_CUDA, "media preparation failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (media_cmax(h->f64, kappa, h->b, h->d_probs, h->batch, h->d_cmax, h->stream) < 0)
+    return fail(h, GBS_ERR_CUDA, "media reduction failed: %s", cudaGetErrorString(cudaGetLastError()));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(h->cmax.data(), h->d_cmax, sizeof(double) * h->batch, cudaMemcpyDeviceToHost));
+  for (int p = 0; p < h->batch; ++p)
+    if (!(h->cmax[p] > 0) || !std::isfinite(h->cmax[p]))
+      return fail(h, GBS_ERR_NONFINITE, "problem %d: media give a non-positive or non-finite wave speed", p);
+  ++h->sched_version;  // graphs hold the kappa pointer
+  return GBS_OK;
+}
+
+gbs_status gbs_set_weights(gbs_handle h, int slot, int order_p, int n_dep, const int* steps_dep, int n_free,
+                           const int* steps_free, const double* c_free, const double* c_full) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (slot < 0 || slot >= GBS_MAX_SLOTS) return fail(h, GBS_ERR_INVALID, "slot %d out of range", slot);
+  if (order_p < 2 || order_p % 2) return fail(h, GBS_ERR_INVALID, "order must be even and >= 2");
+  if (n_dep != order_p / 2) return fail(h, GBS_ERR_INVALID, "n_dep must equal order/2 (%d)", order_p / 2);
+  if (n_free < 0 || n_dep + n_free > GBS_MAX_SEQ) return fail(h, GBS_ERR_INVALID, "too many sequences (max %d)", GBS_MAX_SEQ);
+  if (!steps_dep || (n_free > 0 && !steps_free)) return fail(h, GBS_ERR_INVALID, "step count arrays are required");
+  if (n_free > 0 && !c_free && !c_full) return fail(h, GBS_ERR_INVALID, "free weights are required");
+  const int m = n_dep + n_free;
+  std::vector<int> steps(m);
+  for (int k = 0; k < m; ++k) {
+    const int N = k < n_dep ? steps_dep[k] : steps_free[k - n_dep];
+    if (N < 2 || N > GBS_MAX_STEPS || N % 2) return fail(h, GBS_ERR_INVALID, "step count %d must be even in [2, %d]", N, GBS_MAX_STEPS);
+    for (int l = 0; l < k; ++l)
+      if (steps[l] == N) return fail(h, GBS_ERR_INVALID, "step count %d repeated", N);
+    steps[k] = N;
+  }
+  Slot s;
+  s.order = order_p;
+  s.m = m;
+  for (int k = 0; k < m; ++k) s.steps[k] = steps[k];
+  if (c_full) {
+    for (int k = 0; k < m; ++k) {
+      if (!std::isfinite(c_full[k])) return fail(h, GBS_ERR_INVALID, "weight %d is not finite", k);
+      s.c[k] = c_full[k];
+    }
+  } else {
+    // r_j = b_j - sum_free c_i h_i^(2j), then V_dep c_dep = r (Sec. 3.6), all in dd
+    const int q = n_dep;
+    std::vector<dd> x(q), r(q);
+    for (int i = 0; i < q; ++i) x[i] = inv_sq(steps[i]);
+    for (int j = 0; j < q; ++j) {
+      dd rj = dd_from(j == 0 ? 1.0 : 0.0);
+      for (int i = 0; i < n_free; ++i) {
+        if (!std::isfinite(c_free[i])) return fail(h, GBS_ERR_INVALID, "free weight %d is not finite", i);
+        dd pw = dd_from(1.0);
+        const dd hx = inv_sq(steps[n_dep + i]);
+        for (int e = 0; e < j; ++e) pw = pw * hx;
+        rj = rj - dd_from(c_free[i]) * pw;
+      }
+      r[j] = rj;
+    }
+    bjorck_pereyra_dual(x, r);
+    for (int i = 0; i < q; ++i) s.c[i] = r[i].hi + r[i].lo;
+    for (int i = 0; i < n_free; ++i) s.c[n_dep + i] = c_free[i];
+  }
+  // order constraints with the rounded weights, in dd
+  for (int j = 0; j < order_p / 2; ++j) {
+    dd sum = dd_from(j == 0 ? -1.0 : 0.0);
+    double scale = 0.0;
+    for (int k = 0; k < m; ++k) {
+      dd pw = dd_from(1.0);
+      const dd hx = inv_sq(steps[k]);
+      for (int e = 0; e < j; ++e) pw = pw * hx;
+      sum = sum + dd_from(s.c[k]) * pw;
+      scale += std::fabs(s.c[k]) * (pw.hi + pw.lo);
+    }
+    const double res = std::fabs(sum.hi + sum.lo);
+    if (!(res <= 64.0 * 2.220446049250313e-16 * scale))
+      return fail(h, GBS_ERR_ORDER, "order constraint j=%d violated: residual %.3e > 64 ulp of %.3e", j, res, scale);
+  }
+  s.isb = scan_isb(s);
+  s.set = true;
+  h->slots[slot] = s;
+  if (h->adjoint) {
+    int nmax = 0;
+    for (int k = 0; k < m; ++k) nmax = std::max(nmax, steps[k]);
+    if (nmax > h->levels_steps) {
+      CK(h, cudaStreamSynchronize(h->stream));
+      if (h->levels) cudaFree(h->levels);
+      h->levels = nullptr;
+      h->levels_steps = 0;
+      gbs_status st = dalloc(h, &h->levels, (size_t)(nmax + 2) * h->state_elems * h->esz);
+      if (st != GBS_OK) return st;
+      h->levels_steps = nmax;
+    }
+  }
+  return upload_slots(h);
+}
+
+gbs_status gbs_get_weights(gbs_handle h, int slot, int* m, int* steps, double* c, double* isb) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (slot < 0 || slot >= GBS_MAX_SLOTS) return fail(h, GBS_ERR_INVALID, "slot %d out of range", slot);
+  const Slot& s = h->slots[slot];
+  if (!s.set) return fail(h, GBS_ERR_STATE, "slot %d has no weights", slot);
+  if (m) *m = s.m;
+  for (int k = 0; k < s.m; ++k) {
+    if (steps) steps[k] = s.steps[k];
+    if (c) c[k] = s.c[k];
+  }
+  if (isb) *isb = s.isb;
+  return GBS_OK;
+}
+
+gbs_status gbs_assign_slots(gbs_handle h, const int* slot_per_problem) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!slot_per_problem) return fail(h, GBS_ERR_INVALID, "slot array is NULL");
+  for (int p = 0; p < h->batch; ++p) {
+    const int s = slot_per_problem[p];
+    if (s < 0 || s >= GBS_MAX_SLOTS) return fail(h, GBS_ERR_INVALID, "problem %d: slot %d out of range", p, s);
+    if (!h->slots[s].set) return fail(h, GBS_ERR_STATE, "problem %d: slot %d has no weights", p, s);
+  }
+  h->slot_of.assign(slot_per_problem, slot_per_problem + h->batch);
+  return upload_slots(h);
+}
+
+gbs_status gbs_stability_limit(gbs_handle h, double* H_max) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!H_max) return fail(h, GBS_ERR_INVALID, "H_max is NULL");
+  const double smax = symbol_max(h->R);
+  for (int p = 0; p < h->batch; ++p) {
+    const Slot& s = h->slots[h->slot_of[p]];
+    if (!s.set) return fail(h, GBS_ERR_STATE, "problem %d: slot %d has no weights", p, h->slot_of[p]);
+    double q = 0;
+    for (int d = 0; d < h->ndim; ++d) q += (smax * h->probs[p].inv_dx[d]) * (smax * h->probs[p].inv_dx[d]);
+    const double rho_hat = h->cmax[p] * std::sqrt(q);
+    H_max[p] = s.isb / rho_hat;
+  }
+  return GBS_OK;
+}
+
+gbs_status gbs_step_batch(gbs_handle h, const void* y_in, void* y_out, const double* H, int n_macro) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!H) return fail(h, GBS_ERR_INVALID, "H is NULL");
+  if (n_macro < 0) return fail(h, GBS_ERR_INVALID, "n_macro must be >= 0");
+  if (!y_in || !y_out) return fail(h, GBS_ERR_INVALID, "state pointers must not be NULL");
+  const size_t bytes = (size_t)h->state_elems * h->esz;
+  const char* a = static_cast<const char*>(y_in);
+  const char* b = static_cast<const char*>(y_out);
+  if (a != b && a < b + bytes && b < a + bytes) return fail(h, GBS_ERR_INVALID, "y_in and y_out overlap partially");
+  StepPlan p;
+  gbs_status st = build_plan(h, &p);
+  if (st != GBS_OK) return st;
+  st = set_H(h, H);
+  if (st != GBS_OK) return st;
+  if (h->opt_check_stability) {
+    std::vector<double> hm(h->batch);
+    if ((st = gbs_stability_limit(h, hm.data())) != GBS_OK) return st;
+    for (int q = 0; q < h->batch; ++q)
+      if (H[q] > hm[q]) return fail(h, GBS_ERR_UNSTABLE, "problem %d: H = %g exceeds the stability limit %g", q, H[q], hm[q]);
+  }
+  if (n_macro == 0) {
+    if (a != b) CK(h, cudaMemcpyAsync(y_out, y_in, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return GBS_OK;
+  }
+  for (int it = 0; it < n_macro; ++it) {
+    st = run_macro(h, p, it == 0 ? y_in : y_out, y_out);
+    if (st != GBS_OK) return st;
+  }
+  return GBS_OK;
+}
+
+gbs_status gbs_step(gbs_handle h, const void* y_in, void* y_out, double H, int n_macro) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  std::vector<double> Hs(h->batch, H);
+  return gbs_step_batch(h, y_in, y_out, Hs.data(), n_macro);
+}
+
+gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, double H, int n_macro) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!y_in_host || !y_out_host) return fail(h, GBS_ERR_INVALID, "host buffers must not be NULL");
+  const size_t bytes = (size_t)h->state_elems * h->esz;
+  CK(h, cudaMemcpyAsync(h->stage, y_in_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  gbs_status st = gbs_step(h, h->stage, h->stage, H, n_macro);
+  if (st != GBS_OK) return st;
+  CK(h, cudaMemcpyAsync(y_out_host, h->stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return GBS_OK;
+}
+
+gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out, void* lam_in, double* grad_kappa,
+                            double H, const int64_t* rcv_idx, int n_rcv, const void* rcv_resid) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!h->adjoint) return fail(h, GBS_ERR_STATE, "handle was created without enable_adjoint");
+  if (!y_in || !lam_out || !lam_in || !grad_kappa) return fail(h, GBS_ERR_INVALID, "pointers must not be NULL");
+  if (n_rcv < 0 || (n_rcv > 0 && (!rcv_idx || !rcv_resid))) return fail(h, GBS_ERR_INVALID, "bad receiver arguments");
+  if (n_rcv > 0 && h->batch != 1) return fail(h, GBS_ERR_INVALID, "receivers need batch == 1");
+  AdjPlan a;
+  gbs_status st = build_plan(h, &a.fw);
+  if (st != GBS_OK) return st;
+  for (int k = 0; k < a.fw.max_m; ++k)
+    if (a.fw.max_steps_k[k] > h->levels_steps) return fail(h, GBS_ERR_STATE, "adjoint level store too small");
+  std::vector<double> Hs(h->batch, H);
+  if ((st = set_H(h, Hs.data())) != GBS_OK) return st;
+  a.levels = h->levels;
+  a.mu0 = h->mu0;
+  a.mu1 = h->mu1;
+  a.shared = h->mu_shared;
+  a.max_steps = h->levels_steps;
+  const int n = plain_adjoint_step(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, h->stream);
+  if (n < 0) return fail(h, GBS_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += n;
+  return GBS_OK;
+}
+
+gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n_rcv, const void* data, void* resid,
+                      double* J) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!y || !rcv_idx || !data || n_rcv < 0) return fail(h, GBS_ERR_INVALID, "bad misfit arguments");
+  if (n_rcv == 0) return GBS_OK;
+  if (misfit(h->f64, y, rcv_idx, n_rcv, data, resid, J, h->stream) < 0)
+    return fail(h, GBS_ERR_CUDA, "misfit launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += 1;
+  return GBS_OK;
+}
+
+gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!a || !out) return fail(h, GBS_ERR_INVALID, "bad norms arguments");
+  const int n = norms(h->f64, a, b, h->state_elems, h->d_red, h->d_red + 4 * kNormBlocks, h->stream);
+  if (n < 0) return fail(h, GBS_ERR_CUDA, "norms launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += n;
+  CK(h, cudaMemcpyAsync(out, h->d_red + 4 * kNormBlocks, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return GBS_OK;
+}
+
+gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!name) return fail(h, GBS_ERR_INVALID, "option name is NULL");
+  if (!std::strcmp(name, "kernel")) {
+    if (value < GBS_KERNEL_AUTO || value > GBS_KERNEL_FUSED) return fail(h, GBS_ERR_INVALID, "bad kernel option");
+    if (value == GBS_KERNEL_FUSED) {
+      StepPlan p;
+      gbs_status st = build_plan(h, &p);
+      if (st != GBS_OK) return st;
+      if (!fused_supported(p)) return fail(h, GBS_ERR_INVALID, "the fused kernel does not support this problem");
+    }
+    h->opt_kernel = (int)value;
+  } else if (!std::strcmp(name, "graph")) {
+    h->opt_graph = value != 0;
+  } else if (!std::strcmp(name, "check_stability")) {
+    h->opt_check_stability = value != 0;
+  } else if (!std::strcmp(name, "time_kernels")) {
+    if (value && h->tev.empty()) {
+      const int pairs = 8192;
+      h->tev.resize(2 * pairs);
+      h->tev_bytes.assign(pairs, 0.0);
+      for (auto& e : h->tev) CK(h, cudaEventCreate(&e));
+    }
+    h->opt_time_kernels = value != 0;
+    h->tev_used = 0;
+  } else {
+    return fail(h, GBS_ERR_INVALID, "unknown option '%s'", name);
+  }
+  ++h->sched_version;
+  return GBS_OK;
+}
+
+gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!name || !value) return fail(h, GBS_ERR_INVALID, "bad arguments");
+  if (!std::strcmp(name, "kernel")) *value = h->opt_kernel;
+  else if (!std::strcmp(name, "graph")) *value = h->opt_graph;
+  else if (!std::strcmp(name, "check_stability")) *value = h->opt_check_stability;
+  else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
+  else if (!std::strcmp(name, "kernel_in_use")) {
+    StepPlan p;
+    gbs_status st = build_plan(h, &p);
+    if (st != GBS_OK) return st;
+    *value = use_fused(h, p) ? GBS_KERNEL_FUSED : GBS_KERNEL_PLAIN;
+  } else return fail(h, GBS_ERR_INVALID, "unknown option '%s'", name);
+  return GBS_OK;
+}
+
+gbs_status gbs_kernel_time(gbs_handle h, int64_t* launches, double* total_ms, double* bytes) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!launches || !total_ms) return fail(h, GBS_ERR_INVALID, "output pointers must not be NULL");
+  CK(h, cudaStreamSynchronize(h->stream));
+  double ms = 0, by = 0;
+  for (int u = 0; u < h->tev_used; ++u) {
+    float t = 0;
+    CK(h, cudaEventElapsedTime(&t, h->tev[2 * u], h->tev[2 * u + 1]));
+    ms += t;
+    by += h->tev_bytes[u];
+  }
+  *launches = h->tev_used;
+  *total_ms = ms;
+  if (bytes) *bytes = by;
+  h->tev_used = 0;
+  return GBS_OK;
+}
+
+gbs_status gbs_sync(gbs_handle h) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  CK(h, cudaStreamSynchronize(h->stream));
+  int flag = 0;
+  CK(h, cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(h->d_err, 0, sizeof(int));
+    if (flag == GBS_ERR_TIMEOUT) return fail(h, GBS_ERR_TIMEOUT, "a device-side wait timed out");
+    return fail(h, (gbs_status)flag, "device-side error %d", flag);
+  }
+  return GBS_OK;
+}
+
+gbs_status gbs_destroy(gbs_handle h) {
+  if (!h) return GBS_OK;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return GBS_OK;
+}
+
+const char* gbs_last_error(gbs_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t gbs_kernel_launches(gbs_handle h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the host library and its CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gbs.h"
+
+namespace gbs {
+
+constexpr int kMaxFields = 4;
+
+// One problem of a batch, as the kernels see it.
+struct ProbDev {
+  int n[3];            // nx, ny, nz (unused dims = 1)
+  int slot;            // weight slot
+  int64_t pts;         // nx * ny * nz
+  int64_t state_off;   // element offset of the problem's [F][nz][ny][nx] block
+  int64_t media_off;   // element offset of its [nz][ny][nx] media block
+  int64_t blk_begin;   // first block of this problem in a point-parallel grid
+  double inv_dx[3];
+};
+
+// One weight slot: m sequences with step counts and FP64 weights, in
+// combine order (dependent weights first, then free ones).
+struct SlotDev {
+  int m;
+  int steps[GBS_MAX_SEQ];
+  double c[GBS_MAX_SEQ];
+};
+
+// Everything a macro-step launcher needs (device pointers except where noted).
+struct StepPlan {
+  int system, ndim, R, f64;    // f64: 1 = GBS_F64 path, 0 = FP32 state
+  int F;
+  int batch;
+  const ProbDev* probs;
+  const SlotDev* slots;
+  const double* H;             // per problem
+  int64_t total_blocks;        // point-parallel blocks over the whole batch
+  int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
+  const void* kappa;           // media (state element type)
+  const void* b;               // 1 / rho
+  void* f0;                    // shared first RHS, F x P
+  void* L0;                    // leap-frog level buffers, F x P each
+  void* L1;
+  double* acc;                 // FP64 combine accumulator, F x P
+  // host-side schedule: for sequence index k, the largest step count over problems
+  int max_m;
+  int max_steps_k[GBS_MAX_SEQ];
+  // optional kernel timing (host pointers): event pairs around each dominant-kernel
+  // launch, and the algorithmic bytes of that launch
+  cudaEvent_t* tev;
+  double* tev_bytes;
+  int tev_cap;
+  int* tev_used;
+  const int64_t* active_pts;   // [k * (GBS_MAX_STEPS + 1) + n]: points updated by step (k, n)
+  double unit_bytes;           // algorithmic bytes per grid-point update of the dominant kernel
+};
+
+// Record the start of a timed launch; returns the slot index or -1.
+inline int timing_begin(const StepPlan& p, cudaStream_t s) {
+  if (!p.tev || *p.tev_used >= p.tev_cap) return -1;
+  const int u = (*p.tev_used)++;
+  cudaEventRecord(p.tev[2 * u], s);
+  return u;
+}
+inline void timing_end(const StepPlan& p, int u, cudaStream_t s, double bytes) {
+  if (u < 0) return;
+  cudaEventRecord(p.tev[2 * u + 1], s);
+  p.tev_bytes[u] = bytes;
+}
+
+constexpr int kPlainBlock = 256;
+
+// Enqueue one plain macro-step (y_in -> y_out) on `s`.  Returns the number of
+// kernels launched, or -1 if a launch failed (cudaGetLastError set).
+int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s);
+
+// Adjoint of one macro-step with stored forward levels (plain kernels).
+struct AdjPlan {
+  StepPlan fw;
+  void* levels;                // (max_steps + 2) x F x P forward levels
+  void* mu0;                   // two adjoint level buffers, F x P each
+  void* mu1;
+  void* shared;                // sum_k h_k mu_1^k, F x P (state type)
+  int max_steps;
+};
+int plain_adjoint_step(const AdjPlan& p, const void* y_in, const void* lam_out, void* lam_in,
+                       double* grad_kappa, const int64_t* rcv_idx, int n_rcv,
+                       const void* rcv_resid, cudaStream_t s);
+
+// Media preparation and reductions (gbs_reduce.cu).
+int prep_media(int f64, const void* rho, void* b, int64_t n, cudaStream_t s);
+// max over each problem of sqrt(kappa * b): out[batch] (device double), scratch >= batch*1024 doubles
+int media_cmax(int f64, const void* kappa, const void* b, const ProbDev* probs, int batch,
+               double* out, cudaStream_t s);
+// norms: out4 device doubles; partial: device scratch of >= 4 * kNormBlocks doubles
+constexpr int kNormBlocks = 1024;
+int norms(int f64, const void* a, const void* b, int64_t n, double* partial, double* out4,
+          cudaStream_t s);
+int misfit(int f64, const void* y, const int64_t* idx, int n_rcv, const void* data, void* resid,
+           double* J, cudaStream_t s);
+
+}  // namespace gbs

@@ -1,0 +1,435 @@
+// Point-parallel ("plain") GBS kernels: one kernel per Forward-Euler or
+// leap-frog step, one thread per grid point, neighbours read through the
+// read-only cache.  This is the unfused path, used for FP64 and as the
+// baseline the time-blocked FP32 kernels are measured against.
+//
+// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.5, Sec. 3.2):
+//   k_f0             f0 = f(y_in)                       shared first evaluation
+//   for each sequence index k:
+//     k_fe(k)        L1 = y_in + h_k f0                 Forward Euler
+//     k_lf(k, n)     n = 1..N_k-1: y_(n+1) = y_(n-1) + 2 h_k f(y_n)   (in place over y_(n-1))
+//                    n = N_k: y_(N+1), averaging and the FP64 combine
+//                    acc (+)= c_k y*_k, the last sequence writing y_out
+// With a batch, every launch covers all problems; a problem whose scheme has
+// no step (k, n) leaves the launch at once.
+#include <cuda_runtime.h>
+
+#include "gbs_internal.h"
+#include "gbs_stencil.cuh"
+
+namespace gbs {
+namespace {
+
+struct Loc {
+  int prob;
+  int64_t i;
+};
+
+// Map this thread to (problem, point); prob = -1 when past the problem's end.
+__device__ __forceinline__ Loc locate(const StepPlan& p) {
+  int lo = 0, hi = p.batch - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {  // last problem with blk_begin <= blk
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.probs[mid].blk_begin <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  Loc L;
+  L.prob = lo;
+  L.i = (blk - p.probs[lo].blk_begin) * kPlainBlock + threadIdx.x;
+  if (L.i >= p.probs[lo].pts) L.prob = -1;
+  return L;
+}
+
+__device__ __forceinline__ PointGeo geo_of(const ProbDev& q, int64_t i) {
+  PointGeo g;
+  g.i = i;
+  g.n[0] = q.n[0];
+  g.n[1] = q.n[1];
+  g.n[2] = q.n[2];
+  g.st[0] = 1;
+  g.st[1] = q.n[0];
+  g.st[2] = (int64_t)q.n[0] * q.n[1];
+  g.c[0] = (int)(i % q.n[0]);
+  const int64_t r = i / q.n[0];
+  g.c[1] = (int)(r % q.n[1]);
+  g.c[2] = (int)(r / q.n[1]);
+  return g;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_inv_dx(const ProbDev& q, T* inv_dx) {
+  inv_dx[0] = T(q.inv_dx[0]);
+  inv_dx[1] = T(q.inv_dx[1]);
+  inv_dx[2] = T(q.inv_dx[2]);
+}
+
+template <typename T, int SYS, int DIM, int R>
+__global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* __restrict__ y_in) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const PointGeo g = geo_of(q, L.i);
+  constexpr int F = n_fields<SYS, DIM>();
+  T inv_dx[3];
+  load_inv_dx(q, inv_dx);
+  T kap = T(0), bb = T(0);
+  if (SYS == SYS_ACOUSTIC) {
+    kap = ldg(static_cast<const T*>(p.kappa) + q.media_off + L.i);
+    bb = ldg(static_cast<const T*>(p.b) + q.media_off + L.i);
+  }
+  T f[kMaxFields];
+  rhs_point<T, SYS, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx, kap, bb, f);
+  T* f0 = static_cast<T*>(p.f0) + q.state_off;
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) f0[fl * q.pts + L.i] = f[fl];
+}
+
+template <typename T, int SYS, int DIM>
+__global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* __restrict__ y_in, int k) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  constexpr int F = n_fields<SYS, DIM>();
+  const T h = T(p.H[L.prob] / s.steps[k]);
+  const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
+  T* L1 = static_cast<T*>(p.L1) + q.state_off;
+  const T* y0 = y_in + q.state_off;
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    L1[e] = y0[e] + h * f0[e];
+  }
+}
+
+template <typename T, int SYS, int DIM, int R>
+__global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y_in, T* y_out, int k, int n) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  constexpr int F = n_fields<SYS, DIM>();
+  const double hd = p.H[L.prob] / N;
+  const T h2 = T(2.0 * hd);
+  T* Lb[2] = {static_cast<T*>(p.L0) + q.state_off, static_cast<T*>(p.L1) + q.state_off};
+  const T* cur = Lb[n & 1];
+  const T* prev = (n == 1) ? (y_in + q.state_off) : Lb[(n + 1) & 1];
+  T* dst = Lb[(n + 1) & 1];
+  const PointGeo g = geo_of(q, L.i);
+  T inv_dx[3];
+  load_inv_dx(q, inv_dx);
+  T kap = T(0), bb = T(0);
+  if (SYS == SYS_ACOUSTIC) {
+    kap = ldg(static_cast<const T*>(p.kappa) + q.media_off + L.i);
+    bb = ldg(static_cast<const T*>(p.b) + q.media_off + L.i);
+  }
+  T f[kMaxFields];
+  rhs_point<T, SYS, DIM, R>(cur, q.pts, g, inv_dx, kap, bb, f);
+  if (n < N) {
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * q.pts + L.i;
+      dst[e] = prev[e] + h2 * f[fl];
+    }
+    return;
+  }
+  // n == N: y_(N+1), averaging y* = (y_(N-1) + 2 y_N + y_(N+1)) / 4 in FP64, combine.
+  const double c = s.c[k];
+  const bool first = (k == 0), last = (k == s.m - 1);
+  double* acc = p.acc + q.state_off;
+  T* yo = y_out + q.state_off;
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    const T ym = prev[e];
+    const T y0 = cur[e];
+    const T yp = ym + h2 * f[fl];
+    const double ys = ((double)ym + 2.0 * (double)y0 + (double)yp) * 0.25;
+    const double a = first ? c * ys : fma(c, ys, acc[e]);
+    if (last) yo[e] = T(a);
+    else acc[e] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint kernels (acoustics)
+// ---------------------------------------------------------------------------
+
+// Forward level store: lev[n+1] = lev[n-1] + 2h f(lev[n]) (n >= 1), lev[1] = y_in + h f0.
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(kPlainBlock) k_adj_fwd(const StepPlan p, const T* __restrict__ y_in,
+                                                         T* lev, int64_t lev_stride, int k, int n) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  constexpr int F = 1 + DIM;
+  const double hd = p.H[L.prob] / N;
+  const T* y0 = y_in + q.state_off;
+  auto level = [&](int j) -> T* { return lev + (int64_t)j * lev_stride + q.state_off; };
+  if (n == 0) {
+    const T h = T(hd);
+    const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
+    T* d = level(1);
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * q.pts + L.i;
+      d[e] = y0[e] + h * f0[e];
+    }
+    return;
+  }
+  const T* cur = level(n);
+  const T* prev = (n == 1) ? y0 : level(n - 1);
+  T* dst = level(n + 1);
+  const PointGeo g = geo_of(q, L.i);
+  T inv_dx[3];
+  load_inv_dx(q, inv_dx);
+  const T kap = ldg(static_cast<const T*>(p.kappa) + q.media_off + L.i);
+  const T bb = ldg(static_cast<const T*>(p.b) + q.media_off + L.i);
+  T f[kMaxFields];
+  rhs_point<T, SYS_ACOUSTIC, DIM, R>(cur, q.pts, g, inv_dx, kap, bb, f);
+  const T h2 = T(2.0 * hd);
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    dst[e] = prev[e] + h2 * f[fl];
+  }
+}
+
+// Reverse step j (N >= j >= 1), in place over the buffer of M[j+2]:
+//   M[j] = M[j+2] + init_j + 2h A^T M[j+1],  init_N = w/2, init_(N-1) = w/4 (w = c_k lam_out),
+//   M[N+2] = 0;  g += 2h mu_p (-div y_j) with mu = M[j+1].
+// j == N + 1 initialises M[N+1] = w/4.
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(kPlainBlock) k_adj_rev(const StepPlan p, const T* __restrict__ y_in,
+                                                         const T* __restrict__ lev, int64_t lev_stride,
+                                                         const T* __restrict__ lam_out, T* mA, T* mB,
+                                                         double* grad, int k, int jrev) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  // jrev counts launches 0.. ; launch t handles j = N + 1 - t (problems with smaller N skip)
+  const int j = N + 1 - jrev;
+  if (j < 1) return;
+  constexpr int F = 1 + DIM;
+  const double hd = p.H[L.prob] / N;
+  const double c = s.c[k];
+  // M[j] lives in buffer ((N + 1 - j) & 1) == 0 ? A : B
+  T* dst = (((N + 1 - j) & 1) == 0 ? mA : mB) + q.state_off;
+  const T* src = (((N + 1 - j) & 1) == 0 ? mB : mA) + q.state_off;  // M[j+1]
+  const T* lo = lam_out + q.state_off;
+  if (j == N + 1) {
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * q.pts + L.i;
+      dst[e] = T(0.25 * c * (double)lo[e]);
+    }
+    return;
+  }
+  const PointGeo g = geo_of(q, L.i);
+  T inv_dx[3];
+  load_inv_dx(q, inv_dx);
+  const T* kappa = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  T at[kMaxFields];
+  rhs_T_point<T, DIM, R>(src, q.pts, g, inv_dx, kappa, bmed, at);
+  const T h2 = T(2.0 * hd);
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    T base = (j <= N - 1) ? dst[e] : T(0);          // M[j+2]
+    if (j == N) base += T(0.5 * c * (double)lo[e]);
+    if (j == N - 1) base += T(0.25 * c * (double)lo[e]);
+    dst[e] = base + h2 * at[fl];
+  }
+  // gradient term 2h mu_p (-div y_j), y_j = level j (y_in for j == 0, never here)
+  const T* yj = lev + (int64_t)j * lev_stride + q.state_off;
+  const T dv = div_point<T, DIM, R>(yj, q.pts, g, inv_dx);
+  grad[q.media_off + L.i] += 2.0 * hd * (double)src[L.i] * (-(double)dv);
+}
+
+// After the reverse sweep of sequence k: acc (+)= M[1] + M[2], shared (+)= h_k M[1].
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPlainBlock) k_adj_gather(const StepPlan p, const T* mA, const T* mB,
+                                                            T* shared, int k) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  constexpr int F = 1 + DIM;
+  const double hd = p.H[L.prob] / N;
+  // M[1]: (N + 1 - 1) = N even -> buffer A; M[2] -> buffer B
+  const T* m1 = mA + q.state_off;
+  const T* m2 = mB + q.state_off;
+  double* acc = p.acc + q.state_off;
+  T* sh = shared + q.state_off;
+  const bool first = (k == 0);
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    const double v = (double)m1[e] + (double)m2[e];
+    acc[e] = first ? v : acc[e] + v;
+    const T hv = T(hd) * m1[e];
+    sh[e] = first ? hv : sh[e] + hv;
+  }
+}
+
+// lam_in = acc + A^T shared;  g += (shared)_p (-div y_in).
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(kPlainBlock) k_adj_finish(const StepPlan p, const T* __restrict__ y_in,
+                                                            const T* __restrict__ shared, T* lam_in,
+                                                            double* grad) {
+  const Loc L = locate(p);
+  if (L.prob < 0) return;
+  const ProbDev& q = p.probs[L.prob];
+  constexpr int F = 1 + DIM;
+  const PointGeo g = geo_of(q, L.i);
+  T inv_dx[3];
+  load_inv_dx(q, inv_dx);
+  const T* kappa = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  const T* sh = shared + q.state_off;
+  T at[kMaxFields];
+  rhs_T_point<T, DIM, R>(sh, q.pts, g, inv_dx, kappa, bmed, at);
+  const double* acc = p.acc + q.state_off;
+  T* li = lam_in + q.state_off;
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    li[e] = T(acc[e] + (double)at[fl]);
+  }
+  const T dv = div_point<T, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx);
+  grad[q.media_off + L.i] += (double)sh[L.i] * (-(double)dv);
+}
+
+template <typename T>
+__global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) atomicAdd(lam + idx[r], resid[r]);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch
+// ---------------------------------------------------------------------------
+
+template <typename T, int SYS, int DIM, int R>
+int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStream_t st) {
+  const T* y_in = static_cast<const T*>(y_in_v);
+  T* y_out = static_cast<T*>(y_out_v);
+  const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
+  int launches = 0;
+  k_f0<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in);
+  ++launches;
+  for (int k = 0; k < p.max_m; ++k) {
+    k_fe<T, SYS, DIM><<<grid, block, 0, st>>>(p, y_in, k);
+    ++launches;
+    for (int n = 1; n <= p.max_steps_k[k]; ++n) {
+      const int u = timing_begin(p, st);
+      k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
+      timing_end(p, u, st, p.tev ? p.unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + n] : 0.0);
+      ++launches;
+    }
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+template <typename T, int DIM, int R>
+int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, void* lam_in_v,
+                   double* grad, const int64_t* rcv_idx, int n_rcv, const void* rcv_resid,
+                   cudaStream_t st) {
+  const StepPlan& p = a.fw;
+  const T* y_in = static_cast<const T*>(y_in_v);
+  const T* lam_out = static_cast<const T*>(lam_out_v);
+  T* lam_in = static_cast<T*>(lam_in_v);
+  T* lev = static_cast<T*>(a.levels);
+  const int64_t lev_stride = p.state_elems;
+  T* mA = static_cast<T*>(a.mu0);
+  T* mB = static_cast<T*>(a.mu1);
+  T* shared = static_cast<T*>(a.shared);
+  const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
+  int launches = 0;
+  k_f0<T, SYS_ACOUSTIC, DIM, R><<<grid, block, 0, st>>>(p, y_in);
+  ++launches;
+  for (int k = 0; k < p.max_m; ++k) {
+    const int Nk = p.max_steps_k[k];
+    for (int n = 0; n <= Nk; ++n) {
+      k_adj_fwd<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, k, n);
+      ++launches;
+    }
+    for (int t = 0; t <= Nk; ++t) {
+      k_adj_rev<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, lam_out, mA, mB, grad, k, t);
+      ++launches;
+    }
+    k_adj_gather<T, DIM><<<grid, block, 0, st>>>(p, mA, mB, shared, k);
+    ++launches;
+  }
+  k_adj_finish<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, shared, lam_in, grad);
+  ++launches;
+  if (n_rcv > 0) {
+    k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid));
+    ++launches;
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+template <typename T>
+int macro_step_sys(const StepPlan& p, const void* yi, void* yo, cudaStream_t s) {
+  if (p.system == GBS_WAVE1D) {
+    return p.R == 2 ? macro_step_t<T, SYS_WAVE1D, 1, 2>(p, yi, yo, s)
+                    : macro_step_t<T, SYS_WAVE1D, 1, 3>(p, yi, yo, s);
+  }
+  switch (p.ndim * 10 + p.R) {
+    case 12: return macro_step_t<T, SYS_ACOUSTIC, 1, 2>(p, yi, yo, s);
+    case 13: return macro_step_t<T, SYS_ACOUSTIC, 1, 3>(p, yi, yo, s);
+    case 22: return macro_step_t<T, SYS_ACOUSTIC, 2, 2>(p, yi, yo, s);
+    case 23: return macro_step_t<T, SYS_ACOUSTIC, 2, 3>(p, yi, yo, s);
+    case 32: return macro_step_t<T, SYS_ACOUSTIC, 3, 2>(p, yi, yo, s);
+    case 33: return macro_step_t<T, SYS_ACOUSTIC, 3, 3>(p, yi, yo, s);
+  }
+  return -1;
+}
+
+template <typename T>
+int adjoint_sys(const AdjPlan& a, const void* yi, const void* lo, void* li, double* g,
+                const int64_t* ri, int nr, const void* rr, cudaStream_t s) {
+  switch (a.fw.ndim * 10 + a.fw.R) {
+    case 12: return adjoint_step_t<T, 1, 2>(a, yi, lo, li, g, ri, nr, rr, s);
+    case 13: return adjoint_step_t<T, 1, 3>(a, yi, lo, li, g, ri, nr, rr, s);
+    case 22: return adjoint_step_t<T, 2, 2>(a, yi, lo, li, g, ri, nr, rr, s);
+    case 23: return adjoint_step_t<T, 2, 3>(a, yi, lo, li, g, ri, nr, rr, s);
+    case 32: return adjoint_step_t<T, 3, 2>(a, yi, lo, li, g, ri, nr, rr, s);
+    case 33: return adjoint_step_t<T, 3, 3>(a, yi, lo, li, g, ri, nr, rr, s);
+  }
+  return -1;
+}
+
+}  // namespace
+
+int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
+  return p.f64 ? macro_step_sys<double>(p, y_in, y_out, s) : macro_step_sys<float>(p, y_in, y_out, s);
+}
+
+int plain_adjoint_step(const AdjPlan& a, const void* y_in, const void* lam_out, void* lam_in,
+                       double* grad_kappa, const int64_t* rcv_idx, int n_rcv,
+                       const void* rcv_resid, cudaStream_t s) {
+  if (a.fw.system != GBS_ACOUSTIC) return -1;
+  return a.fw.f64 ? adjoint_sys<double>(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, s)
+                  : adjoint_sys<float>(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, s);
+}
+
+}  // namespace gbs

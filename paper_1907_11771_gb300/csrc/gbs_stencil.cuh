@@ -1,0 +1,117 @@
+// Periodic centred finite-difference stencils and the wave right-hand sides,
+// as device functions over global memory (point-parallel kernels).
+//
+// First derivative, radius R (order 2R), antisymmetric weights a_j:
+//   (D f)_i = (1/dx) sum_{j=1..R} a_j (f_{i+j} - f_{i-j})
+//   R = 2 (order 4): a = (2/3, -1/12)
+//   R = 3 (order 6): a = (3/4, -3/20, 1/60)
+// Systems (f(y) = A y):
+//   1D wave:   f_u = D v, f_v = D u
+//   acoustics: f_p = -kappa sum_d D_d u_d,  f_{u_d} = -b D_d p   (b = 1/rho)
+// Transposed operator (D_d^T = -D_d on a periodic grid):
+//   (A^T l)_p = sum_d D_d (b l_{u_d}),  (A^T l)_{u_d} = D_d (kappa l_p)
+#pragma once
+
+#include <cstdint>
+
+namespace gbs {
+
+enum { SYS_WAVE1D = 1, SYS_ACOUSTIC = 2 };
+
+template <int R>
+__host__ __device__ constexpr double fd_coef(int j) {
+  return R == 2 ? (j == 1 ? 2.0 / 3.0 : -1.0 / 12.0)
+                : (j == 1 ? 0.75 : (j == 2 ? -0.15 : 1.0 / 60.0));
+}
+
+template <int SYS, int DIM>
+__host__ __device__ constexpr int n_fields() {
+  return SYS == SYS_WAVE1D ? 2 : 1 + DIM;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Geometry of one point inside one problem.
+struct PointGeo {
+  int64_t i;        // flat point index inside the problem
+  int c[3];         // coordinates (x, y, z)
+  int n[3];         // sizes
+  int64_t st[3];    // strides (1, nx, nx*ny)
+};
+
+__device__ __forceinline__ int64_t nb_off(int c, int j, int n, int64_t st) {
+  int cj = c + j;
+  if (cj >= n) cj -= n;
+  else if (cj < 0) cj += n;
+  return (int64_t)(cj - c) * st;
+}
+
+// D_d f at the point (read-only input f).
+template <typename T, int R>
+__device__ __forceinline__ T dstencil(const T* __restrict__ f, const PointGeo& g, int d, T inv_dx) {
+  T s = T(0);
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const T fp = ldg(f + g.i + nb_off(g.c[d], j, g.n[d], g.st[d]));
+    const T fm = ldg(f + g.i + nb_off(g.c[d], -j, g.n[d], g.st[d]));
+    s += T(fd_coef<R>(j)) * (fp - fm);
+  }
+  return s * inv_dx;
+}
+
+// D_d (w * f) at the point, w a media array (for the transposed operator).
+template <typename T, int R>
+__device__ __forceinline__ T dstencil_w(const T* __restrict__ f, const T* __restrict__ w,
+                                        const PointGeo& g, int d, T inv_dx) {
+  T s = T(0);
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const int64_t op = nb_off(g.c[d], j, g.n[d], g.st[d]);
+    const int64_t om = nb_off(g.c[d], -j, g.n[d], g.st[d]);
+    s += T(fd_coef<R>(j)) * (ldg(w + g.i + op) * ldg(f + g.i + op) - ldg(w + g.i + om) * ldg(f + g.i + om));
+  }
+  return s * inv_dx;
+}
+
+// f(y) at the point; y points to the problem's state block, fields P apart.
+template <typename T, int SYS, int DIM, int R>
+__device__ __forceinline__ void rhs_point(const T* __restrict__ y, int64_t P, const PointGeo& g,
+                                          const T* inv_dx, T kap, T bb, T* f) {
+  if (SYS == SYS_WAVE1D) {
+    f[0] = dstencil<T, R>(y + P, g, 0, inv_dx[0]);
+    f[1] = dstencil<T, R>(y, g, 0, inv_dx[0]);
+  } else {
+    T div = T(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) div += dstencil<T, R>(y + (1 + d) * P, g, d, inv_dx[d]);
+    f[0] = -kap * div;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[1 + d] = -bb * dstencil<T, R>(y, g, d, inv_dx[d]);
+  }
+}
+
+// div u of the acoustic state at the point.
+template <typename T, int DIM, int R>
+__device__ __forceinline__ T div_point(const T* __restrict__ y, int64_t P, const PointGeo& g,
+                                       const T* inv_dx) {
+  T div = T(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) div += dstencil<T, R>(y + (1 + d) * P, g, d, inv_dx[d]);
+  return div;
+}
+
+// A^T l at the point for acoustics.
+template <typename T, int DIM, int R>
+__device__ __forceinline__ void rhs_T_point(const T* __restrict__ l, int64_t P, const PointGeo& g,
+                                            const T* inv_dx, const T* __restrict__ kappa,
+                                            const T* __restrict__ b, T* f) {
+  T s = T(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) s += dstencil_w<T, R>(l + (1 + d) * P, b, g, d, inv_dx[d]);
+  f[0] = s;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) f[1 + d] = dstencil_w<T, R>(l, kappa, g, d, inv_dx[d]);
+}
+
+}  // namespace gbs

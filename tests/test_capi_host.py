@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads, exports
+every entry point declared in include/gbs.h, rejects invalid problem
+descriptions before touching the GPU, and sizes states/workspaces correctly.
+Also cross-checks the product's scheme table against the paper's printed values
+(tests/golden/paper_schemes.txt)."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import pytest
+
+from paper_1907_11771_gb300 import binding as B
+from paper_1907_11771_gb300 import build as Bld
+from paper_1907_11771_gb300 import schemes as S
+from tests.conftest import ROOT, load_golden
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return Bld.build()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gbs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(L, s), s
+    # the binding wraps every declared entry point under the same name
+    for s in syms:
+        assert hasattr(B, s), s
+
+
+def test_invalid_problems_rejected_without_gpu(libpath):
+    B.lib()
+    bad = [
+        dict(system=3, ndim=1, fd_order=4),
+        dict(system=B.GBS_WAVE1D, ndim=2, fd_order=4),
+        dict(system=B.GBS_ACOUSTIC, ndim=2, fd_order=5),
+        dict(system=B.GBS_ACOUSTIC, ndim=4, fd_order=4),
+    ]
+    for kw in bad:
+        pb = B.make_problem(kw["system"], kw["ndim"], kw["fd_order"], B.GBS_F64, [(16, 16, 1)], [(1.0, 1.0, 1.0)])
+        with pytest.raises(B.GbsError) as e:
+            B.gbs_create(pb)
+        assert e.value.status == 1
+        assert B.gbs_state_elems(pb) == 0
+    # a grid smaller than the stencil radius, and a non-unit unused dimension
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 6, B.GBS_F64, [(2, 16, 1)], [(1.0, 1.0, 1.0)])
+    with pytest.raises(B.GbsError):
+        B.gbs_create(pb)
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F64, [(16, 16, 2)], [(1.0, 1.0, 1.0)])
+    with pytest.raises(B.GbsError):
+        B.gbs_create(pb)
+    # wave system with media is refused before any device call
+    pb = B.make_problem(B.GBS_WAVE1D, 1, 4, B.GBS_F64, [(16,)], [(1.0,)])
+    with pytest.raises(B.GbsError):
+        B.gbs_create(pb, kappa=1234, rho=5678)
+    assert "media" in B.gbs_last_error(None)
+
+
+def test_state_and_workspace_sizes(libpath):
+    B.lib()
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 6, B.GBS_F32_STATE_F64_COMBINE, [(128, 64), (32, 32)], [(1, 1), (1, 1)])
+    assert B.gbs_state_elems(pb) == 3 * (128 * 64 + 32 * 32)
+    ws = B.gbs_workspace_bytes(pb, 22)
+    E = 3 * (128 * 64 + 32 * 32)
+    assert ws >= 4 * 4 * E + 8 * E
+    pb3 = B.make_problem(B.GBS_ACOUSTIC, 3, 4, B.GBS_F64, [(8, 9, 10)], [(1, 1, 1)], enable_adjoint=True)
+    assert B.gbs_state_elems(pb3) == 4 * 8 * 9 * 10
+    assert B.gbs_workspace_bytes(pb3, 22) > B.gbs_workspace_bytes(pb3, 2)
+
+
+def test_product_scheme_table_matches_printed_values():
+    gold = load_golden("paper_schemes.txt")
+    pairs = [("gbs_8_6", S.GBS_8_6), ("gbs_8_8", S.GBS_8_8), ("gbs_12_8", S.GBS_12_8),
+             ("table1_order8", S.SQ8_TABLE1), ("table1_order12", S.SQ12_TABLE1), ("table1_order16", S.SQ16_TABLE1)]
+    for key, sc in pairs:
+        g = gold[key]
+        assert sc.order == int(g["order"])
+        assert list(sc.steps_dep) == [int(t) for t in g["dep"].split()]
+        assert list(sc.steps_free) == [int(t) for t in g.get("free", "").split()]
+        assert [Fraction(t) for t in sc.c_free_text] == [Fraction(t) for t in g.get("cfree", "").split()]
+        assert sc.evals_per_core == int(g["evals"])
+    assert S.GBS_8_6.updates_per_point == 143
+    assert S.GBS_8_8.updates_per_point == 255
+    assert S.SQ8_2468.updates_per_point == 24
