@@ -161,14 +161,17 @@ gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, 
  * grad_kappa: device double array (media layout), accumulated.  S^T r adds
  * rcv_resid[i] to field 0 at flat point index rcv_idx[i] (device arrays;
  * indices per problem 0, i.e. batch must be 1 when n_rcv > 0); n_rcv may be 0.
- * Requires enable_adjoint and GBS_ACOUSTIC. */
+ * An index outside [0, points) is skipped and latches GBS_ERR_INVALID, which
+ * gbs_sync() reports.  Requires enable_adjoint and GBS_ACOUSTIC. */
 gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out, void* lam_in,
                             double* grad_kappa, double H, const int64_t* rcv_idx, int n_rcv,
                             const void* rcv_resid);
 
 /* Receiver misfit helper: resid[i] = y_field0[rcv_idx[i]] - data[i] (device
  * arrays, state element type) and, if J is non-NULL (device double), adds
- * 0.5 * sum_i resid[i]^2 to *J with a warp-shuffle reduction. */
+ * 0.5 * sum_i resid[i]^2 to *J with a warp-shuffle reduction.  Indices are
+ * flat points of field 0 of problem 0; one outside [0, points) gets a zero
+ * residual and latches GBS_ERR_INVALID (reported by gbs_sync()). */
 gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n_rcv,
                       const void* data, void* resid, double* J);
 

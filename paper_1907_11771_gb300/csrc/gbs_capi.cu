@@ -740,6 +740,8 @@ gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out,
   a.mu1 = h->mu1;
   a.shared = h->mu_shared;
   a.max_steps = h->levels_steps;
+  a.rcv_pts = h->probs[0].pts;
+  a.err = h->d_err;
   const int n = plain_adjoint_step(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, h->stream);
   if (n < 0) return fail(h, GBS_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += n;
@@ -751,7 +753,7 @@ gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n
   if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
   if (!y || !rcv_idx || !data || n_rcv < 0) return fail(h, GBS_ERR_INVALID, "bad misfit arguments");
   if (n_rcv == 0) return GBS_OK;
-  if (misfit(h->f64, y, rcv_idx, n_rcv, data, resid, J, h->stream) < 0)
+  if (misfit(h->f64, y, rcv_idx, n_rcv, data, resid, J, h->probs[0].pts, h->d_err, h->stream) < 0)
     return fail(h, GBS_ERR_CUDA, "misfit launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += 1;
   return GBS_OK;

@@ -85,6 +85,8 @@ struct AdjPlan {
   void* mu1;
   void* shared;                // sum_k h_k mu_1^k, F x P (state type)
   int max_steps;
+  int64_t rcv_pts;             // valid receiver indices: [0, rcv_pts)
+  int* err;                    // device error flag
 };
 int plain_adjoint_step(const AdjPlan& p, const void* y_in, const void* lam_out, void* lam_in,
                        double* grad_kappa, const int64_t* rcv_idx, int n_rcv,
@@ -100,6 +102,6 @@ constexpr int kNormBlocks = 1024;
 int norms(int f64, const void* a, const void* b, int64_t n, double* partial, double* out4,
           cudaStream_t s);
 int misfit(int f64, const void* y, const int64_t* idx, int n_rcv, const void* data, void* resid,
-           double* J, cudaStream_t s);
+           double* J, int64_t n_valid, int* err, cudaStream_t s);
 
 }  // namespace gbs

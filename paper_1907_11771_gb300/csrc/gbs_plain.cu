@@ -315,10 +315,17 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_finish(const StepPlan p, co
   grad[q.media_off + L.i] += (double)sh[L.i] * (-(double)dv);
 }
 
+// Receiver injection; an index outside [0, n_pts) latches GBS_ERR_INVALID and is skipped.
 template <typename T>
-__global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid) {
+__global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid, int64_t n_pts, int* err) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) atomicAdd(lam + idx[r], resid[r]);
+  if (r >= n) return;
+  const int64_t i = idx[r];
+  if (i < 0 || i >= n_pts) {
+    atomicCAS(err, 0, (int)GBS_ERR_INVALID);
+    return;
+  }
+  atomicAdd(lam + i, resid[r]);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,7 +387,8 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
   k_adj_finish<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, shared, lam_in, grad);
   ++launches;
   if (n_rcv > 0) {
-    k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid));
+    k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid),
+                                                     a.rcv_pts, a.err);
     ++launches;
   }
   if (cudaPeekAtLastError() != cudaSuccess) return -1;

@@ -111,11 +111,18 @@ __global__ void k_norms_final(const double* partial, int nb, double* out) {
 
 template <typename T>
 __global__ void k_misfit(const T* __restrict__ y, const int64_t* __restrict__ idx, int n,
-                         const T* __restrict__ data, T* __restrict__ resid, double* J) {
+                         const T* __restrict__ data, T* __restrict__ resid, double* J, int64_t n_valid,
+                         int* err) {
   __shared__ double sh[32];
   double s = 0;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const T v = y[idx[r]] - data[r];
+    const int64_t i = idx[r];
+    if (i < 0 || i >= n_valid) {   // out-of-range receiver: latch an error, skip it
+      atomicCAS(err, 0, (int)GBS_ERR_INVALID);
+      if (resid) resid[r] = T(0);
+      continue;
+    }
+    const T v = y[i] - data[r];
     if (resid) resid[r] = v;
     s += (double)v * (double)v;
   }
@@ -159,13 +166,13 @@ int norms(int f64, const void* a, const void* b, int64_t n, double* partial, dou
 }
 
 int misfit(int f64, const void* y, const int64_t* idx, int n_rcv, const void* data, void* resid, double* J,
-           cudaStream_t s) {
+           int64_t n_valid, int* err, cudaStream_t s) {
   if (f64)
     k_misfit<double><<<1, 256, 0, s>>>(static_cast<const double*>(y), idx, n_rcv, static_cast<const double*>(data),
-                                       static_cast<double*>(resid), J);
+                                       static_cast<double*>(resid), J, n_valid, err);
   else
     k_misfit<float><<<1, 256, 0, s>>>(static_cast<const float*>(y), idx, n_rcv, static_cast<const float*>(data),
-                                      static_cast<float*>(resid), J);
+                                      static_cast<float*>(resid), J, n_valid, err);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
