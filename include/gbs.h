@@ -213,6 +213,43 @@ const char* gbs_last_error(gbs_handle h);
 /* Number of GPU kernels this handle has launched (for launch accounting). */
 int64_t gbs_kernel_launches(gbs_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Stepping without any memory allocation.  The paper has no counterpart: this
+ * is a service for callers that cannot call cudaMalloc -- e.g. an application
+ * whose GPU memory is owned entirely by its own allocator or pool, or a
+ * plug-in living inside such a process -- and therefore cannot create a
+ * handle (gbs_create allocates its workspace).
+ *
+ * gbs_step_noalloc does what gbs_create + gbs_set_weights + gbs_step do for
+ * one scheme, but keeps all of its scratch (leap-frog levels, shared first
+ * right-hand side, FP64 accumulator, 1/rho, problem tables) in one array of
+ * GBS_NOALLOC_SCRATCH_BYTES compiled into the library as a __device__
+ * variable, which every GPU that loads the library reserves until the process
+ * exits.  It calls no cudaMalloc/cudaFree and uses no heap memory.
+ *  - Arguments as in gbs_create (pb, kappa, rho; pb->enable_adjoint must be 0,
+ *    batch <= 256), gbs_set_weights (order_p .. c_free; all problems use this
+ *    scheme) and gbs_step (y_in, y_out, H, n_macro); cuda_stream is a
+ *    cudaStream_t.  The caller owns every pointer it passes.
+ *  - A problem whose scratch would exceed GBS_NOALLOC_SCRATCH_BYTES is
+ *    rejected with GBS_ERR_INVALID; the message is returned by
+ *    gbs_noalloc_last_error().
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address with cudaGetSymbolAddress; make that first call
+ *    outside any stream capture.
+ *  - All calls on a device share the one array, which keeps the previous
+ *    call's contents: calls whose GPU work overlaps (other streams or threads)
+ *    race and must be serialised by the caller.
+ *  - Asynchronous on cuda_stream, like gbs_step.
+ * ------------------------------------------------------------------------- */
+#define GBS_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa, const void* rho, int order_p,
+                            int n_dep, const int* steps_dep, int n_free, const int* steps_free,
+                            const double* c_free, const void* y_in, void* y_out, double H,
+                            int n_macro, void* cuda_stream);
+
+/* Message of the last failed gbs_step_noalloc call on this thread ("" if none). */
+const char* gbs_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,9 @@ _SIGS = {
     "gbs_destroy": (_I, [_P]),
     "gbs_last_error": (ctypes.c_char_p, [_P]),
     "gbs_kernel_launches": (_I64, [_P]),
+    "gbs_step_noalloc": (_I, [ctypes.POINTER(gbs_problem), _P, _P, _I, _I, ctypes.POINTER(_I), _I,
+                              ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P, _D, _I, _P]),
+    "gbs_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 
@@ -232,3 +235,20 @@ def gbs_last_error(h):
 
 def gbs_kernel_launches(h):
     return lib().gbs_kernel_launches(h)
+
+
+def gbs_step_noalloc(pb, kappa, rho, order, steps_dep, steps_free, c_free, y_in, y_out, H, n_macro, stream=None):
+    """Allocation-free stepping (see include/gbs.h); raises GbsError on failure."""
+    sd, sf = list(steps_dep), list(steps_free)
+    cf = _arr(_D, [float(v) for v in c_free]) if sf else None
+    st = lib().gbs_step_noalloc(ctypes.byref(pb), _ptr(kappa), _ptr(rho), int(order), len(sd), _arr(_I, sd),
+                                len(sf), _arr(_I, sf) if sf else None, cf, _ptr(y_in), _ptr(y_out), float(H),
+                                int(n_macro), _ptr(stream))
+    if st != GBS_OK:
+        msg = lib().gbs_noalloc_last_error()
+        raise GbsError(st, msg.decode() if msg else "")
+
+
+def gbs_noalloc_last_error():
+    m = lib().gbs_noalloc_last_error()
+    return m.decode() if m else ""
