@@ -15,13 +15,6 @@
 #include "gbs_dd.h"
 #include "gbs_internal.h"
 
-namespace gbs {
-int fused_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err_flag,
-                     void* scratch, int64_t scratch_bytes);
-bool fused_supported(const StepPlan& p);
-int64_t fused_scratch_bytes(const StepPlan& p);
-}  // namespace gbs
-
 using namespace gbs;
 
 namespace {
@@ -65,7 +58,9 @@ struct gbs_ctx {
   ProbDev* d_probs = nullptr;
   SlotDev* d_slots = nullptr;
   double* d_H = nullptr;
+  double* d_hk = nullptr;                 // per problem x GBS_MAX_SEQ: H / N_k
   std::vector<double> cur_H;
+  std::vector<double> hk_host;
   int* d_err = nullptr;
   double* d_red = nullptr;                // norm partials (4 * kNormBlocks) + 4 results
   double* d_cmax = nullptr;
@@ -80,8 +75,8 @@ struct gbs_ctx {
   void* mu0 = nullptr;
   void* mu1 = nullptr;
   void* mu_shared = nullptr;
-  void* fused_scratch = nullptr;
-  int64_t fused_scratch_bytes = 0;
+  FusedWork* fw = nullptr;                // time-blocked path: schedule and level store
+  bool fw_ready = false;
   // execution
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
@@ -89,6 +84,7 @@ struct gbs_ctx {
   int opt_graph = 1;
   int opt_check_stability = 0;
   int opt_time_kernels = 0;
+  int opt_hseg = 512;
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
   std::vector<double> tev_bytes;
   int tev_used = 0;
@@ -167,6 +163,8 @@ gbs_status validate_problem(const gbs_problem* pb, gbs_ctx* h) {
         return fail(h, GBS_ERR_INVALID, "problem %d: unused dim %d must have size 1", p, d);
       }
     }
+    if (pb->shape[3 * p] * pb->shape[3 * p + 1] * pb->shape[3 * p + 2] >= (int64_t(1) << 31))
+      return fail(h, GBS_ERR_INVALID, "problem %d has 2^31 or more grid points", p);
   }
   return GBS_OK;
 }
@@ -201,13 +199,15 @@ void free_graphs(gbs_ctx* h) {
 
 void free_all(gbs_ctx* h) {
   free_graphs(h);
-  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
-                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->fused_scratch};
+  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
+                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
   h->tev.clear();
+  fused_destroy(h->fw);
+  h->fw = nullptr;
 }
 
 struct Sizes {
@@ -284,6 +284,22 @@ double scan_isb(const Slot& s) {
   return ymax;
 }
 
+gbs_status prepare_fused(gbs_ctx* h);
+
+// h_k = H_p / N_k for every problem and sequence, computed once on the host so that no
+// kernel divides in FP64 (GB300's FP64 rate is low).
+gbs_status upload_hk(gbs_ctx* h) {
+  if ((int)h->cur_H.size() != h->batch) return GBS_OK;
+  h->hk_host.assign((size_t)h->batch * GBS_MAX_SEQ, 0.0);
+  for (int p = 0; p < h->batch; ++p) {
+    const Slot& s = h->slots[h->slot_of[p]];
+    for (int k = 0; k < s.m; ++k) h->hk_host[(size_t)p * GBS_MAX_SEQ + k] = h->cur_H[p] / s.steps[k];
+  }
+  CK(h, cudaMemcpyAsync(h->d_hk, h->hk_host.data(), sizeof(double) * h->hk_host.size(), cudaMemcpyHostToDevice,
+                        h->stream));
+  return GBS_OK;
+}
+
 gbs_status upload_slots(gbs_ctx* h) {
   SlotDev sd[GBS_MAX_SLOTS];
   std::memset(sd, 0, sizeof sd);
@@ -299,7 +315,9 @@ gbs_status upload_slots(gbs_ctx* h) {
   for (int p = 0; p < h->batch; ++p) h->probs[p].slot = h->slot_of[p];
   CK(h, cudaMemcpy(h->d_probs, h->probs.data(), sizeof(ProbDev) * h->batch, cudaMemcpyHostToDevice));
   ++h->sched_version;
-  return GBS_OK;
+  gbs_status st = upload_hk(h);
+  if (st != GBS_OK) return st;
+  return prepare_fused(h);
 }
 
 gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
@@ -313,6 +331,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->probs = h->d_probs;
   p->slots = h->d_slots;
   p->H = h->d_H;
+  p->hk = h->d_hk;
   p->total_blocks = h->total_blocks;
   p->state_elems = h->state_elems;
   p->kappa = h->kappa;
@@ -343,6 +362,35 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   return GBS_OK;
 }
 
+// (Re)build the time-blocked schedule when it applies (set-up time: may allocate).
+gbs_status prepare_fused(gbs_ctx* h) {
+  h->fw_ready = false;
+  if (h->opt_kernel == GBS_KERNEL_PLAIN) return GBS_OK;
+  StepPlan p;
+  if (build_plan(h, &p) != GBS_OK) {  // some slot without weights yet: nothing to prepare
+    h->err.clear();
+    return GBS_OK;
+  }
+  if (!fused_supported(p, h->probs.data())) return GBS_OK;
+  SlotDev sd[GBS_MAX_SLOTS];
+  std::memset(sd, 0, sizeof sd);
+  for (int i = 0; i < GBS_MAX_SLOTS; ++i) {
+    sd[i].m = h->slots[i].m;
+    for (int k = 0; k < h->slots[i].m; ++k) {
+      sd[i].steps[k] = h->slots[i].steps[k];
+      sd[i].c[k] = h->slots[i].c[k];
+    }
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  char msg[256] = {0};
+  const int r = fused_prepare(h->fw, p, h->probs.data(), sd, h->opt_hseg, msg, sizeof msg);
+  if (r == -2) return fail(h, GBS_ERR_NOMEM, "%s", msg);
+  if (r < 0) return fail(h, GBS_ERR_CUDA, "%s", msg);
+  h->fw_ready = true;
+  ++h->sched_version;
+  return GBS_OK;
+}
+
 gbs_status set_H(gbs_ctx* h, const double* H) {
   bool same = (int)h->cur_H.size() == h->batch;
   for (int p = 0; p < h->batch; ++p) {
@@ -353,18 +401,14 @@ gbs_status set_H(gbs_ctx* h, const double* H) {
   h->cur_H.assign(H, H + h->batch);
   // pageable source: the call returns once the values are staged, so cur_H may change afterwards
   CK(h, cudaMemcpyAsync(h->d_H, h->cur_H.data(), sizeof(double) * h->batch, cudaMemcpyHostToDevice, h->stream));
-  return GBS_OK;
+  return upload_hk(h);
 }
 
-bool use_fused(gbs_ctx* h, const StepPlan& p) {
-  if (h->opt_kernel == GBS_KERNEL_PLAIN) return false;
-  return fused_supported(p);
-}
+bool use_fused(gbs_ctx* h, const StepPlan&) { return h->opt_kernel != GBS_KERNEL_PLAIN && h->fw_ready; }
 
 // Enqueue one macro-step on stream s (no graph).  Returns launches or -1.
 int enqueue_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo, cudaStream_t s, int kernel) {
-  if (kernel == GBS_KERNEL_FUSED)
-    return fused_macro_step(p, yi, yo, s, h->d_err, h->fused_scratch, h->fused_scratch_bytes);
+  if (kernel == GBS_KERNEL_FUSED) return fused_macro_step(h->fw, p, yi, yo, s, h->d_err);
   return plain_macro_step(p, yi, yo, s);
 }
 
@@ -494,6 +538,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   if ((st = dalloc(h, &h->d_probs, sizeof(ProbDev) * h->batch)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_slots, sizeof(SlotDev) * GBS_MAX_SLOTS)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_H, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_hk, sizeof(double) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_err, 64)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_red, sizeof(double) * (4 * kNormBlocks + 4))) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_cmax, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
@@ -518,6 +563,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
     return bail(GBS_ERR_CUDA);
   }
   h->cmax.assign(h->batch, 1.0);
+  h->fw = fused_create();
   *out = h;
   if (h->system == GBS_ACOUSTIC) {
     st = gbs_set_media(h, kappa, rho);
@@ -779,13 +825,21 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
       StepPlan p;
       gbs_status st = build_plan(h, &p);
       if (st != GBS_OK) return st;
-      if (!fused_supported(p)) return fail(h, GBS_ERR_INVALID, "the fused kernel does not support this problem");
+      if (!fused_supported(p, h->probs.data()))
+        return fail(h, GBS_ERR_INVALID, "the time-blocked kernel does not support this problem");
     }
     h->opt_kernel = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "graph")) {
     h->opt_graph = value != 0;
   } else if (!std::strcmp(name, "check_stability")) {
     h->opt_check_stability = value != 0;
+  } else if (!std::strcmp(name, "hseg")) {
+    if (value < 16 || value > 65536) return fail(h, GBS_ERR_INVALID, "hseg must be in [16, 65536]");
+    h->opt_hseg = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "time_kernels")) {
     if (value && h->tev.empty()) {
       const int pairs = 8192;
@@ -809,6 +863,7 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "graph")) *value = h->opt_graph;
   else if (!std::strcmp(name, "check_stability")) *value = h->opt_check_stability;
   else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
+  else if (!std::strcmp(name, "hseg")) *value = h->opt_hseg;
   else if (!std::strcmp(name, "kernel_in_use")) {
     StepPlan p;
     gbs_status st = build_plan(h, &p);

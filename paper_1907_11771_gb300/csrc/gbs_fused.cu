@@ -1,10 +1,631 @@
-// Time-blocked FP32 macro-step kernels (not yet available: the plain path is used).
+// Time-blocked FP32 macro-step for 2D acoustics: a persistent dataflow kernel.
+//
+// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.5, Sec. 3.2) runs as
+//   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.5)
+//   2. k_passes                  all Forward-Euler / leap-frog levels of all sequences
+//   3. k_combine                 y_out = sum_k c_k y*_k, an FP64 sum of the averages
+//
+// Work items.  Sequence k has the Forward-Euler level y_1 and N_k leap-frog
+// levels y_2 .. y_(N+1).  The leap-frog levels are cut into passes of
+// T in {2, 4, 6, 8} levels (the first pass takes N mod 8, the others 8), and
+// every pass into tiles: strips of at most 128 columns times segments of rows.
+// An item (problem, k, pass, tile) reads the two levels (y_(n-1), y_n) of the
+// previous pass over its tile plus an R*T halo, advances them T levels and
+// writes (y_(n+T-1), y_(n+T)) -- or, in the sequence's last pass, the average
+// y*_k = (y_(N-1) + 2 y_N + y_(N+1)) / 4 -- for its tile.  The first pass
+// starts from (y_0, y_1 = y_0 + h f0).  Passes alternate between two buffer
+// sets, so an item never overwrites data a neighbour may still read, and an
+// item waits (bounded spin, then GBS_ERR_TIMEOUT) until the previous pass is
+// done on the 3 x 3 neighbouring tiles.  Items are dequeued from one atomic
+// counter in an order where every dependency comes first, so the kernel makes
+// progress with any grid size.
+//
+// Inside an item (one CTA, one grid column per thread) the tile is swept row
+// by row with a time skew: at sweep step s, level t computes local row
+// s - R T - R t.  Every level keeps the last 2R+1 rows of p and v of its
+// thread's column in registers (the y-stencils and the leap-frog "previous"
+// value) and publishes its newest row of p and u in a shared-memory ring of
+// 2R+1 rows, from which the neighbouring columns take their x-stencils.  One
+// __syncthreads per sweep step orders the ring traffic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
 #include "gbs_internal.h"
+#include "gbs_stencil.cuh"
 
 namespace gbs {
+namespace fused {
 
-bool fused_supported(const StepPlan&) { return false; }
-int64_t fused_scratch_bytes(const StepPlan&) { return 0; }
-int fused_macro_step(const StepPlan&, const void*, void*, cudaStream_t, int*, void*, int64_t) { return -1; }
+constexpr int kThreads = 192;      // strip width including the halo: one column per thread
+constexpr int kMaxOut = 128;       // output columns per strip
+constexpr int kTMax = 8;           // leap-frog levels per pass
+constexpr int kMaxDeps = 9;
+constexpr int kMaxPasses = GBS_MAX_STEPS / 2 + 2;
+constexpr long long kSpinLimit = 1ll << 20;   // about half a second of polling
+
+struct Item {
+  int prob, seq, pass, tile;
+};
+
+// Per (slot, sequence, pass).
+struct PassDesc {
+  int T;      // leap-frog levels in this pass
+  int first;  // level 0 is y_1 = y_0 + h f0 and level -1 is y_0
+  int last;   // writes the average y* instead of two levels
+  int pad;
+};
+
+// Strips and row segments of one problem.  Strip sx covers columns
+// [sx nx / nst, (sx+1) nx / nst) and segment sy rows [sy ny / nseg, (sy+1) ny / nseg),
+// so sizes differ by at most one; every strip and segment is at least as wide
+// as the R*T halo unless it is the only one.
+struct TileGeo {
+  int nst, nseg;
+  int pad0, pad1;
+};
+
+struct Params {
+  const Item* items;
+  const int* deps;
+  int n_items;
+  int* done;
+  int* queue;
+  int* err;
+  const ProbDev* probs;
+  const SlotDev* slots;
+  const double* hk;
+  const float* kappa;
+  const float* b;
+  const float* y0;
+  const float* f0;
+  float* lev;            // [seq][set][2][E]
+  float* ystar;          // [seq][E]
+  int64_t E;
+  const PassDesc* pdesc; // [slot][seq][pass]
+  const TileGeo* tgeo;   // per problem
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+// a mod n for -2n <= a < 3n (rows and columns never stray further from the tile)
+__device__ __forceinline__ int wrapf(int a, int n) {
+  if (a >= n) a -= n;
+  if (a >= n) a -= n;
+  if (a < 0) a += n;
+  if (a < 0) a += n;
+  return a;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// x-derivative sum over a ring row (shared memory), unscaled
+template <int R>
+__device__ __forceinline__ float dsum(const float* row, int xs) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) s += float(fd_coef<R>(j)) * (row[xs + j] - row[xs - j]);
+  return s;
+}
+
+// y-derivative sum over a register window indexed by row mod (2R+1), unscaled
+template <int R>
+__device__ __forceinline__ float dwin(const float (&w)[2 * R + 1], int c) {
+  constexpr int U = 2 * R + 1;
+  float s = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) s += float(fd_coef<R>(j)) * (w[(c + j) % U] - w[(c + U - j) % U]);
+  return s;
+}
+
+template <int R, int T>
+__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float* ring) {
+  constexpr int U = 2 * R + 1;
+  constexpr int OFF = 64 * U;  // keeps slot arithmetic non-negative
+  const int tid = threadIdx.x;
+  const ProbDev q = P.probs[it.prob];
+  const TileGeo tg = P.tgeo[it.prob];
+  const int nx = q.n[0], ny = q.n[1];
+  const int sx = it.tile % tg.nst, sy = it.tile / tg.nst;
+  const int x0 = (sx * nx) / tg.nst;
+  const int wout = ((sx + 1) * nx) / tg.nst - x0;
+  const int Y0 = (sy * ny) / tg.nseg;
+  const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
+  const int win = wout + 2 * R * T;
+  const bool active = tid < win;
+  const int x = wrapi(x0 - R * T + tid, nx);
+  const double hd = P.hk[it.prob * GBS_MAX_SEQ + it.seq];
+  const float h1 = float(hd), h2 = float(2.0 * hd);
+  const float idx = float(q.inv_dx[0]), idy = float(q.inv_dx[1]);
+  const int64_t PP = q.pts;
+  const float* kap = P.kappa + q.media_off;
+  const float* bb = P.b + q.media_off;
+  const float* inA;
+  const float* inB;
+  if (pd.first) {
+    inA = P.y0 + q.state_off;   // level -1 = y_0
+    inB = P.f0 + q.state_off;   // level 0 = y_0 + h f0
+  } else {
+    const int set_in = (it.pass - 1) & 1;
+    inA = P.lev + ((int64_t)(it.seq * 2 + set_in) * 2 + 0) * P.E + q.state_off;
+    inB = P.lev + ((int64_t)(it.seq * 2 + set_in) * 2 + 1) * P.E + q.state_off;
+  }
+  float* outA;
+  float* outB = nullptr;
+  if (pd.last) {
+    outA = P.ystar + (int64_t)it.seq * P.E + q.state_off;
+  } else {
+    const int set_out = it.pass & 1;
+    outA = P.lev + ((int64_t)(it.seq * 2 + set_out) * 2 + 0) * P.E + q.state_off;
+    outB = P.lev + ((int64_t)(it.seq * 2 + set_out) * 2 + 1) * P.E + q.state_off;
+  }
+  const bool out_col = tid >= R * T && tid < R * T + wout;
+
+  float wp[T][U], wv[T][U];
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int u = 0; u < U; ++u) wp[t][u] = wv[t][u] = 0.f;
+
+  auto RP = [&](int t, int slot) -> float* { return ring + ((t * U + slot) * 2 + 0) * kThreads; };
+  auto RU = [&](int t, int slot) -> float* { return ring + ((t * U + slot) * 2 + 1) * kThreads; };
+
+  const int S = hs + 2 * R * T;
+  for (int sb = 0; sb < S; sb += U) {
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) {
+      const int s = sb + uu;
+      if (s >= S) break;
+      // ---- level 0: local row s - R T ----
+      const int slot0 = (uu + OFF - R * T) % U;
+      if (active) {
+        const int gy = wrapf(Y0 - R * T + s, ny);
+        const int64_t e = (int64_t)gy * nx + x;
+        float p0, u0, v0;
+        if (pd.first) {
+          p0 = __ldg(inA + e) + h1 * __ldg(inB + e);
+          u0 = __ldg(inA + PP + e) + h1 * __ldg(inB + PP + e);
+          v0 = __ldg(inA + 2 * PP + e) + h1 * __ldg(inB + 2 * PP + e);
+        } else {
+          p0 = __ldcg(inB + e);
+          u0 = __ldcg(inB + PP + e);
+          v0 = __ldcg(inB + 2 * PP + e);
+        }
+        wp[0][slot0] = p0;
+        wv[0][slot0] = v0;
+        RP(0, slot0)[tid] = p0;
+        RU(0, slot0)[tid] = u0;
+      }
+      // ---- level -1 at level 1's row (s - R T - R) ----
+      float am_p = 0.f, am_u = 0.f, am_v = 0.f;
+      if (s >= 2 * R && tid >= R && tid < win - R) {
+        const int gy = wrapf(Y0 - R * T + s - R, ny);
+        const int64_t e = (int64_t)gy * nx + x;
+        if (pd.first) {
+          am_p = __ldg(inA + e);
+          am_u = __ldg(inA + PP + e);
+          am_v = __ldg(inA + 2 * PP + e);
+        } else {
+          am_p = __ldcg(inA + e);
+          am_u = __ldcg(inA + PP + e);
+          am_v = __ldcg(inA + 2 * PP + e);
+        }
+      }
+      // ---- levels 1..T ----
+#pragma unroll
+      for (int t = 1; t <= T; ++t) {
+        if (s >= 2 * t * R && tid >= R * t && tid < win - R * t) {
+          const int sl = (uu + OFF - R * T - R * t) % U;   // slot of this level's row
+          const int rho = s - R * T - R * t;                // local row
+          const int gy = wrapf(Y0 + rho, ny);
+          const int64_t em = (int64_t)gy * nx + x;
+          const float kv = __ldg(kap + em), bv = __ldg(bb + em);
+          const float dxp = dsum<R>(RP(t - 1, sl), tid) * idx;
+          const float dxu = dsum<R>(RU(t - 1, sl), tid) * idx;
+          const float dyp = dwin<R>(wp[t - 1], sl) * idy;
+          const float dyv = dwin<R>(wv[t - 1], sl) * idy;
+          float pp, pu, pv;
+          if (t == 1) {
+            pp = am_p;
+            pu = am_u;
+            pv = am_v;
+          } else {
+            pp = wp[t - 2][sl];
+            pv = wv[t - 2][sl];
+            pu = RU(t - 2, sl)[tid];
+          }
+          const float np = pp + h2 * (-kv * (dxu + dyv));
+          const float nu = pu + h2 * (-bv * dxp);
+          const float nv = pv + h2 * (-bv * dyp);
+          if (t < T) {
+            wp[t][sl] = np;
+            wv[t][sl] = nv;
+            RP(t, sl)[tid] = np;
+            RU(t, sl)[tid] = nu;
+          }
+          if (out_col && rho >= 0 && rho < hs) {
+            const int64_t e = (int64_t)(Y0 + rho) * nx + x;
+            if (!pd.last) {
+              if (t == T - 1) {
+                __stcg(outA + e, np);
+                __stcg(outA + PP + e, nu);
+                __stcg(outA + 2 * PP + e, nv);
+              }
+              if (t == T) {
+                __stcg(outB + e, np);
+                __stcg(outB + PP + e, nu);
+                __stcg(outB + 2 * PP + e, nv);
+              }
+            } else if (t == T) {
+              // y_(N-1) = prev, y_N = level T-1 at this row, y_(N+1) = new; average in FP64
+              const float cp = wp[T - 1][sl], cv = wv[T - 1][sl], cu = RU(T - 1, sl)[tid];
+              __stcg(outA + e, float(((double)pp + 2.0 * (double)cp + (double)np) * 0.25));
+              __stcg(outA + PP + e, float(((double)pu + 2.0 * (double)cu + (double)nu) * 0.25));
+              __stcg(outA + 2 * PP + e, float(((double)pv + 2.0 * (double)cv + (double)nv) * 0.25));
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads, 1) k_passes(const Params P) {
+  extern __shared__ float ring[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
+    __syncthreads();
+    const int i = s_item;
+    __syncthreads();
+    if (i >= P.n_items) return;
+    if (threadIdx.x < kMaxDeps) {
+      const int d = P.deps[i * kMaxDeps + threadIdx.x];
+      if (d >= 0) {
+        long long spins = 0;
+        while (ld_acquire(P.done + d) == 0) {
+          if (++spins > kSpinLimit) {
+            atomicCAS(P.err, 0, (int)GBS_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+    }
+    __syncthreads();
+    const Item it = P.items[i];
+    const ProbDev& q = P.probs[it.prob];
+    const PassDesc pd = P.pdesc[(q.slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
+    switch (pd.T) {
+      case 2: run_item<R, 2>(P, it, pd, ring); break;
+      case 4: run_item<R, 4>(P, it, pd, ring); break;
+      case 6: run_item<R, 6>(P, it, pd, ring); break;
+      default: run_item<R, 8>(P, it, pd, ring); break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(P.done + i, 1);
+    }
+  }
+}
+
+// y_out = sum_k c_k y*_k in FP64 (per problem, its slot's weights).
+__global__ void k_combine(const ProbDev* probs, int batch, const SlotDev* slots, const float* __restrict__ ystar,
+                          int64_t E, float* __restrict__ y_out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = batch - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].state_off <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const SlotDev& s = slots[probs[lo].slot];
+    double acc = 0.0;
+    for (int k = 0; k < s.m; ++k) acc = fma(s.c[k], (double)__ldcg(ystar + (int64_t)k * E + e), acc);
+    y_out[e] = float(acc);
+  }
+}
+
+size_t ring_bytes(int R) { return (size_t)kTMax * (2 * R + 1) * 2 * kThreads * sizeof(float); }
+
+}  // namespace fused
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+
+struct FusedWork {
+  int64_t E = 0;
+  int m_max = 0;
+  int n_items = 0;
+  int grid = 0;
+  int R = 0;
+  int hseg = 512;
+  float* lev = nullptr;
+  float* ystar = nullptr;
+  fused::Item* items = nullptr;
+  int* deps = nullptr;
+  int* done = nullptr;   // n_items flags followed by the queue counter
+  fused::PassDesc* pdesc = nullptr;
+  fused::TileGeo* tgeo = nullptr;
+  size_t lev_cap = 0, ystar_cap = 0, items_cap = 0;
+  double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
+};
+
+namespace {
+
+void free_work(FusedWork* w) {
+  void* ptrs[] = {w->lev, w->ystar, w->items, w->deps, w->done, w->pdesc, w->tgeo};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w->lev = w->ystar = nullptr;
+  w->items = nullptr;
+  w->deps = w->done = nullptr;
+  w->pdesc = nullptr;
+  w->tgeo = nullptr;
+  w->lev_cap = w->ystar_cap = w->items_cap = 0;
+}
+
+// Leap-frog levels of sequence N split into passes: first N mod 8 (if nonzero), then 8s.
+std::vector<int> pass_plan(int N) {
+  std::vector<int> v;
+  int rem = N % fused::kTMax;
+  if (rem) v.push_back(rem);
+  for (int l = rem; l < N; l += fused::kTMax) v.push_back(fused::kTMax);
+  return v;
+}
+
+fused::TileGeo tiles_of(int nx, int ny, int hseg, int halo) {
+  fused::TileGeo g;
+  std::memset(&g, 0, sizeof g);
+  g.nst = (nx + fused::kMaxOut - 1) / fused::kMaxOut;
+  g.nseg = std::max(1, std::min((ny + hseg - 1) / hseg, ny / halo));
+  return g;
+}
+
+}  // namespace
+
+bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
+  if (p.system != GBS_ACOUSTIC || p.ndim != 2 || p.f64 || (p.R != 2 && p.R != 3)) return false;
+  const int halo = p.R * fused::kTMax;
+  for (int q = 0; q < p.batch; ++q) {
+    // rows wrap at most twice around the period, and strips (>= 64 columns once there
+    // are several) always exceed the halo
+    if (probs_h[q].n[1] < halo) return false;
+    const fused::TileGeo g = tiles_of(probs_h[q].n[0], probs_h[q].n[1], 512, halo);
+    if (g.nst > 1 && probs_h[q].n[0] / g.nst < halo) return false;
+  }
+  return true;
+}
+
+FusedWork* fused_create() { return new FusedWork(); }
+
+void fused_destroy(FusedWork* w) {
+  if (!w) return;
+  free_work(w);
+  delete w;
+}
+
+template <class T>
+static int grow(T** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes) return 0;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return -1;
+  }
+  *cap = bytes;
+  return 0;
+}
+
+int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h, int hseg,
+                  char* msg, size_t msglen) {
+  using namespace fused;
+  w->E = p.state_elems;
+  w->R = p.R;
+  w->hseg = hseg;
+  w->m_max = p.max_m;
+  // pass descriptors per (slot, seq, pass)
+  std::vector<PassDesc> pdesc((size_t)GBS_MAX_SLOTS * GBS_MAX_SEQ * kMaxPasses);
+  std::memset(pdesc.data(), 0, pdesc.size() * sizeof(PassDesc));
+  for (int sl = 0; sl < GBS_MAX_SLOTS; ++sl)
+    for (int k = 0; k < slots_h[sl].m; ++k) {
+      const std::vector<int> pl = pass_plan(slots_h[sl].steps[k]);
+      for (size_t qq = 0; qq < pl.size(); ++qq) {
+        PassDesc& d = pdesc[((size_t)sl * GBS_MAX_SEQ + k) * kMaxPasses + qq];
+        d.T = pl[qq];
+        d.first = qq == 0;
+        d.last = qq + 1 == pl.size();
+      }
+    }
+  // items, ordered by remaining depth (longest chains first), then problem, sequence, tile
+  std::vector<TileGeo> tg(p.batch);
+  struct Key {
+    int depth, prob, seq, pass, tile;
+  };
+  std::vector<Key> keys;
+  for (int q = 0; q < p.batch; ++q) {
+    tg[q] = tiles_of(probs_h[q].n[0], probs_h[q].n[1], hseg, p.R * kTMax);
+    const SlotDev& s = slots_h[probs_h[q].slot];
+    for (int k = 0; k < s.m; ++k) {
+      const int np = (int)pass_plan(s.steps[k]).size();
+      for (int qq = 0; qq < np; ++qq)
+        for (int t = 0; t < tg[q].nst * tg[q].nseg; ++t) keys.push_back({np - qq, q, k, qq, t});
+    }
+  }
+  std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+    if (a.depth != b.depth) return a.depth > b.depth;
+    if (a.pass != b.pass) return a.pass < b.pass;
+    return false;
+  });
+  const int n = (int)keys.size();
+  std::vector<Item> items(n);
+  std::vector<int> index_of;  // (prob, seq, pass, tile) -> item index via map
+  // flat lookup: offsets per (prob, seq, pass)
+  std::vector<int64_t> base((size_t)p.batch * GBS_MAX_SEQ * kMaxPasses, -1);
+  {
+    int64_t off = 0;
+    for (int q = 0; q < p.batch; ++q) {
+      const SlotDev& s = slots_h[probs_h[q].slot];
+      for (int k = 0; k < s.m; ++k) {
+        const int np = (int)pass_plan(s.steps[k]).size();
+        for (int qq = 0; qq < np; ++qq) {
+          base[((size_t)q * GBS_MAX_SEQ + k) * kMaxPasses + qq] = off;
+          off += tg[q].nst * tg[q].nseg;
+        }
+      }
+    }
+    index_of.assign((size_t)off, -1);
+  }
+  for (int i = 0; i < n; ++i) {
+    items[i] = {keys[i].prob, keys[i].seq, keys[i].pass, keys[i].tile};
+    index_of[base[((size_t)keys[i].prob * GBS_MAX_SEQ + keys[i].seq) * kMaxPasses + keys[i].pass] + keys[i].tile] = i;
+  }
+  std::vector<int> deps((size_t)n * kMaxDeps, -1);
+  for (int i = 0; i < n; ++i) {
+    const Item& it = items[i];
+    if (it.pass == 0) continue;
+    const TileGeo& g = tg[it.prob];
+    const int sx = it.tile % g.nst, sy = it.tile / g.nst;
+    int nd = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int tx = ((sx + dx) % g.nst + g.nst) % g.nst, ty = ((sy + dy) % g.nseg + g.nseg) % g.nseg;
+        const int j = index_of[base[((size_t)it.prob * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass - 1] +
+                               ty * g.nst + tx];
+        bool dup = false;
+        for (int e = 0; e < nd; ++e) dup |= deps[(size_t)i * kMaxDeps + e] == j;
+        if (!dup) deps[(size_t)i * kMaxDeps + nd++] = j;
+        if (j >= i) {
+          std::snprintf(msg, msglen, "fused schedule is not topologically ordered");
+          return -1;
+        }
+      }
+  }
+  // device buffers
+  const size_t lev_bytes = (size_t)4 * p.max_m * p.state_elems * sizeof(float);
+  const size_t ys_bytes = (size_t)p.max_m * p.state_elems * sizeof(float);
+  if (grow(&w->lev, &w->lev_cap, lev_bytes) || grow(&w->ystar, &w->ystar_cap, ys_bytes)) {
+    std::snprintf(msg, msglen, "cudaMalloc of the fused level store (%zu bytes) failed", lev_bytes + ys_bytes);
+    return -2;
+  }
+  if (w->items) cudaFree(w->items);
+  if (w->deps) cudaFree(w->deps);
+  if (w->done) cudaFree(w->done);
+  if (w->pdesc) cudaFree(w->pdesc);
+  if (w->tgeo) cudaFree(w->tgeo);
+  w->items = nullptr;
+  w->deps = w->done = nullptr;
+  w->pdesc = nullptr;
+  w->tgeo = nullptr;
+  if (cudaMalloc(&w->items, sizeof(Item) * std::max(n, 1)) != cudaSuccess ||
+      cudaMalloc(&w->deps, sizeof(int) * kMaxDeps * std::max(n, 1)) != cudaSuccess ||
+      cudaMalloc(&w->done, sizeof(int) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&w->pdesc, sizeof(PassDesc) * pdesc.size()) != cudaSuccess ||
+      cudaMalloc(&w->tgeo, sizeof(TileGeo) * p.batch) != cudaSuccess) {
+    cudaGetLastError();
+    std::snprintf(msg, msglen, "cudaMalloc of the fused schedule failed");
+    return -2;
+  }
+  if (cudaMemcpy(w->items, items.data(), sizeof(Item) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(w->deps, deps.data(), sizeof(int) * deps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(w->pdesc, pdesc.data(), sizeof(PassDesc) * pdesc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(w->tgeo, tg.data(), sizeof(TileGeo) * p.batch, cudaMemcpyHostToDevice) != cudaSuccess) {
+    std::snprintf(msg, msglen, "upload of the fused schedule failed");
+    return -3;
+  }
+  w->n_items = n;
+  // algorithmic bytes per launch: every item reads its two input levels (y_0 and f0 for a
+  // first pass) and the two media over its tile once and writes two levels (one average)
+  {
+    double by = 0;
+    for (int i = 0; i < n; ++i) {
+      const Item& it = items[i];
+      const TileGeo& g = tg[it.prob];
+      const int sx = it.tile % g.nst, sy = it.tile / g.nst;
+      const int nx = probs_h[it.prob].n[0], ny = probs_h[it.prob].n[1];
+      const double pts = (double)(((sx + 1) * nx) / g.nst - (sx * nx) / g.nst) *
+                         (((sy + 1) * ny) / g.nseg - (sy * ny) / g.nseg);
+      const PassDesc& d = pdesc[((size_t)probs_h[it.prob].slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
+      by += pts * 4.0 * (2.0 * p.F + 2.0 + (d.last ? 1.0 : 2.0) * p.F);
+    }
+    w->alg_bytes = by;
+  }
+  // persistent grid: resident CTAs per SM times SMs
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = ring_bytes(p.R);
+  if (p.R == 2) {
+    cudaFuncSetAttribute(k_passes<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_passes<2>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(k_passes<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_passes<3>, kThreads, smem);
+  }
+  if (cudaGetLastError() != cudaSuccess || per_sm < 1) {
+    std::snprintf(msg, msglen, "the fused kernel cannot be resident (smem %zu bytes)", smem);
+    return -3;
+  }
+  w->grid = std::max(1, std::min(n, sms * per_sm));
+  return 0;
+}
+
+int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err) {
+  using namespace fused;
+  int launches = 0;
+  if (launch_f0(p, y_in, s) < 0) return -1;
+  ++launches;
+  if (cudaMemsetAsync(w->done, 0, sizeof(int) * (w->n_items + 1), s) != cudaSuccess) return -1;
+  Params P;
+  P.items = w->items;
+  P.deps = w->deps;
+  P.n_items = w->n_items;
+  P.done = w->done;
+  P.queue = w->done + w->n_items;
+  P.err = err;
+  P.probs = p.probs;
+  P.slots = p.slots;
+  P.hk = p.hk;
+  P.kappa = static_cast<const float*>(p.kappa);
+  P.b = static_cast<const float*>(p.b);
+  P.y0 = static_cast<const float*>(y_in);
+  P.f0 = static_cast<const float*>(p.f0);
+  P.lev = w->lev;
+  P.ystar = w->ystar;
+  P.E = w->E;
+  P.pdesc = w->pdesc;
+  P.tgeo = w->tgeo;
+  const size_t smem = ring_bytes(w->R);
+  const int u = timing_begin(p, s);
+  if (w->R == 2) k_passes<2><<<w->grid, kThreads, smem, s>>>(P);
+  else k_passes<3><<<w->grid, kThreads, smem, s>>>(P);
+  timing_end(p, u, s, w->alg_bytes);
+  ++launches;
+  k_combine<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<float*>(y_out));
+  ++launches;
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return launches;
+}
 
 }  // namespace gbs

@@ -37,6 +37,7 @@ struct StepPlan {
   const ProbDev* probs;
   const SlotDev* slots;
   const double* H;             // per problem
+  const double* hk;            // per problem x GBS_MAX_SEQ: h_k = H / N_k (host-computed)
   int64_t total_blocks;        // point-parallel blocks over the whole batch
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   const void* kappa;           // media (state element type)
@@ -76,6 +77,19 @@ constexpr int kPlainBlock = 256;
 // Enqueue one plain macro-step (y_in -> y_out) on `s`.  Returns the number of
 // kernels launched, or -1 if a launch failed (cudaGetLastError set).
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s);
+
+// f0 = f(y_in) for every problem (point-parallel); returns 1 or -1.
+int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s);
+
+// Time-blocked FP32 path for 2D acoustics (gbs_fused.cu).  FusedWork holds its
+// schedule and level store; fused_prepare (set-up time) allocates them.
+struct FusedWork;
+FusedWork* fused_create();
+void fused_destroy(FusedWork* w);
+bool fused_supported(const StepPlan& p, const ProbDev* probs_h);
+int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h, int hseg,
+                  char* msg, size_t msglen);
+int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err);
 
 // Adjoint of one macro-step with stored forward levels (plain kernels).
 struct AdjPlan {

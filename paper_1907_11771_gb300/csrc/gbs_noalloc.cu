@@ -166,6 +166,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
       d.n[k] = (int)n;
     }
     d.pts = (int64_t)d.n[0] * d.n[1] * d.n[2];
+    if (d.pts >= (int64_t(1) << 31)) return noalloc_fail(GBS_ERR_INVALID, "a problem has 2^31 or more points");
     d.slot = 0;
     d.state_off = soff;
     d.media_off = moff;
@@ -177,7 +178,8 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const size_t o_probs = 0;
   const size_t o_slot = align256(o_probs + sizeof(ProbDev) * pb->batch);
   const size_t o_H = align256(o_slot + sizeof(SlotDev));
-  const size_t o_b = align256(o_H + sizeof(double) * pb->batch);
+  const size_t o_hk = align256(o_H + sizeof(double) * pb->batch);
+  const size_t o_b = align256(o_hk + sizeof(double) * pb->batch * GBS_MAX_SEQ);
   const size_t o_f0 = align256(o_b + (pb->system == GBS_ACOUSTIC ? moff * esz : 0));
   const size_t o_L0 = align256(o_f0 + soff * esz);
   const size_t o_L1 = align256(o_L0 + soff * esz);
@@ -199,11 +201,17 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   char* sc = static_cast<char*>(base);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double Hs[256];
-  for (int p = 0; p < pb->batch; ++p) Hs[p] = H;
+  static thread_local double hk[256 * GBS_MAX_SEQ];
+  for (int p = 0; p < pb->batch; ++p) {
+    Hs[p] = H;
+    for (int k = 0; k < GBS_MAX_SEQ; ++k) hk[p * GBS_MAX_SEQ + k] = k < m ? H / slot.steps[k] : 0.0;
+  }
   // pageable sources: each copy returns once its data are staged, so the stack arrays may go
   if (cudaMemcpyAsync(sc + o_probs, probs, sizeof(ProbDev) * pb->batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(sc + o_slot, &slot, sizeof(SlotDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(sc + o_H, Hs, sizeof(double) * pb->batch, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaMemcpyAsync(sc + o_H, Hs, sizeof(double) * pb->batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(sc + o_hk, hk, sizeof(double) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: table upload failed");
   }
@@ -225,6 +233,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.probs = reinterpret_cast<const ProbDev*>(sc + o_probs);
   p.slots = reinterpret_cast<const SlotDev*>(sc + o_slot);
   p.H = reinterpret_cast<const double*>(sc + o_H);
+  p.hk = reinterpret_cast<const double*>(sc + o_hk);
   p.total_blocks = blk;
   p.state_elems = soff;
   p.kappa = kappa;

@@ -41,6 +41,8 @@ __device__ __forceinline__ Loc locate(const StepPlan& p) {
   return L;
 }
 
+// Coordinates of flat point i (problems hold fewer than 2^31 points, so 32-bit
+// unsigned division suffices).
 __device__ __forceinline__ PointGeo geo_of(const ProbDev& q, int64_t i) {
   PointGeo g;
   g.i = i;
@@ -50,10 +52,12 @@ __device__ __forceinline__ PointGeo geo_of(const ProbDev& q, int64_t i) {
   g.st[0] = 1;
   g.st[1] = q.n[0];
   g.st[2] = (int64_t)q.n[0] * q.n[1];
-  g.c[0] = (int)(i % q.n[0]);
-  const int64_t r = i / q.n[0];
-  g.c[1] = (int)(r % q.n[1]);
-  g.c[2] = (int)(r / q.n[1]);
+  const unsigned ui = (unsigned)i, nx = (unsigned)q.n[0], ny = (unsigned)q.n[1];
+  const unsigned r = ui / nx;
+  g.c[0] = (int)(ui - r * nx);
+  const unsigned z = r / ny;
+  g.c[1] = (int)(r - z * ny);
+  g.c[2] = (int)z;
   return g;
 }
 
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* _
   const SlotDev& s = p.slots[q.slot];
   if (k >= s.m) return;
   constexpr int F = n_fields<SYS, DIM>();
-  const T h = T(p.H[L.prob] / s.steps[k]);
+  const T h = T(p.hk[L.prob * GBS_MAX_SEQ + k]);
   const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
   T* L1 = static_cast<T*>(p.L1) + q.state_off;
   const T* y0 = y_in + q.state_off;
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   const int N = s.steps[k];
   if (n > N) return;
   constexpr int F = n_fields<SYS, DIM>();
-  const double hd = p.H[L.prob] / N;
+  const double hd = p.hk[L.prob * GBS_MAX_SEQ + k];
   const T h2 = T(2.0 * hd);
   T* Lb[2] = {static_cast<T*>(p.L0) + q.state_off, static_cast<T*>(p.L1) + q.state_off};
   const T* cur = Lb[n & 1];
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_fwd(const StepPlan p, const
   const int N = s.steps[k];
   if (n > N) return;
   constexpr int F = 1 + DIM;
-  const double hd = p.H[L.prob] / N;
+  const double hd = p.hk[L.prob * GBS_MAX_SEQ + k];
   const T* y0 = y_in + q.state_off;
   auto level = [&](int j) -> T* { return lev + (int64_t)j * lev_stride + q.state_off; };
   if (n == 0) {
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_rev(const StepPlan p, const
   const int j = N + 1 - jrev;
   if (j < 1) return;
   constexpr int F = 1 + DIM;
-  const double hd = p.H[L.prob] / N;
+  const double hd = p.hk[L.prob * GBS_MAX_SEQ + k];
   const double c = s.c[k];
   // M[j] lives in buffer ((N + 1 - j) & 1) == 0 ? A : B
   T* dst = (((N + 1 - j) & 1) == 0 ? mA : mB) + q.state_off;
@@ -268,9 +272,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_gather(const StepPlan p, co
   const ProbDev& q = p.probs[L.prob];
   const SlotDev& s = p.slots[q.slot];
   if (k >= s.m) return;
-  const int N = s.steps[k];
   constexpr int F = 1 + DIM;
-  const double hd = p.H[L.prob] / N;
+  const double hd = p.hk[L.prob * GBS_MAX_SEQ + k];
   // M[1]: (N + 1 - 1) = N even -> buffer A; M[2] -> buffer B
   const T* m1 = mA + q.state_off;
   const T* m2 = mB + q.state_off;
@@ -427,6 +430,33 @@ int adjoint_sys(const AdjPlan& a, const void* yi, const void* lo, void* li, doub
 }
 
 }  // namespace
+
+namespace {
+template <typename T>
+int f0_sys(const StepPlan& p, const void* yi, cudaStream_t st) {
+  const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
+  const T* y = static_cast<const T*>(yi);
+  if (p.system == GBS_WAVE1D) {
+    if (p.R == 2) k_f0<T, SYS_WAVE1D, 1, 2><<<grid, block, 0, st>>>(p, y);
+    else k_f0<T, SYS_WAVE1D, 1, 3><<<grid, block, 0, st>>>(p, y);
+  } else {
+    switch (p.ndim * 10 + p.R) {
+      case 12: k_f0<T, SYS_ACOUSTIC, 1, 2><<<grid, block, 0, st>>>(p, y); break;
+      case 13: k_f0<T, SYS_ACOUSTIC, 1, 3><<<grid, block, 0, st>>>(p, y); break;
+      case 22: k_f0<T, SYS_ACOUSTIC, 2, 2><<<grid, block, 0, st>>>(p, y); break;
+      case 23: k_f0<T, SYS_ACOUSTIC, 2, 3><<<grid, block, 0, st>>>(p, y); break;
+      case 32: k_f0<T, SYS_ACOUSTIC, 3, 2><<<grid, block, 0, st>>>(p, y); break;
+      case 33: k_f0<T, SYS_ACOUSTIC, 3, 3><<<grid, block, 0, st>>>(p, y); break;
+      default: return -1;
+    }
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+}  // namespace
+
+int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s) {
+  return p.f64 ? f0_sys<double>(p, y_in, s) : f0_sys<float>(p, y_in, s);
+}
 
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
   return p.f64 ? macro_step_sys<double>(p, y_in, y_out, s) : macro_step_sys<float>(p, y_in, y_out, s);
