@@ -53,7 +53,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,7 +70,7 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -231,6 +231,8 @@ def run_gpu(args):
     sol.set_scheme(S.GBS_8_6)
     kernel = {"auto": B.GBS_KERNEL_AUTO, "plain": B.GBS_KERNEL_PLAIN, "fused": B.GBS_KERNEL_FUSED}[args.kernel]
     sol.set_option("kernel", kernel)
+    if args.hseg:
+        sol.set_option("hseg", args.hseg)
     H = H_FRACTION * sol.stability_limit()[0]
     y = torch.tensor(y0.astype(np.float32).ravel(), device="cuda")
     upd_per_step = S.GBS_8_6.updates_per_point * n * n
@@ -333,6 +335,7 @@ def main():
     ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
     ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
     ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gbs":

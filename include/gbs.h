@@ -175,6 +175,11 @@ gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out,
 gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n_rcv,
                       const void* data, void* resid, double* J);
 
+/* Adjoint of receiver sampling: lam[field 0][rcv_idx[i]] += values[i] (device
+ * arrays; indices of problem 0, range-checked like gbs_misfit).  Used to seed
+ * the adjoint with the misfit residual of the final state. */
+gbs_status gbs_inject(gbs_handle h, void* lam, const int64_t* rcv_idx, int n_rcv, const void* values);
+
 /* Norms over a whole state buffer, accumulated in FP64 with warp-shuffle and
  * block reductions in a fixed order: out[0] = sum (a - b)^2,
  * out[1] = sum b^2, out[2] = max |a - b|, out[3] = number of non-finite

@@ -57,6 +57,7 @@ _SIGS = {
     "gbs_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _P, _I, _P]),
     "gbs_misfit": (_I, [_P, _P, _P, _I, _P, _P, _P]),
     "gbs_norms": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
+    "gbs_inject": (_I, [_P, _P, _P, _I, _P]),
     "gbs_set_option": (_I, [_P, ctypes.c_char_p, _I64]),
     "gbs_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_I64)]),
     "gbs_kernel_time": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -195,6 +196,10 @@ def gbs_adjoint_step(h, y_in, lam_out, lam_in, grad_kappa, H, rcv_idx=None, rcv_
 def gbs_misfit(h, y, rcv_idx, data, resid=None, J=None):
     n = int(rcv_idx.numel())
     _check(h, lib().gbs_misfit(h, _ptr(y), _ptr(rcv_idx), n, _ptr(data), _ptr(resid), _ptr(J)))
+
+
+def gbs_inject(h, lam, rcv_idx, values):
+    _check(h, lib().gbs_inject(h, _ptr(lam), _ptr(rcv_idx), int(rcv_idx.numel()), _ptr(values)))
 
 
 def gbs_norms(h, a, b=None):

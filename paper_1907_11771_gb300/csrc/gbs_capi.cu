@@ -59,8 +59,10 @@ struct gbs_ctx {
   SlotDev* d_slots = nullptr;
   double* d_H = nullptr;
   double* d_hk = nullptr;                 // per problem x GBS_MAX_SEQ: H / N_k
+  float2* d_hkf = nullptr;                // the same as FP32 (h_k, 2 h_k)
   std::vector<double> cur_H;
   std::vector<double> hk_host;
+  std::vector<float2> hkf_host;
   int* d_err = nullptr;
   double* d_red = nullptr;                // norm partials (4 * kNormBlocks) + 4 results
   double* d_cmax = nullptr;
@@ -84,7 +86,7 @@ struct gbs_ctx {
   int opt_graph = 1;
   int opt_check_stability = 0;
   int opt_time_kernels = 0;
-  int opt_hseg = 512;
+  int opt_hseg = 256;
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
   std::vector<double> tev_bytes;
   int tev_used = 0;
@@ -199,7 +201,7 @@ void free_graphs(gbs_ctx* h) {
 
 void free_all(gbs_ctx* h) {
   free_graphs(h);
-  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
+  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
                   h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -291,11 +293,18 @@ gbs_status prepare_fused(gbs_ctx* h);
 gbs_status upload_hk(gbs_ctx* h) {
   if ((int)h->cur_H.size() != h->batch) return GBS_OK;
   h->hk_host.assign((size_t)h->batch * GBS_MAX_SEQ, 0.0);
+  h->hkf_host.assign((size_t)h->batch * GBS_MAX_SEQ, make_float2(0.f, 0.f));
   for (int p = 0; p < h->batch; ++p) {
     const Slot& s = h->slots[h->slot_of[p]];
-    for (int k = 0; k < s.m; ++k) h->hk_host[(size_t)p * GBS_MAX_SEQ + k] = h->cur_H[p] / s.steps[k];
+    for (int k = 0; k < s.m; ++k) {
+      const double hk = h->cur_H[p] / s.steps[k];
+      h->hk_host[(size_t)p * GBS_MAX_SEQ + k] = hk;
+      h->hkf_host[(size_t)p * GBS_MAX_SEQ + k] = make_float2((float)hk, (float)(2.0 * hk));
+    }
   }
   CK(h, cudaMemcpyAsync(h->d_hk, h->hk_host.data(), sizeof(double) * h->hk_host.size(), cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaMemcpyAsync(h->d_hkf, h->hkf_host.data(), sizeof(float2) * h->hkf_host.size(), cudaMemcpyHostToDevice,
                         h->stream));
   return GBS_OK;
 }
@@ -309,6 +318,7 @@ gbs_status upload_slots(gbs_ctx* h) {
       sd[i].steps[k] = h->slots[i].steps[k];
       sd[i].c[k] = h->slots[i].c[k];
     }
+    split_weights(sd[i]);
   }
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaMemcpy(h->d_slots, sd, sizeof sd, cudaMemcpyHostToDevice));
@@ -332,6 +342,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->slots = h->d_slots;
   p->H = h->d_H;
   p->hk = h->d_hk;
+  p->hkf = h->d_hkf;
   p->total_blocks = h->total_blocks;
   p->state_elems = h->state_elems;
   p->kappa = h->kappa;
@@ -380,6 +391,7 @@ gbs_status prepare_fused(gbs_ctx* h) {
       sd[i].steps[k] = h->slots[i].steps[k];
       sd[i].c[k] = h->slots[i].c[k];
     }
+    split_weights(sd[i]);
   }
   CK(h, cudaStreamSynchronize(h->stream));
   char msg[256] = {0};
@@ -539,6 +551,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   if ((st = dalloc(h, &h->d_slots, sizeof(SlotDev) * GBS_MAX_SLOTS)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_H, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_hk, sizeof(double) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_hkf, sizeof(float2) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_err, 64)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_red, sizeof(double) * (4 * kNormBlocks + 4))) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_cmax, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
@@ -802,6 +815,15 @@ gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n
   if (misfit(h->f64, y, rcv_idx, n_rcv, data, resid, J, h->probs[0].pts, h->d_err, h->stream) < 0)
     return fail(h, GBS_ERR_CUDA, "misfit launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += 1;
+  return GBS_OK;
+}
+
+gbs_status gbs_inject(gbs_handle h, void* lam, const int64_t* rcv_idx, int n_rcv, const void* values) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!lam || n_rcv < 0 || (n_rcv > 0 && (!rcv_idx || !values))) return fail(h, GBS_ERR_INVALID, "bad inject arguments");
+  const int n = inject(h->f64, lam, rcv_idx, n_rcv, values, h->probs[0].pts, h->d_err, h->stream);
+  if (n < 0) return fail(h, GBS_ERR_CUDA, "inject launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += n;
   return GBS_OK;
 }
 

@@ -41,9 +41,8 @@
 namespace gbs {
 namespace fused {
 
-constexpr int kThreads = 192;      // strip width including the halo: one column per thread
-constexpr int kMaxOut = 128;       // output columns per strip
-constexpr int kTMax = 8;           // leap-frog levels per pass
+constexpr int kThreads = 256;      // strip width including the halo: one column per thread
+constexpr int kTMax = 4;           // leap-frog levels per pass
 constexpr int kMaxDeps = 9;
 constexpr int kMaxPasses = GBS_MAX_STEPS / 2 + 2;
 constexpr long long kSpinLimit = 1ll << 20;   // about half a second of polling
@@ -79,6 +78,7 @@ struct Params {
   const ProbDev* probs;
   const SlotDev* slots;
   const double* hk;
+  const float2* hkf;
   const float* kappa;
   const float* b;
   const float* y0;
@@ -132,10 +132,40 @@ __device__ __forceinline__ float dwin(const float (&w)[2 * R + 1], int c) {
   return s;
 }
 
+// Shared memory of one CTA: level rings of (p, u) pairs [T_MAX][UR][kRow] followed by media
+// rings of (kappa, b) pairs [M][kRow].  Rows are padded by kPad on both sides so the
+// x-stencil of every thread (including the halo columns, whose values are discarded) stays
+// inside the row.  The CTA synchronises once every kSyncEvery sweep steps, so a ring must
+// hold 2R + kSyncEvery rows of a level (readers lag up to 2R rows behind the writer) and the
+// media ring R T_MAX + kSyncEvery + 1 rows.
+constexpr int kPad = 4;
+constexpr int kRow = kThreads + 2 * kPad;
+constexpr int kSyncEvery = 2;
+
+template <int R>
+__host__ __device__ constexpr int ring_rows() { return 2 * R + kSyncEvery; }
+template <int R>
+__host__ __device__ constexpr int media_rows() { return R * kTMax + kSyncEvery + 1; }
+
+// x-derivative sums of p and u at once from a ring row of (p, u) pairs, unscaled
+template <int R>
+__device__ __forceinline__ float2 dsum2(const float2* row) {
+  float sp = 0.f, su = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const float2 a = row[j], b = row[-j];
+    sp += float(fd_coef<R>(j)) * (a.x - b.x);
+    su += float(fd_coef<R>(j)) * (a.y - b.y);
+  }
+  return make_float2(sp, su);
+}
+
 template <int R, int T>
-__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float* ring) {
-  constexpr int U = 2 * R + 1;
-  constexpr int OFF = 64 * U;  // keeps slot arithmetic non-negative
+__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float* smem) {
+  constexpr int U = 2 * R + 1;       // register window rows
+  constexpr int UR = ring_rows<R>();  // shared ring rows per level
+  constexpr int M = media_rows<R>();
+  constexpr int OFF = 64 * U;        // keeps compile-time slot arithmetic non-negative
   const int tid = threadIdx.x;
   const ProbDev q = P.probs[it.prob];
   const TileGeo tg = P.tgeo[it.prob];
@@ -145,12 +175,11 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int wout = ((sx + 1) * nx) / tg.nst - x0;
   const int Y0 = (sy * ny) / tg.nseg;
   const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
-  const int win = wout + 2 * R * T;
-  const bool active = tid < win;
   const int x = wrapi(x0 - R * T + tid, nx);
-  const double hd = P.hk[it.prob * GBS_MAX_SEQ + it.seq];
-  const float h1 = float(hd), h2 = float(2.0 * hd);
-  const float idx = float(q.inv_dx[0]), idy = float(q.inv_dx[1]);
+  const float2 hf = P.hkf[it.prob * GBS_MAX_SEQ + it.seq];
+  const float h1 = hf.x, h2 = hf.y;
+  const float h2x = h2 * float(q.inv_dx[0]), h2y = h2 * float(q.inv_dx[1]);
+  const float rxy = float(q.inv_dx[1] / q.inv_dx[0]);   // y-stencil weight relative to x
   const int64_t PP = q.pts;
   const float* kap = P.kappa + q.media_off;
   const float* bb = P.b + q.media_off;
@@ -174,6 +203,9 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
     outB = P.lev + ((int64_t)(it.seq * 2 + set_out) * 2 + 1) * P.E + q.state_off;
   }
   const bool out_col = tid >= R * T && tid < R * T + wout;
+  float2* const lvl = reinterpret_cast<float2*>(smem) + kPad + tid;               // this column
+  float2* const med = reinterpret_cast<float2*>(smem) + kTMax * UR * kRow + kPad + tid;
+  auto RING = [&](int t, int slot) -> float2* { return lvl + (t * UR + slot) * kRow; };
 
   float wp[T][U], wv[T][U];
 #pragma unroll
@@ -181,63 +213,71 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
 #pragma unroll
     for (int u = 0; u < U; ++u) wp[t][u] = wv[t][u] = 0.f;
 
-  auto RP = [&](int t, int slot) -> float* { return ring + ((t * U + slot) * 2 + 0) * kThreads; };
-  auto RU = [&](int t, int slot) -> float* { return ring + ((t * U + slot) * 2 + 1) * kThreads; };
-
+  // global loads of one sweep step, issued one step ahead
   const int S = hs + 2 * R * T;
+  int gy0 = wrapf(Y0 - R * T, ny);          // grid row of level 0 at step 0
+  int gy1 = wrapf(Y0 - R * T - R, ny);      // grid row of level -1 (level 1's row) at step 0
+  float n0p, n0u, n0v, n1p = 0.f, n1u = 0.f, n1v = 0.f, nk, nb;
+  auto fetch = [&](int s) {
+    const int64_t e0 = (int64_t)gy0 * nx + x;
+    if (pd.first) {
+      n0p = __ldg(inA + e0) + h1 * __ldg(inB + e0);
+      n0u = __ldg(inA + PP + e0) + h1 * __ldg(inB + PP + e0);
+      n0v = __ldg(inA + 2 * PP + e0) + h1 * __ldg(inB + 2 * PP + e0);
+    } else {
+      n0p = __ldcg(inB + e0);
+      n0u = __ldcg(inB + PP + e0);
+      n0v = __ldcg(inB + 2 * PP + e0);
+    }
+    nk = __ldg(kap + e0);
+    nb = __ldg(bb + e0);
+    if (s >= 2 * R) {
+      const int64_t e1 = (int64_t)gy1 * nx + x;
+      if (pd.first) {
+        n1p = __ldg(inA + e1);
+        n1u = __ldg(inA + PP + e1);
+        n1v = __ldg(inA + 2 * PP + e1);
+      } else {
+        n1p = __ldcg(inA + e1);
+        n1u = __ldcg(inA + PP + e1);
+        n1v = __ldcg(inA + 2 * PP + e1);
+      }
+    }
+  };
+  fetch(0);
+  int ms0 = 0;   // media ring slot of level 0's row
+  int rs0 = 0;   // level ring slot of level 0's row
   for (int sb = 0; sb < S; sb += U) {
 #pragma unroll
     for (int uu = 0; uu < U; ++uu) {
       const int s = sb + uu;
       if (s >= S) break;
-      // ---- level 0: local row s - R T ----
+      // ---- commit level 0 (local row s - R T), level -1, media ----
       const int slot0 = (uu + OFF - R * T) % U;
-      if (active) {
-        const int gy = wrapf(Y0 - R * T + s, ny);
-        const int64_t e = (int64_t)gy * nx + x;
-        float p0, u0, v0;
-        if (pd.first) {
-          p0 = __ldg(inA + e) + h1 * __ldg(inB + e);
-          u0 = __ldg(inA + PP + e) + h1 * __ldg(inB + PP + e);
-          v0 = __ldg(inA + 2 * PP + e) + h1 * __ldg(inB + 2 * PP + e);
-        } else {
-          p0 = __ldcg(inB + e);
-          u0 = __ldcg(inB + PP + e);
-          v0 = __ldcg(inB + 2 * PP + e);
-        }
-        wp[0][slot0] = p0;
-        wv[0][slot0] = v0;
-        RP(0, slot0)[tid] = p0;
-        RU(0, slot0)[tid] = u0;
-      }
-      // ---- level -1 at level 1's row (s - R T - R) ----
-      float am_p = 0.f, am_u = 0.f, am_v = 0.f;
-      if (s >= 2 * R && tid >= R && tid < win - R) {
-        const int gy = wrapf(Y0 - R * T + s - R, ny);
-        const int64_t e = (int64_t)gy * nx + x;
-        if (pd.first) {
-          am_p = __ldg(inA + e);
-          am_u = __ldg(inA + PP + e);
-          am_v = __ldg(inA + 2 * PP + e);
-        } else {
-          am_p = __ldcg(inA + e);
-          am_u = __ldcg(inA + PP + e);
-          am_v = __ldcg(inA + 2 * PP + e);
-        }
-      }
-      // ---- levels 1..T ----
+      const float p0 = n0p, u0 = n0u, v0 = n0v;
+      const float am_p = n1p, am_u = n1u, am_v = n1v;
+      wp[0][slot0] = p0;
+      wv[0][slot0] = v0;
+      RING(0, rs0)[0] = make_float2(p0, u0);
+      med[ms0 * kRow] = make_float2(nk, nb);
+      // ---- prefetch step s + 1 ----
+      gy0 = gy0 + 1 == ny ? 0 : gy0 + 1;
+      gy1 = gy1 + 1 == ny ? 0 : gy1 + 1;
+      if (s + 1 < S) fetch(s + 1);
+      // ---- levels 1..T: level t computes local row s - R T - R t ----
 #pragma unroll
       for (int t = 1; t <= T; ++t) {
-        if (s >= 2 * t * R && tid >= R * t && tid < win - R * t) {
-          const int sl = (uu + OFF - R * T - R * t) % U;   // slot of this level's row
-          const int rho = s - R * T - R * t;                // local row
-          const int gy = wrapf(Y0 + rho, ny);
-          const int64_t em = (int64_t)gy * nx + x;
-          const float kv = __ldg(kap + em), bv = __ldg(bb + em);
-          const float dxp = dsum<R>(RP(t - 1, sl), tid) * idx;
-          const float dxu = dsum<R>(RU(t - 1, sl), tid) * idx;
-          const float dyp = dwin<R>(wp[t - 1], sl) * idy;
-          const float dyv = dwin<R>(wv[t - 1], sl) * idy;
+        if (s >= 2 * t * R) {
+          const int sl = (uu + OFF - R * T - R * t) % U;   // register window slot of this row
+          int rs = rs0 - R * t;                             // ring slot of this row
+          if (rs < 0) rs += UR;
+          if (rs < 0) rs += UR;
+          int ms = ms0 - R * t;
+          if (ms < 0) ms += M;
+          const float2 kb = med[ms * kRow];
+          const float2 sxpu = dsum2<R>(RING(t - 1, rs));
+          const float syp = dwin<R>(wp[t - 1], sl);
+          const float syv = dwin<R>(wv[t - 1], sl);
           float pp, pu, pv;
           if (t == 1) {
             pp = am_p;
@@ -246,48 +286,46 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
           } else {
             pp = wp[t - 2][sl];
             pv = wv[t - 2][sl];
-            pu = RU(t - 2, sl)[tid];
+            pu = RING(t - 2, rs)[0].y;
           }
-          const float np = pp + h2 * (-kv * (dxu + dyv));
-          const float nu = pu + h2 * (-bv * dxp);
-          const float nv = pv + h2 * (-bv * dyp);
+          const float np = fmaf(-h2x * kb.x, fmaf(rxy, syv, sxpu.y), pp);
+          const float nu = fmaf(-h2x * kb.y, sxpu.x, pu);
+          const float nv = fmaf(-h2y * kb.y, syp, pv);
           if (t < T) {
             wp[t][sl] = np;
             wv[t][sl] = nv;
-            RP(t, sl)[tid] = np;
-            RU(t, sl)[tid] = nu;
+            RING(t, rs)[0] = make_float2(np, nu);
           }
-          if (out_col && rho >= 0 && rho < hs) {
-            const int64_t e = (int64_t)(Y0 + rho) * nx + x;
-            if (!pd.last) {
-              if (t == T - 1) {
-                __stcg(outA + e, np);
-                __stcg(outA + PP + e, nu);
-                __stcg(outA + 2 * PP + e, nv);
+          if (t >= T - 1 && (t == T || !pd.last)) {
+            const int rho = s - R * T - R * t;
+            if (out_col && rho >= 0 && rho < hs) {
+              const int64_t e = (int64_t)(Y0 + rho) * nx + x;
+              if (!pd.last) {
+                float* o = (t == T) ? outB : outA;
+                __stcg(o + e, np);
+                __stcg(o + PP + e, nu);
+                __stcg(o + 2 * PP + e, nv);
+              } else {
+                // y_(N-1) = prev, y_N = level T-1 at this row, y_(N+1) = new
+                const float cp = wp[T - 1][sl], cv = wv[T - 1][sl], cu = RING(T - 1, rs)[0].y;
+                __stcg(outA + e, gragg_avg(pp, cp, np));
+                __stcg(outA + PP + e, gragg_avg(pu, cu, nu));
+                __stcg(outA + 2 * PP + e, gragg_avg(pv, cv, nv));
               }
-              if (t == T) {
-                __stcg(outB + e, np);
-                __stcg(outB + PP + e, nu);
-                __stcg(outB + 2 * PP + e, nv);
-              }
-            } else if (t == T) {
-              // y_(N-1) = prev, y_N = level T-1 at this row, y_(N+1) = new; average in FP64
-              const float cp = wp[T - 1][sl], cv = wv[T - 1][sl], cu = RU(T - 1, sl)[tid];
-              __stcg(outA + e, float(((double)pp + 2.0 * (double)cp + (double)np) * 0.25));
-              __stcg(outA + PP + e, float(((double)pu + 2.0 * (double)cu + (double)nu) * 0.25));
-              __stcg(outA + 2 * PP + e, float(((double)pv + 2.0 * (double)cv + (double)nv) * 0.25));
             }
           }
         }
       }
-      __syncthreads();
+      ms0 = ms0 + 1 == M ? 0 : ms0 + 1;
+      rs0 = rs0 + 1 == UR ? 0 : rs0 + 1;
+      if ((s % kSyncEvery) == kSyncEvery - 1) __syncthreads();
     }
   }
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 1) k_passes(const Params P) {
-  extern __shared__ float ring[];
+__global__ void __launch_bounds__(kThreads, 2) k_passes(const Params P) {
+  extern __shared__ float smem[];
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
@@ -312,12 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_passes(const Params P) {
     const Item it = P.items[i];
     const ProbDev& q = P.probs[it.prob];
     const PassDesc pd = P.pdesc[(q.slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
-    switch (pd.T) {
-      case 2: run_item<R, 2>(P, it, pd, ring); break;
-      case 4: run_item<R, 4>(P, it, pd, ring); break;
-      case 6: run_item<R, 6>(P, it, pd, ring); break;
-      default: run_item<R, 8>(P, it, pd, ring); break;
-    }
+    if (pd.T == 2) run_item<R, 2>(P, it, pd, smem);
+    else run_item<R, 4>(P, it, pd, smem);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -326,7 +360,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_passes(const Params P) {
   }
 }
 
-// y_out = sum_k c_k y*_k in FP64 (per problem, its slot's weights).
+// y_out = sum_k c_k y*_k (per problem, its slot's weights), accumulated in FP32 pairs:
+// c_k = chi + clo, the product chi*y is split exactly by one FMA (TwoProd), clo*y is added
+// to its error, and the running sum is kept as (hi, lo) with TwoSum.  The accumulated
+// error is about 2^-48 of sum_k |c_k y*_k| -- FP64-class -- while using only FP32 units
+// (GB300 runs FP64 at a small fraction of the FP32 rate; a plain FP64 sum of 11 terms
+// per element would saturate that pipe).
 __global__ void k_combine(const ProbDev* probs, int batch, const SlotDev* slots, const float* __restrict__ ystar,
                           int64_t E, float* __restrict__ y_out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -337,13 +376,27 @@ __global__ void k_combine(const ProbDev* probs, int batch, const SlotDev* slots,
       else hi = mid - 1;
     }
     const SlotDev& s = slots[probs[lo].slot];
-    double acc = 0.0;
-    for (int k = 0; k < s.m; ++k) acc = fma(s.c[k], (double)__ldcg(ystar + (int64_t)k * E + e), acc);
-    y_out[e] = float(acc);
+    float sh = 0.f, sl = 0.f;
+    for (int k = 0; k < s.m; ++k) {
+      const float y = __ldcg(ystar + (int64_t)k * E + e);
+      // _rn intrinsics keep the compiler from contracting these into FMAs
+      const float p = __fmul_rn(s.chi[k], y);
+      const float pe = fmaf(s.clo[k], y, fmaf(s.chi[k], y, -p));   // chi*y - p exactly, plus clo*y
+      const float t = __fadd_rn(sh, p);
+      const float bv = __fsub_rn(t, sh);
+      const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+      sl = __fadd_rn(sl, __fadd_rn(te, pe));
+      sh = __fadd_rn(t, sl);
+      sl = __fsub_rn(sl, __fsub_rn(sh, t));
+    }
+    y_out[e] = sh + sl;
   }
 }
 
-size_t ring_bytes(int R) { return (size_t)kTMax * (2 * R + 1) * 2 * kThreads * sizeof(float); }
+size_t ring_bytes(int R) {
+  const int ur = 2 * R + kSyncEvery, m = R * kTMax + kSyncEvery + 1;
+  return (size_t)(kTMax * ur + m) * kRow * sizeof(float2);
+}
 
 }  // namespace fused
 
@@ -395,7 +448,8 @@ std::vector<int> pass_plan(int N) {
 fused::TileGeo tiles_of(int nx, int ny, int hseg, int halo) {
   fused::TileGeo g;
   std::memset(&g, 0, sizeof g);
-  g.nst = (nx + fused::kMaxOut - 1) / fused::kMaxOut;
+  const int wmax = fused::kThreads - 2 * halo;   // output columns a CTA can hold with its halo
+  g.nst = (nx + wmax - 1) / wmax;
   g.nseg = std::max(1, std::min((ny + hseg - 1) / hseg, ny / halo));
   return g;
 }
@@ -406,8 +460,8 @@ bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
   if (p.system != GBS_ACOUSTIC || p.ndim != 2 || p.f64 || (p.R != 2 && p.R != 3)) return false;
   const int halo = p.R * fused::kTMax;
   for (int q = 0; q < p.batch; ++q) {
-    // rows wrap at most twice around the period, and strips (>= 64 columns once there
-    // are several) always exceed the halo
+    // rows wrap at most twice around the period; several strips must each be wider than
+    // the halo
     if (probs_h[q].n[1] < halo) return false;
     const fused::TileGeo g = tiles_of(probs_h[q].n[0], probs_h[q].n[1], 512, halo);
     if (g.nst > 1 && probs_h[q].n[0] / g.nst < halo) return false;
@@ -607,6 +661,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.probs = p.probs;
   P.slots = p.slots;
   P.hk = p.hk;
+  P.hkf = p.hkf;
   P.kappa = static_cast<const float*>(p.kappa);
   P.b = static_cast<const float*>(p.b);
   P.y0 = static_cast<const float*>(y_in);

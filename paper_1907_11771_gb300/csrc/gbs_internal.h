@@ -27,7 +27,17 @@ struct SlotDev {
   int m;
   int steps[GBS_MAX_SEQ];
   double c[GBS_MAX_SEQ];
+  float chi[GBS_MAX_SEQ];   // c = chi + clo (+ O(2^-48 c)): the weights split for FP32-pair sums
+  float clo[GBS_MAX_SEQ];
 };
+
+// Fill chi/clo from c (host).
+inline void split_weights(SlotDev& s) {
+  for (int k = 0; k < GBS_MAX_SEQ; ++k) {
+    s.chi[k] = (float)s.c[k];
+    s.clo[k] = (float)(s.c[k] - (double)s.chi[k]);
+  }
+}
 
 // Everything a macro-step launcher needs (device pointers except where noted).
 struct StepPlan {
@@ -38,6 +48,7 @@ struct StepPlan {
   const SlotDev* slots;
   const double* H;             // per problem
   const double* hk;            // per problem x GBS_MAX_SEQ: h_k = H / N_k (host-computed)
+  const float2* hkf;           // the same as FP32 pairs (h_k, 2 h_k)
   int64_t total_blocks;        // point-parallel blocks over the whole batch
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   const void* kappa;           // media (state element type)
@@ -115,6 +126,8 @@ int media_cmax(int f64, const void* kappa, const void* b, const ProbDev* probs, 
 constexpr int kNormBlocks = 1024;
 int norms(int f64, const void* a, const void* b, int64_t n, double* partial, double* out4,
           cudaStream_t s);
+int inject(int f64, void* lam, const int64_t* idx, int n, const void* values, int64_t n_valid, int* err,
+           cudaStream_t s);
 int misfit(int f64, const void* y, const int64_t* idx, int n_rcv, const void* data, void* resid,
            double* J, int64_t n_valid, int* err, cudaStream_t s);
 

@@ -147,6 +147,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
     for (int i = 0; i < n_free; ++i) slot.c[n_dep + i] = c_free[i];
     for (int k = 0; k < m; ++k)
       if (!std::isfinite(slot.c[k])) return noalloc_fail(GBS_ERR_ORDER, "weights are not finite");
+    split_weights(slot);
   }
   // ---- layout inside the scratch array ----
   ProbDev probs[256];
@@ -179,7 +180,8 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const size_t o_slot = align256(o_probs + sizeof(ProbDev) * pb->batch);
   const size_t o_H = align256(o_slot + sizeof(SlotDev));
   const size_t o_hk = align256(o_H + sizeof(double) * pb->batch);
-  const size_t o_b = align256(o_hk + sizeof(double) * pb->batch * GBS_MAX_SEQ);
+  const size_t o_hkf = align256(o_hk + sizeof(double) * pb->batch * GBS_MAX_SEQ);
+  const size_t o_b = align256(o_hkf + sizeof(float2) * pb->batch * GBS_MAX_SEQ);
   const size_t o_f0 = align256(o_b + (pb->system == GBS_ACOUSTIC ? moff * esz : 0));
   const size_t o_L0 = align256(o_f0 + soff * esz);
   const size_t o_L1 = align256(o_L0 + soff * esz);
@@ -202,15 +204,21 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double Hs[256];
   static thread_local double hk[256 * GBS_MAX_SEQ];
+  static thread_local float2 hkf[256 * GBS_MAX_SEQ];
   for (int p = 0; p < pb->batch; ++p) {
     Hs[p] = H;
-    for (int k = 0; k < GBS_MAX_SEQ; ++k) hk[p * GBS_MAX_SEQ + k] = k < m ? H / slot.steps[k] : 0.0;
+    for (int k = 0; k < GBS_MAX_SEQ; ++k) {
+      hk[p * GBS_MAX_SEQ + k] = k < m ? H / slot.steps[k] : 0.0;
+      hkf[p * GBS_MAX_SEQ + k] = make_float2((float)hk[p * GBS_MAX_SEQ + k], (float)(2.0 * hk[p * GBS_MAX_SEQ + k]));
+    }
   }
   // pageable sources: each copy returns once its data are staged, so the stack arrays may go
   if (cudaMemcpyAsync(sc + o_probs, probs, sizeof(ProbDev) * pb->batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(sc + o_slot, &slot, sizeof(SlotDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(sc + o_H, Hs, sizeof(double) * pb->batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(sc + o_hk, hk, sizeof(double) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(sc + o_hkf, hkf, sizeof(float2) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
           cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: table upload failed");
@@ -234,6 +242,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.slots = reinterpret_cast<const SlotDev*>(sc + o_slot);
   p.H = reinterpret_cast<const double*>(sc + o_H);
   p.hk = reinterpret_cast<const double*>(sc + o_hk);
+  p.hkf = reinterpret_cast<const float2*>(sc + o_hkf);
   p.total_blocks = blk;
   p.state_elems = soff;
   p.kappa = kappa;

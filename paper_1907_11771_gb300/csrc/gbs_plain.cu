@@ -61,6 +61,21 @@ __device__ __forceinline__ PointGeo geo_of(const ProbDev& q, int64_t i) {
   return g;
 }
 
+// (h_k, 2 h_k) in the state type, without FP64 arithmetic on the FP32 path.
+template <typename T>
+__device__ __forceinline__ void step_sizes(const StepPlan& p, int prob, int k, T& h, T& h2) {
+  const int i = prob * GBS_MAX_SEQ + k;
+  if (sizeof(T) == 4) {
+    const float2 v = p.hkf[i];
+    h = T(v.x);
+    h2 = T(v.y);
+  } else {
+    const double d = p.hk[i];
+    h = T(d);
+    h2 = T(2.0 * d);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void load_inv_dx(const ProbDev& q, T* inv_dx) {
   inv_dx[0] = T(q.inv_dx[0]);
@@ -97,7 +112,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* _
   const SlotDev& s = p.slots[q.slot];
   if (k >= s.m) return;
   constexpr int F = n_fields<SYS, DIM>();
-  const T h = T(p.hk[L.prob * GBS_MAX_SEQ + k]);
+  T h, h2;
+  step_sizes(p, L.prob, k, h, h2);
   const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
   T* L1 = static_cast<T*>(p.L1) + q.state_off;
   const T* y0 = y_in + q.state_off;
@@ -118,8 +134,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   const int N = s.steps[k];
   if (n > N) return;
   constexpr int F = n_fields<SYS, DIM>();
-  const double hd = p.hk[L.prob * GBS_MAX_SEQ + k];
-  const T h2 = T(2.0 * hd);
+  T h, h2;
+  step_sizes(p, L.prob, k, h, h2);
   T* Lb[2] = {static_cast<T*>(p.L0) + q.state_off, static_cast<T*>(p.L1) + q.state_off};
   const T* cur = Lb[n & 1];
   const T* prev = (n == 1) ? (y_in + q.state_off) : Lb[(n + 1) & 1];
@@ -142,7 +158,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     }
     return;
   }
-  // n == N: y_(N+1), averaging y* = (y_(N-1) + 2 y_N + y_(N+1)) / 4 in FP64, combine.
+  // n == N: y_(N+1), averaging y* = (y_(N-1) + 2 y_N + y_(N+1)) / 4 in the state type,
+  // then the FP64 combine.
   const double c = s.c[k];
   const bool first = (k == 0), last = (k == s.m - 1);
   double* acc = p.acc + q.state_off;
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const T ym = prev[e];
     const T y0 = cur[e];
     const T yp = ym + h2 * f[fl];
-    const double ys = ((double)ym + 2.0 * (double)y0 + (double)yp) * 0.25;
+    const double ys = (double)gragg_avg(ym, y0, yp);
     const double a = first ? c * ys : fma(c, ys, acc[e]);
     if (last) yo[e] = T(a);
     else acc[e] = a;
@@ -460,6 +477,18 @@ int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s) {
 
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
   return p.f64 ? macro_step_sys<double>(p, y_in, y_out, s) : macro_step_sys<float>(p, y_in, y_out, s);
+}
+
+int inject(int f64, void* lam, const int64_t* idx, int n, const void* values, int64_t n_valid, int* err,
+           cudaStream_t s) {
+  if (n <= 0) return 0;
+  if (f64)
+    k_inject<double><<<(n + 127) / 128, 128, 0, s>>>(static_cast<double*>(lam), idx, n,
+                                                      static_cast<const double*>(values), n_valid, err);
+  else
+    k_inject<float><<<(n + 127) / 128, 128, 0, s>>>(static_cast<float*>(lam), idx, n,
+                                                     static_cast<const float*>(values), n_valid, err);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int plain_adjoint_step(const AdjPlan& a, const void* y_in, const void* lam_out, void* lam_in,

@@ -32,6 +32,23 @@ __host__ __device__ constexpr int n_fields() {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Gragg's average (y_(N-1) + 2 y_N + y_(N+1)) / 4 rounded once.  In FP32 the two additions
+// are carried as exact sum/error pairs (Knuth's TwoSum), so the result is the FP32 rounding of
+// the exact average without touching the (slow) FP64 pipe.
+__device__ __forceinline__ float gragg_avg(float ym, float y0, float yp) {
+  const float s = ym + yp;
+  const float bs = s - ym;
+  const float es = (ym - (s - bs)) + (yp - bs);
+  const float y2 = 2.f * y0;
+  const float t = s + y2;
+  const float bt = t - s;
+  const float et = (s - (t - bt)) + (y2 - bt);
+  return (t + (es + et)) * 0.25f;
+}
+__device__ __forceinline__ double gragg_avg(double ym, double y0, double yp) {
+  return (ym + 2.0 * y0 + yp) * 0.25;
+}
+
 // Geometry of one point inside one problem.
 struct PointGeo {
   int64_t i;        // flat point index inside the problem
@@ -47,15 +64,21 @@ __device__ __forceinline__ int64_t nb_off(int c, int j, int n, int64_t st) {
   return (int64_t)(cj - c) * st;
 }
 
-// D_d f at the point (read-only input f).
+// D_d f at the point (read-only input f).  Interior points use fixed offsets; only points
+// within R of the periodic boundary wrap.
 template <typename T, int R>
 __device__ __forceinline__ T dstencil(const T* __restrict__ f, const PointGeo& g, int d, T inv_dx) {
+  const T* p = f + g.i;
+  const int c = g.c[d], n = g.n[d];
+  const int64_t st = g.st[d];
   T s = T(0);
+  if (c >= R && c < n - R) {
 #pragma unroll
-  for (int j = 1; j <= R; ++j) {
-    const T fp = ldg(f + g.i + nb_off(g.c[d], j, g.n[d], g.st[d]));
-    const T fm = ldg(f + g.i + nb_off(g.c[d], -j, g.n[d], g.st[d]));
-    s += T(fd_coef<R>(j)) * (fp - fm);
+    for (int j = 1; j <= R; ++j) s += T(fd_coef<R>(j)) * (ldg(p + j * st) - ldg(p - j * st));
+  } else {
+#pragma unroll
+    for (int j = 1; j <= R; ++j)
+      s += T(fd_coef<R>(j)) * (ldg(p + nb_off(c, j, n, st)) - ldg(p + nb_off(c, -j, n, st)));
   }
   return s * inv_dx;
 }

@@ -41,6 +41,11 @@ class GBSSolver:
         except Exception:
             pass
 
+    def set_media(self, kappa, rho):
+        """Point the solver at new media tensors (kept alive here; b = 1/rho recomputed)."""
+        B.gbs_set_media(self.h, kappa, rho)
+        self._media = (kappa, rho)
+
     # -- scheme set-up -------------------------------------------------------
     def set_scheme(self, scheme: Scheme, slot=0):
         B.gbs_set_weights(self.h, slot, scheme.order, scheme.steps_dep, scheme.steps_free, scheme.c_free)
@@ -77,6 +82,9 @@ class GBSSolver:
 
     def misfit(self, y, rcv_idx, data, resid=None, J=None):
         B.gbs_misfit(self.h, y, rcv_idx, data, resid, J)
+
+    def inject(self, lam, rcv_idx, values):
+        B.gbs_inject(self.h, lam, rcv_idx, values)
 
     def norms(self, a, b=None):
         return B.gbs_norms(self.h, a, b)
