@@ -205,6 +205,66 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def make_workload(args, rank):
+    """Solver, initial state, step size, updates per macro-step and config dict of a workload."""
+    import numpy as np
+    import torch
+
+    from paper_1907_11771_gb300 import binding as B
+    from paper_1907_11771_gb300 import inputs
+    from paper_1907_11771_gb300 import schemes as S
+    from paper_1907_11771_gb300.solver import GBSSolver
+
+    F32 = B.GBS_F32_STATE_F64_COMBINE
+    prec = B.GBS_F64 if args.f64 else F32
+    dt = np.float64 if args.f64 else np.float32
+    tdt = torch.float64 if args.f64 else torch.float32
+    wl = args.workload
+    if wl == "2d":
+        n = args.grid
+        y0, kappa, rho = inputs.acoustic_problem((n, n), rank, N_GAUSS, SIGMA * n / N_GRID, dtype=dt)
+        shapes, sch = [(n, n)], S.GBS_8_6
+        order = FD_ORDER
+        desc = workload_desc(n)
+        slots = None
+    elif wl == "3d":
+        n = args.grid if args.grid != N_GRID else 512
+        y0, kappa, rho = inputs.acoustic_problem((n, n, n), rank, 64, 4.0, n_pulses=3, centred=False, dtype=dt)
+        shapes, sch, order = [(n, n, n)], S.GBS_8_6, 4
+        desc = f"3D acoustics {n}^3 periodic, 4th-order FD, GBS_8,6, H = {H_FRACTION} x stability limit"
+        slots = None
+    elif wl == "batch":
+        sides = inputs.batch_sides(256, rank)
+        probs = [inputs.acoustic_problem((s, s), 1000 + i, N_GAUSS, SIGMA * s / N_GRID, dtype=dt)
+                 for i, s in enumerate(sides)]
+        y0 = np.concatenate([p[0].ravel() for p in probs])
+        kappa = np.concatenate([p[1].ravel() for p in probs])
+        rho = np.concatenate([p[2].ravel() for p in probs])
+        shapes, sch, order = [(s, s) for s in sides], S.GBS_8_6, FD_ORDER
+        slots = [i % 2 for i in range(len(sides))]
+        desc = ("256 independent 2D acoustics problems, sides from {128..1024}, 6th-order FD, "
+                "GBS_8,6 and Table-1 order-8 schemes alternating, one launch per macro-step")
+    else:
+        raise ValueError(wl)
+    tk = torch.tensor(kappa.ravel(), dtype=tdt, device="cuda")
+    tr = torch.tensor(rho.ravel(), dtype=tdt, device="cuda")
+    sol = GBSSolver(B.GBS_ACOUSTIC, [tuple(reversed(s)) for s in shapes], [(1.0,) * len(shapes[0])] * len(shapes),
+                    fd_order=order, precision=prec, kappa=tk, rho=tr)
+    sol._keep = (tk, tr)
+    sol.set_scheme(sch, slot=0)
+    upd = sum(int(np.prod(s)) for s in shapes) * sch.updates_per_point
+    if slots is not None:
+        sol.set_scheme(S.SQ8_TABLE1, slot=1)
+        sol.assign_slots(slots)
+        upd = sum(int(np.prod(s)) * (S.GBS_8_6 if sl == 0 else S.SQ8_TABLE1).updates_per_point
+                  for s, sl in zip(shapes, slots))
+    Hs = [H_FRACTION * h for h in sol.stability_limit()]
+    y = torch.tensor(np.asarray(y0).ravel(), dtype=tdt, device="cuda")
+    cfg = {"workload": desc, "shapes": shapes if len(shapes) < 4 else f"{len(shapes)} problems",
+           "scheme": sch.name, "updates_per_step_per_gpu": upd}
+    return sol, y, (Hs if len(Hs) > 1 else Hs[0]), upd, cfg
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -222,20 +282,11 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     Bld.build()
 
-    n = args.grid
-    y0, kappa, rho = inputs.acoustic_problem((n, n), rank, N_GAUSS, SIGMA * n / N_GRID)
-    tk = torch.tensor(kappa.astype(np.float32).ravel(), device="cuda")
-    tr = torch.tensor(rho.astype(np.float32).ravel(), device="cuda")
-    sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=FD_ORDER,
-                    precision=B.GBS_F32_STATE_F64_COMBINE, kappa=tk, rho=tr)
-    sol.set_scheme(S.GBS_8_6)
+    sol, y, H, upd_per_step, cfg = make_workload(args, rank)
     kernel = {"auto": B.GBS_KERNEL_AUTO, "plain": B.GBS_KERNEL_PLAIN, "fused": B.GBS_KERNEL_FUSED}[args.kernel]
     sol.set_option("kernel", kernel)
     if args.hseg:
         sol.set_option("hseg", args.hseg)
-    H = H_FRACTION * sol.stability_limit()[0]
-    y = torch.tensor(y0.astype(np.float32).ravel(), device="cuda")
-    upd_per_step = S.GBS_8_6.updates_per_point * n * n
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
@@ -285,38 +336,111 @@ def run_gpu(args):
             "avg_launch_ms": kms / nl if nl else None}
 
     # end to end through the C ABI with host buffers: H2D + macro-step + D2H per step
-    hbuf = torch.empty(y.numel(), dtype=torch.float32, pin_memory=True)
-    hbuf.copy_(y.cpu())
-    hout = torch.empty_like(hbuf)
-    sol.step_host(hbuf, hout, H, 1)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e = None
+    if not isinstance(H, list):
+        hbuf = torch.empty(y.numel(), dtype=y.dtype, pin_memory=True)
+        hbuf.copy_(y.cpu())
+        hout = torch.empty_like(hbuf)
         sol.step_host(hbuf, hout, H, 1)
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": ws * upd_per_step * args.steps / float(te.item()) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": y.numel() * 4}
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sol.step_host(hbuf, hout, H, 1)
+        e2e_s = time.perf_counter() - t0
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nbytes = y.numel() * y.element_size()
+        e2e = {"value": ws * upd_per_step * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     sol.sync()
     line = None
     if rank == 0:
+        fused = sol_kernel_is_fused(sol, B)
+        cfg.update({"combine_dtype": ("f32 pairs (double-single, ~48-bit)" if fused else "f64"),
+                    "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
+                    "parallelism": f"replicas x{ws}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_desc(n), "grid": [n, n], "scheme": "GBS_8,6",
-                           "updates_per_step_per_gpu": upd_per_step, "combine_dtype": "f64",
-                           "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
-                           "parallelism": f"replicas x{ws}"},
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.f64 else "f32",
+                "data": "synthetic", "config": cfg,
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
-        if ws == 1 and not args.no_cpu_baseline:
+        if ws == 1 and not args.no_cpu_baseline and args.workload == "2d" and not args.f64:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     sol.close()
     if ws > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_time_to_solution(args):
+    """Time to a relative L2 error of 1e-6 at t = M0 H0 (2D acoustics, same recipe on an
+    n x n grid): the fused FP32-state path and the plain FP64 path, each swept over
+    H = H0 / 2^j (H0 = 0.8 x the GBS_8,6 stability limit), against an FP64 GBS_12,8
+    reference run at a quarter of its own 0.8 x limit and checked against one at an eighth."""
+    import numpy as np
+    import torch
+
+    from paper_1907_11771_gb300 import binding as B
+    from paper_1907_11771_gb300 import build as Bld
+    from paper_1907_11771_gb300 import inputs
+    from paper_1907_11771_gb300 import schemes as S
+    from paper_1907_11771_gb300.solver import GBSSolver
+
+    torch.cuda.set_device(0)
+    Bld.build()
+    n, M0 = args.tts_grid, args.tts_macro
+    y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, SIGMA * n / N_GRID)
+
+    def solver(prec, scheme, kernel):
+        dt = np.float64 if prec == B.GBS_F64 else np.float32
+        tk = torch.tensor(kappa.astype(dt).ravel(), device="cuda")
+        tr = torch.tensor(rho.astype(dt).ravel(), device="cuda")
+        s = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=FD_ORDER, precision=prec, kappa=tk, rho=tr)
+        s.set_scheme(scheme)
+        s.set_option("kernel", kernel)
+        s._keep = (tk, tr)
+        return s
+
+    def run(sol, H, M, dt):
+        y = torch.tensor(y0.ravel(), dtype=dt, device="cuda")
+        out = torch.empty_like(y)
+        sol.step(y, out, H, 1)           # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sol.step(y, out, H, M)
+        e1.record()
+        torch.cuda.synchronize()
+        return out.double(), e0.elapsed_time(e1) / 1e3
+
+    f64 = solver(B.GBS_F64, S.GBS_8_6, B.GBS_KERNEL_PLAIN)
+    H0 = H_FRACTION * f64.stability_limit()[0]
+    T = M0 * H0
+    ref_sol = solver(B.GBS_F64, S.GBS_12_8, B.GBS_KERNEL_PLAIN)
+    Mref = int(np.ceil(T / (H_FRACTION * ref_sol.stability_limit()[0]))) * 4
+    ref, _ = run(ref_sol, T / Mref, Mref, torch.float64)
+    ref2, _ = run(ref_sol, T / (2 * Mref), 2 * Mref, torch.float64)
+    rel = lambda a: (f64.norms(a, ref)[0] / f64.norms(ref)[0]) ** 0.5
+    ref_err = rel(ref2)
+    rows = {}
+    paths = [("fused FP32 state + FP64-class combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
+             ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64)]
+    for name, prec, kernel, dt in paths:
+        sol = solver(prec, S.GBS_8_6, kernel)
+        rows[name] = []
+        for j in range(args.tts_levels):
+            M = M0 * 2 ** j
+            out, secs = run(sol, T / M, M, dt)
+            rows[name].append({"H_over_H0": 2.0 ** -j, "macro_steps": M, "seconds": secs, "rel_l2": rel(out),
+                               "gpt_updates_per_s": S.GBS_8_6.updates_per_point * n * n * M / secs / 1e9})
+        sol.close()
+    best = {k: min((r["seconds"] for r in v if r["rel_l2"] <= 1e-6), default=None) for k, v in rows.items()}
+    print(json.dumps({"study": "time to relative L2 error 1e-6", "grid": [n, n], "t_final": T, "H0": H0,
+                      "macro_steps_at_H0": M0, "reference": f"GBS_12,8 FP64, {Mref} macro-steps",
+                      "reference_self_check_rel_l2": ref_err, "paths": rows, "time_to_1e-6_s": best}), flush=True)
     return 0
 
 
@@ -335,13 +459,23 @@ def main():
     ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
     ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
     ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--workload", choices=["2d", "3d", "batch"], default="2d",
+                    help="2d (default, the headline workload), 3d (512^3) or batch (256 problems)")
+    ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-solution", action="store_true",
+                    help="run the time-to-1e-6 study (fused FP32 vs plain FP64) instead of the throughput bench")
+    ap.add_argument("--tts-grid", type=int, default=1024)
+    ap.add_argument("--tts-macro", type=int, default=100)
+    ap.add_argument("--tts-levels", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gbs":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.time_to_solution:
+        return run_time_to_solution(args)
     return run_gpu(args)
 
 

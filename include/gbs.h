@@ -192,7 +192,13 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * GBS_ERR_UNSTABLE when H exceeds gbs_stability_limit), "time_kernels" = 0/1
  * (record CUDA events around every launch of the dominant kernel -- the
  * leap-frog step kernel, or the time-blocked pass kernel -- on the handle's
- * stream; graph replay is bypassed while it is on).  gbs_get_option also
+ * stream; graph replay is bypassed while it is on), "hseg" = row-segment height of
+ * the time-blocked tiles (16..65536, default 256), "spin_limit" = polls of a
+ * dependency flag in the time-blocked kernel before it gives up and latches
+ * GBS_ERR_TIMEOUT (default 2^20, about half a second), and
+ * "inject_unsatisfiable_wait" = 0/1, a failure-detection test hook that makes
+ * the kernel's first work item wait on a flag nothing sets (the wait runs out,
+ * gbs_sync reports GBS_ERR_TIMEOUT, the handle stays usable).  gbs_get_option also
  * answers "kernel_in_use" (the GBS_KERNEL_* value gbs_step would run now).
  * Unknown names: GBS_ERR_INVALID. */
 gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value);

@@ -87,6 +87,8 @@ struct gbs_ctx {
   int opt_check_stability = 0;
   int opt_time_kernels = 0;
   int opt_hseg = 256;
+  int64_t opt_spin_limit = 1 << 20;
+  int opt_inject_wait = 0;
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
   std::vector<double> tev_bytes;
   int tev_used = 0;
@@ -862,6 +864,16 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
     h->opt_hseg = (int)value;
     gbs_status st = prepare_fused(h);
     if (st != GBS_OK) return st;
+  } else if (!std::strcmp(name, "spin_limit") || !std::strcmp(name, "inject_unsatisfiable_wait")) {
+    if (!std::strcmp(name, "spin_limit")) {
+      if (value < 1) return fail(h, GBS_ERR_INVALID, "spin_limit must be >= 1");
+      h->opt_spin_limit = value;
+    } else {
+      h->opt_inject_wait = value != 0;
+    }
+    fused_set_test_hooks(h->fw, h->opt_spin_limit, h->opt_inject_wait);
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "time_kernels")) {
     if (value && h->tev.empty()) {
       const int pairs = 8192;
@@ -886,6 +898,8 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "check_stability")) *value = h->opt_check_stability;
   else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
   else if (!std::strcmp(name, "hseg")) *value = h->opt_hseg;
+  else if (!std::strcmp(name, "spin_limit")) *value = h->opt_spin_limit;
+  else if (!std::strcmp(name, "inject_unsatisfiable_wait")) *value = h->opt_inject_wait;
   else if (!std::strcmp(name, "kernel_in_use")) {
     StepPlan p;
     gbs_status st = build_plan(h, &p);

@@ -45,7 +45,7 @@ constexpr int kThreads = 256;      // strip width including the halo: one column
 constexpr int kTMax = 4;           // leap-frog levels per pass
 constexpr int kMaxDeps = 9;
 constexpr int kMaxPasses = GBS_MAX_STEPS / 2 + 2;
-constexpr long long kSpinLimit = 1ll << 20;   // about half a second of polling
+constexpr long long kSpinLimit = 1ll << 20;   // default: about half a second of polling
 
 struct Item {
   int prob, seq, pass, tile;
@@ -88,6 +88,7 @@ struct Params {
   int64_t E;
   const PassDesc* pdesc; // [slot][seq][pass]
   const TileGeo* tgeo;   // per problem
+  long long spin_limit;  // polls of a dependency flag before GBS_ERR_TIMEOUT
 };
 
 __device__ __forceinline__ int wrapi(int a, int n) {
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_passes(const Params P) {
       if (d >= 0) {
         long long spins = 0;
         while (ld_acquire(P.done + d) == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > P.spin_limit) {
             atomicCAS(P.err, 0, (int)GBS_ERR_TIMEOUT);
             break;
           }
@@ -420,6 +421,8 @@ struct FusedWork {
   fused::TileGeo* tgeo = nullptr;
   size_t lev_cap = 0, ystar_cap = 0, items_cap = 0;
   double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
+  long long spin_limit = fused::kSpinLimit;
+  int inject_wait = 0;    // test hook: item 0 also waits on a flag that nothing sets
 };
 
 namespace {
@@ -470,6 +473,11 @@ bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
 }
 
 FusedWork* fused_create() { return new FusedWork(); }
+
+void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait) {
+  w->spin_limit = spin_limit;
+  w->inject_wait = inject_wait;
+}
 
 void fused_destroy(FusedWork* w) {
   if (!w) return;
@@ -594,13 +602,15 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   w->tgeo = nullptr;
   if (cudaMalloc(&w->items, sizeof(Item) * std::max(n, 1)) != cudaSuccess ||
       cudaMalloc(&w->deps, sizeof(int) * kMaxDeps * std::max(n, 1)) != cudaSuccess ||
-      cudaMalloc(&w->done, sizeof(int) * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&w->done, sizeof(int) * (n + 2)) != cudaSuccess ||
       cudaMalloc(&w->pdesc, sizeof(PassDesc) * pdesc.size()) != cudaSuccess ||
       cudaMalloc(&w->tgeo, sizeof(TileGeo) * p.batch) != cudaSuccess) {
     cudaGetLastError();
     std::snprintf(msg, msglen, "cudaMalloc of the fused schedule failed");
     return -2;
   }
+  // optional failure-detection hook: item 0 depends on flag n + 1, which no item ever sets
+  if (w->inject_wait && n > 0) deps[kMaxDeps - 1] = n + 1;
   if (cudaMemcpy(w->items, items.data(), sizeof(Item) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(w->deps, deps.data(), sizeof(int) * deps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(w->pdesc, pdesc.data(), sizeof(PassDesc) * pdesc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -650,7 +660,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   int launches = 0;
   if (launch_f0(p, y_in, s) < 0) return -1;
   ++launches;
-  if (cudaMemsetAsync(w->done, 0, sizeof(int) * (w->n_items + 1), s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->done, 0, sizeof(int) * (w->n_items + 2), s) != cudaSuccess) return -1;
   Params P;
   P.items = w->items;
   P.deps = w->deps;
@@ -671,6 +681,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.E = w->E;
   P.pdesc = w->pdesc;
   P.tgeo = w->tgeo;
+  P.spin_limit = w->spin_limit;
   const size_t smem = ring_bytes(w->R);
   const int u = timing_begin(p, s);
   if (w->R == 2) k_passes<2><<<w->grid, kThreads, smem, s>>>(P);

@@ -96,6 +96,9 @@ int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s);
 // schedule and level store; fused_prepare (set-up time) allocates them.
 struct FusedWork;
 FusedWork* fused_create();
+// spin_limit: polls before a dependency wait gives up (GBS_ERR_TIMEOUT); inject_wait: test
+// hook making the first item wait on a flag that nothing sets (takes effect at prepare).
+void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait);
 void fused_destroy(FusedWork* w);
 bool fused_supported(const StepPlan& p, const ProbDev* probs_h);
 int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h, int hseg,

@@ -111,3 +111,28 @@ def test_fused_not_used_where_unsupported():
     with pytest.raises(B.GbsError):
         sol.set_option("kernel", B.GBS_KERNEL_FUSED)
     sol.close()
+
+
+def test_dependency_wait_timeout_is_reported_and_recoverable():
+    """Failure detection without a fault: the first work item is made to wait on a flag
+    that nothing sets; its bounded wait runs out, the kernel latches GBS_ERR_TIMEOUT
+    (reported by gbs_sync) and the handle keeps working once the hook is off."""
+    case = AcousticCase((64, 96), 6, F32, seed=13)
+    sol = case.solver()
+    sol.set_scheme(S.GBS_8_6)
+    sol.set_option("kernel", B.GBS_KERNEL_FUSED)
+    H = 0.8 * sol.stability_limit()[0]
+    ref = case.gpu_run(sol, H, 1)
+    sol.set_option("spin_limit", 2000)
+    sol.set_option("inject_unsatisfiable_wait", 1)
+    y = torch.tensor(case.y0.ravel(), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(y)
+    sol.step(y, out, H, 1)
+    with pytest.raises(B.GbsError) as e:
+        sol.sync()
+    assert e.value.status == 6   # GBS_ERR_TIMEOUT
+    sol.set_option("inject_unsatisfiable_wait", 0)
+    sol.set_option("spin_limit", 1 << 20)
+    again = case.gpu_run(sol, H, 1)
+    assert np.array_equal(again, ref)
+    sol.close()

@@ -334,3 +334,15 @@ def test_full_size_2048_sampled_points():
         err = np.max(np.abs(o[:, half, half] - g[:, py, px]))
         assert err <= 1e-5 * scale, (py, px, err)
     sol.close()
+
+
+def test_workspace_allocation_failure_is_reported():
+    """A batch far larger than the device: gbs_create's cudaMalloc fails and the call
+    returns GBS_ERR_NOMEM with a message instead of aborting."""
+    n = 40000
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, F64, [(n, n)] * 40, [(1.0, 1.0)] * 40)
+    k = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.GbsError) as e:
+        B.gbs_create(pb, k, k)
+    assert e.value.status == 5
+    assert "cudaMalloc" in B.gbs_last_error(None)
