@@ -4,7 +4,7 @@
  * Method: Ellison & Fornberg, "A parallel-in-time approach for wave-type PDEs"
  * (arXiv 1907.11771).  An ODE y' = f(y) from a method-of-lines wave system is
  * advanced over sections of length H.  Each section is one extrapolated GBS
- * macro-step (Sec. 2.1 eq. "GBS", Sec. 3.2, Sec. 3.5):
+ * macro-step (Sec. 2.1 eq. "GBS", Sec. 3.2, Sec. 3.6):
  *
  *   for every sequence k with even step count N_k and h_k = H / N_k
  *     y_1 = y_0 + h_k f(y_0)                                  Forward Euler
@@ -12,11 +12,11 @@
  *     y*_k = (y_(N_k-1) + 2 y_(N_k) + y_(N_k+1)) / 4          averaging
  *   y(t + H) = sum_k c_k y*_k                                 extrapolation
  *
- * f(y_0) is evaluated once and shared by all sequences (Sec. 3.5).  The
+ * f(y_0) is evaluated once and shared by all sequences (Sec. 3.6).  The
  * weights c satisfy the order constraints sum_k c_k h_k^(2j) = [j == 0],
  * j < p/2 (Sec. 3.2 eq. "vander"); with more sequences than constraints the
  * free weights are given and the dependent ones follow from
- * c_dep = V_dep^-1 (b - V_free c_free) (Sec. 3.6 eq. "cdep_computation").
+ * c_dep = V_dep^-1 (b - V_free c_free) (Sec. 3.7 eq. "cdep_computation").
  *
  * Conventions for every entry point
  *  - All functions return a gbs_status; none aborts, throws or prints.  The
@@ -110,7 +110,7 @@ gbs_status gbs_set_media(gbs_handle h, const void* kappa, const void* rho);
  * weights (taken as exact binary values); may be NULL when n_free == 0.
  * c_full: optional host array of all n_dep + n_free weights (dependent
  * first); when given it is validated and used as is, otherwise the dependent
- * weights are solved from Sec. 3.6 eq. "cdep_computation" in double-double
+ * weights are solved from Sec. 3.7 eq. "cdep_computation" in double-double
  * arithmetic (Bjorck-Pereyra for the dual Vandermonde system) and rounded to
  * FP64.  Either way the rounded weights must satisfy every order constraint
  * to within 64 ulp of sum_k |c_k| h_k^(2j), else GBS_ERR_ORDER.  The order

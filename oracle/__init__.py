@@ -6,7 +6,7 @@ unoptimised restatement of what the paper defines, written so that a reader
 can check it against the paper by eye:
 
 * ``weights``  -- exact rational extrapolation weights (Sec. 3.2 eq. "vander",
-  Sec. 3.6 eqs. "order_constraints"/"cdep_computation"), the stability
+  Sec. 3.7 eqs. "order_constraints"/"cdep_computation"), the stability
   polynomial R(xi) = sum_k c_k P_k(xi) (Appendix A, Appendix B) and the
   imaginary stability boundary ISB by exact root isolation (Sec. 2.2).
 * ``mol``      -- the method-of-lines right-hand sides: periodic centred

@@ -6,7 +6,7 @@ Paper passages followed:
       y_1 = y_0 + h f(y_0)                       (Forward Euler)
       y_(n+1) = y_(n-1) + 2 h f(y_n), n = 1..N   (leap-frog)
       y*_N = (y_(N-1) + 2 y_N + y_(N+1)) / 4     (averaging)
-* Sec. 3.5: the first function evaluation f(y_0) has the same argument for
+* Sec. 3.6: the first function evaluation f(y_0) has the same argument for
   every sequence and is computed once and shared.
 * Sec. 2.1 / Sec. 3.2: the extrapolated result is sum_k c_k y*_k.  The sum is
   taken in FP64 in the order the sequences are given.

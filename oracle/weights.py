@@ -2,7 +2,7 @@
 
 Everything here works in exact rational arithmetic (``fractions.Fraction``)
 and is rounded to FP64 only at the very end, as the paper asks for the
-dependent weights (Sec. 3.6: they are best computed symbolically and only then
+dependent weights (Sec. 3.7: they are best computed symbolically and only then
 converted to floating point).
 
 Paper passages followed:
@@ -12,13 +12,13 @@ Paper passages followed:
   sum_i c_i h_i^(2j) = [j == 0], j = 0..p/2-1.  The weights do not depend on
   H (row j scales by H^(2j) and its right-hand side is 0 for j > 0), so
   h_i = 1/n_i is used throughout.
-* Sec. 3.6, eqs. "order_constraints" and "cdep_computation":
+* Sec. 3.7, eqs. "order_constraints" and "cdep_computation":
   c_dep = V_dep^-1 (b - V_free c_free).
 * Sec. 2.1 eq. "GBS" applied to Dahlquist's test equation y' = lambda y
   (Appendix A, eq. "SD_ODE"): the stability polynomial P_n(xi), xi = H lambda,
   of one sequence with n steps; Appendix B: R(xi) = sum_i c_i P_i(xi).
 * Sec. 2.2: ISB is the largest y with [-iy, iy] inside {|R| <= 1}; 0 if none.
-  ISB_n divides by the function evaluations per core (Sec. 3.5: with pair
+  ISB_n divides by the function evaluations per core (Sec. 3.6: with pair
   folding and the shared first evaluation, N_max + 1).
 """
 from fractions import Fraction
@@ -27,7 +27,7 @@ import sympy
 
 
 # ---------------------------------------------------------------------------
-# Order constraints (Sec. 3.2 eq. "vander"; Sec. 3.6)
+# Order constraints (Sec. 3.2 eq. "vander"; Sec. 3.7)
 # ---------------------------------------------------------------------------
 
 def vandermonde(steps, order):
@@ -67,7 +67,7 @@ def square_weights(steps, order):
 
 
 def dependent_weights(order, steps_dep, steps_free, c_free):
-    """c_dep = V_dep^-1 (b - V_free c_free), Sec. 3.6 eq. "cdep_computation"."""
+    """c_dep = V_dep^-1 (b - V_free c_free), Sec. 3.7 eq. "cdep_computation"."""
     Vd = vandermonde(steps_dep, order)
     Vf = vandermonde(steps_free, order) if steps_free else [[] for _ in Vd]
     b = rhs_b(order)
@@ -174,8 +174,12 @@ def _abs2_minus_one(R):
     return [q[k] for k in range(0, len(q), 2)]
 
 
-def isb_exact(R, eps=None):
-    """ISB of the stability polynomial R: inf{ y > 0 : |R(iy)| > 1 }, or 0.
+def isb_exact(R, eps=None, tol=0):
+    """ISB of the stability polynomial R: inf{ y > 0 : |R(iy)|^2 > 1 + tol }, or 0.
+
+    tol = 0 is the definition of Sec. 2.2.  A small positive tol (a Fraction or a float
+    taken exactly) reports where |R| leaves the unit circle by more than rounding, which
+    is the meaningful boundary for weights that were optimised in floating point.
 
     Exact: |R(iy)|^2 - 1 is a polynomial q(s) in s = y^2 with rational
     coefficients.  Its factor s^k (q(0) = 0 because R(0) = 1) is divided out, the
@@ -186,6 +190,7 @@ def isb_exact(R, eps=None):
     relative width below ``eps`` (default 1e-18).
     """
     qs = _abs2_minus_one(R)
+    qs[0] -= Fraction(tol)
     k = 0
     while k < len(qs) and qs[k] == 0:
         k += 1
@@ -213,5 +218,5 @@ def isb_exact(R, eps=None):
 
 
 def evals_per_core(steps):
-    """N_max + 1: function evaluations per core with pair folding and a shared first RHS (Sec. 3.5)."""
+    """N_max + 1: function evaluations per core with pair folding and a shared first RHS (Sec. 3.6)."""
     return max(steps) + 1

@@ -46,7 +46,7 @@ struct gbs_ctx {
   int system = 0, ndim = 0, order = 0, R = 0, f64 = 0, batch = 0, F = 0, adjoint = 0;
   size_t esz = 4;                         // state element size
   std::vector<ProbDev> probs;
-  int64_t state_elems = 0, media_elems = 0, total_blocks = 0;
+  int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0;
   std::vector<double> cmax;               // per problem max sqrt(kappa b)
   // media
   const void* kappa = nullptr;
@@ -346,6 +346,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->hk = h->d_hk;
   p->hkf = h->d_hkf;
   p->total_blocks = h->total_blocks;
+  p->total_tiles = h->total_tiles;
   p->state_elems = h->state_elems;
   p->kappa = h->kappa;
   p->b = h->b;
@@ -538,6 +539,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   h->state_elems = soff;
   h->media_elems = moff;
   h->total_blocks = blk;
+  h->total_tiles = assign_tiles(h->probs.data(), h->batch, h->ndim);
   if (blk > 0x7fffffff) {
     delete h;
     return fail(nullptr, GBS_ERR_INVALID, "problem too large for one launch grid");
@@ -639,7 +641,7 @@ gbs_status gbs_set_weights(gbs_handle h, int slot, int order_p, int n_dep, const
       s.c[k] = c_full[k];
     }
   } else {
-    // r_j = b_j - sum_free c_i h_i^(2j), then V_dep c_dep = r (Sec. 3.6), all in dd
+    // r_j = b_j - sum_free c_i h_i^(2j), then V_dep c_dep = r (Sec. 3.7), all in dd
     const int q = n_dep;
     std::vector<dd> x(q), r(q);
     for (int i = 0; i < q; ++i) x[i] = inv_sq(steps[i]);

@@ -1,7 +1,7 @@
 // Time-blocked FP32 macro-step for 2D acoustics: a persistent dataflow kernel.
 //
-// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.5, Sec. 3.2) runs as
-//   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.5)
+// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.6, Sec. 3.2) runs as
+//   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.6)
 //   2. k_passes                  all Forward-Euler / leap-frog levels of all sequences
 //   3. k_combine                 y_out = sum_k c_k y*_k, an FP64 sum of the averages
 //

@@ -18,6 +18,8 @@ struct ProbDev {
   int64_t state_off;   // element offset of the problem's [F][nz][ny][nx] block
   int64_t media_off;   // element offset of its [nz][ny][nx] media block
   int64_t blk_begin;   // first block of this problem in a point-parallel grid
+  int64_t tblk_begin;  // first block of this problem in the x-y tiled grid
+  int tiles_x, tiles_y;  // x-y tiles per z plane (kTileX x kTileY points each)
   double inv_dx[3];
 };
 
@@ -50,6 +52,7 @@ struct StepPlan {
   const double* hk;            // per problem x GBS_MAX_SEQ: h_k = H / N_k (host-computed)
   const float2* hkf;           // the same as FP32 pairs (h_k, 2 h_k)
   int64_t total_blocks;        // point-parallel blocks over the whole batch
+  int64_t total_tiles;         // x-y tiled blocks over the whole batch (2D/3D)
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   const void* kappa;           // media (state element type)
   const void* b;               // 1 / rho
@@ -84,6 +87,22 @@ inline void timing_end(const StepPlan& p, int u, cudaStream_t s, double bytes) {
 }
 
 constexpr int kPlainBlock = 256;
+constexpr int kTileX = 32;   // tiled step kernels: 32 x 8 threads, 4 rows per thread
+constexpr int kTileRows = 4;
+constexpr int kTileY = 8 * kTileRows;
+
+// Fill the tiled-grid fields of a problem table (host); returns the total tile count.
+inline int64_t assign_tiles(ProbDev* probs, int batch, int ndim) {
+  int64_t t = 0;
+  for (int i = 0; i < batch; ++i) {
+    ProbDev& q = probs[i];
+    q.tiles_x = (q.n[0] + kTileX - 1) / kTileX;
+    q.tiles_y = ndim >= 2 ? (q.n[1] + kTileY - 1) / kTileY : 1;
+    q.tblk_begin = t;
+    t += (int64_t)q.tiles_x * q.tiles_y * q.n[2];
+  }
+  return t;
+}
 
 // Enqueue one plain macro-step (y_in -> y_out) on `s`.  Returns the number of
 // kernels launched, or -1 if a launch failed (cudaGetLastError set).

@@ -107,7 +107,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const int F = pb->system == GBS_WAVE1D ? 2 : 1 + pb->ndim;
   const int R = pb->fd_order / 2;
   const size_t esz = pb->precision == GBS_F64 ? 8 : 4;
-  // ---- scheme: dependent weights by Bjorck-Pereyra in double-double (Sec. 3.6) ----
+  // ---- scheme: dependent weights by Bjorck-Pereyra in double-double (Sec. 3.7) ----
   if (order_p < 2 || order_p % 2 || n_dep != order_p / 2 || n_free < 0 || n_dep + n_free > GBS_MAX_SEQ)
     return noalloc_fail(GBS_ERR_INVALID, "bad order or number of sequences");
   if (!steps_dep || (n_free > 0 && (!steps_free || !c_free))) return noalloc_fail(GBS_ERR_INVALID, "scheme arrays missing");
@@ -176,6 +176,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
     moff += d.pts;
     blk += (d.pts + kPlainBlock - 1) / kPlainBlock;
   }
+  const int64_t tiles = assign_tiles(probs, pb->batch, pb->ndim);
   const size_t o_probs = 0;
   const size_t o_slot = align256(o_probs + sizeof(ProbDev) * pb->batch);
   const size_t o_H = align256(o_slot + sizeof(SlotDev));
@@ -244,6 +245,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.hk = reinterpret_cast<const double*>(sc + o_hk);
   p.hkf = reinterpret_cast<const float2*>(sc + o_hkf);
   p.total_blocks = blk;
+  p.total_tiles = tiles;
   p.state_elems = soff;
   p.kappa = kappa;
   p.b = sc + o_b;

@@ -3,7 +3,7 @@
 // read-only cache.  This is the unfused path, used for FP64 and as the
 // baseline the time-blocked FP32 kernels are measured against.
 //
-// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.5, Sec. 3.2):
+// One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.6, Sec. 3.2):
 //   k_f0             f0 = f(y_in)                       shared first evaluation
 //   for each sequence index k:
 //     k_fe(k)        L1 = y_in + h_k f0                 Forward Euler
@@ -136,10 +136,11 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   constexpr int F = n_fields<SYS, DIM>();
   T h, h2;
   step_sizes(p, L.prob, k, h, h2);
-  T* Lb[2] = {static_cast<T*>(p.L0) + q.state_off, static_cast<T*>(p.L1) + q.state_off};
-  const T* cur = Lb[n & 1];
-  const T* prev = (n == 1) ? (y_in + q.state_off) : Lb[(n + 1) & 1];
-  T* dst = Lb[(n + 1) & 1];
+  T* const L0 = static_cast<T*>(p.L0) + q.state_off;
+  T* const L1 = static_cast<T*>(p.L1) + q.state_off;
+  const T* cur = (n & 1) ? L1 : L0;
+  T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
+  const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
   const PointGeo g = geo_of(q, L.i);
   T inv_dx[3];
   load_inv_dx(q, inv_dx);
@@ -174,6 +175,133 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const double a = first ? c * ys : fma(c, ys, acc[e]);
     if (last) yo[e] = T(a);
     else acc[e] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled leap-frog step for 2D/3D acoustics.  A block of 32 x 8 threads owns a
+// 32 x 32 x-y tile of one z plane (4 rows per thread).  It stages the current level's
+// p, u, v over the tile plus an R-wide periodic halo in shared memory with coalesced
+// loads, takes the x- and y-stencils from there, and the z-stencils (3D) through the
+// cache.  Same arithmetic and the same last-step averaging/combine as k_lf.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int wrap_any(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_in, T* y_out, int k, int n) {
+  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
+  __shared__ T sh[3][Hh][W + 1];
+  // problem of this block (binary search over the tiled-grid offsets)
+  int lo = 0, hi = p.batch - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.probs[mid].tblk_begin <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const ProbDev& q = p.probs[lo];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  const int tile = (int)(blk - q.tblk_begin);
+  const int tx = tile % q.tiles_x;
+  const int rest = tile / q.tiles_x;
+  const int ty = rest % q.tiles_y;
+  const int z = rest / q.tiles_y;
+  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  const int64_t P = q.pts;
+  const int64_t plane = (int64_t)z * nx * ny;
+  T h, h2;
+  step_sizes(p, lo, k, h, h2);
+  T* const L0 = static_cast<T*>(p.L0) + q.state_off;
+  T* const L1 = static_cast<T*>(p.L1) + q.state_off;
+  const T* cur = (n & 1) ? L1 : L0;
+  T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
+  const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
+  // stage p, u, v of the current level (tile + halo, periodic): rows by threadIdx.y,
+  // columns by threadIdx.x, one wrap per row and only halo columns wrapping
+  for (int r = threadIdx.y; r < Hh; r += 8) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    const T* rowp = cur + plane + (int64_t)gy * nx;
+    for (int c = threadIdx.x; c < W; c += kTileX) {
+      int gx = x0 - R + c;
+      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+      sh[0][r][c] = ldg(rowp + gx);
+      sh[1][r][c] = ldg(rowp + P + gx);
+      sh[2][r][c] = ldg(rowp + 2 * P + gx);
+    }
+  }
+  __syncthreads();
+  const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
+  const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  const int x = x0 + threadIdx.x;
+  if (x >= nx) return;
+  constexpr int F = 1 + DIM;
+  const double c = s.c[k];
+  const bool first = (k == 0), last = (k == s.m - 1);
+#pragma unroll
+  for (int i = 0; i < kTileRows; ++i) {
+    const int ly = threadIdx.y + 8 * i;
+    const int y = y0 + ly;
+    if (y >= ny) break;
+    const int r = ly + R, cc = threadIdx.x + R;
+    T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const T a = T(fd_coef<R>(j));
+      sxp += a * (sh[0][r][cc + j] - sh[0][r][cc - j]);
+      sxu += a * (sh[1][r][cc + j] - sh[1][r][cc - j]);
+      syp += a * (sh[0][r + j][cc] - sh[0][r - j][cc]);
+      syv += a * (sh[2][r + j][cc] - sh[2][r - j][cc]);
+    }
+    const int64_t pt = plane + (int64_t)y * nx + x;
+    T div = sxu * idx + syv * idy;
+    T szp = T(0);
+    if (DIM == 3) {
+      T szw = T(0);
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const int zp = z + j >= nz ? z + j - nz : z + j;
+        const int zm = z - j < 0 ? z - j + nz : z - j;
+        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
+        const T a = T(fd_coef<R>(j));
+        szp += a * (ldg(cur + pt + op) - ldg(cur + pt + om));
+        szw += a * (ldg(cur + 3 * P + pt + op) - ldg(cur + 3 * P + pt + om));
+      }
+      div += szw * idz;
+    }
+    const T kv = ldg(kap + pt), bv = ldg(bmed + pt);
+    T f[kMaxFields];
+    f[0] = -kv * div;
+    f[1] = -bv * (sxp * idx);
+    f[2] = -bv * (syp * idy);
+    if (DIM == 3) f[3] = -bv * (szp * idz);
+    if (n < N) {
+#pragma unroll
+      for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
+    } else {
+      double* acc = p.acc + q.state_off;
+      T* yo = y_out + q.state_off;
+#pragma unroll
+      for (int fl = 0; fl < F; ++fl) {
+        const int64_t e = fl * P + pt;
+        const T ym = prev[e];
+        const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
+        const T yp = ym + h2 * f[fl];
+        const double ys = (double)gragg_avg(ym, yc, yp);
+        const double a2 = first ? c * ys : fma(c, ys, acc[e]);
+        if (last) yo[e] = T(a2);
+        else acc[e] = a2;
+      }
+    }
   }
 }
 
@@ -365,7 +493,10 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
     ++launches;
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
       const int u = timing_begin(p, st);
-      k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
+      if (SYS == SYS_ACOUSTIC && DIM >= 2)
+        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+      else
+        k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
       timing_end(p, u, st, p.tev ? p.unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + n] : 0.0);
       ++launches;
     }

@@ -1,17 +1,22 @@
 """Extrapolation schemes printed in the paper, as data for gbs_set_weights.
 
 A scheme is fully specified by its dependent step counts {n_dep}, its free
-step counts {n_free} and the free weights c_free (Sec. 3.6); the library
+step counts {n_free} and the free weights c_free (Sec. 3.7); the library
 solves the dependent weights from the order constraints.  Square schemes have
 no free part (Sec. 3.2).
 
-* GBS_8_6   -- Sec. 3.7.1 (order 8, six cores, ISB_n 0.7675)
-* GBS_8_8   -- Sec. 3.7.2 (order 8, eight cores, ISB_n 0.8176); the printed
+* GBS_8_6   -- Sec. 3.8.1 (order 8, six cores, ISB_n 0.7675)
+* GBS_8_8   -- Sec. 3.8.2 (order 8, eight cores, ISB_n 0.8176); the printed
                list of free step counts is one short of its 11 weights, and all
-               even counts up to N_max = 30 are used (Sec. 3.5), so 24 is added.
-* GBS_12_8  -- Sec. 3.7.3 (order 12, eight cores, ISB_n 0.7116)
+               even counts up to N_max = 30 are used (Sec. 3.6), so 24 is added.
+* GBS_12_8  -- Sec. 3.8.3 (order 12, eight cores, ISB_n 0.7116)
 * SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1 -- Table 1 (fully determined)
 * SQ8_2468  -- classical Richardson extrapolation with N = 2, 4, 6, 8 (order 8)
+* GBS_6_6   -- order 6 on six cores (all even counts up to N_max = 22), free weights
+               optimised for the imaginary axis with paper_1907_11771_gb300.optimize (App. B)
+               and rounded to rationals with denominators below 2^16 (as Sec. 3.8 does for its
+               schemes); exact ISB 15.00302 (ISB_n 0.65231).  The paper prints no order-6
+               scheme: square order-6 schemes have ISB 0 (Sec. 2.2).
 """
 from dataclasses import dataclass
 from fractions import Fraction
@@ -40,7 +45,7 @@ class Scheme:
 
     @property
     def evals_per_core(self):
-        """N_max + 1: function evaluations per core with pair folding (Sec. 3.5)."""
+        """N_max + 1: function evaluations per core with pair folding (Sec. 3.6)."""
         return max(self.steps) + 1
 
     @property
@@ -67,4 +72,8 @@ SQ12_TABLE1 = Scheme("SQ12{2,8,12,14,16,20}", 12, (2, 8, 12, 14, 16, 20))
 SQ16_TABLE1 = Scheme("SQ16{2,8,...,22}", 16, (2, 8, 10, 12, 14, 16, 18, 22))
 SQ8_2468 = Scheme("SQ8{2,4,6,8}", 8, (2, 4, 6, 8))
 
-ALL = {s.name: s for s in (GBS_8_6, GBS_8_8, GBS_12_8, SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1, SQ8_2468)}
+GBS_6_6 = Scheme("GBS_6,6", 6, (2, 4, 6), (8, 10, 12, 14, 16, 18, 20, 22),
+                 ("269/59612", "197/13930", "1486/33929", "11883/63743", "19127/15572", "-162418/33125",
+                  "-20111/27925", "197282/38345"))
+
+ALL = {s.name: s for s in (GBS_8_6, GBS_8_8, GBS_12_8, SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1, SQ8_2468, GBS_6_6)}

@@ -27,6 +27,9 @@ def oracle_scheme(scheme):
         free = [int(t) for t in g.get("free", "").split()]
         cf = [Fraction(t) for t in g.get("cfree", "").split()]
         steps, c = OW.scheme_weights(int(g["order"]), dep, free, cf)
+    elif scheme.steps_free:  # schemes optimised here: their recorded rationals are the data
+        steps, c = OW.scheme_weights(scheme.order, list(scheme.steps_dep), list(scheme.steps_free),
+                                     [Fraction(t) for t in scheme.c_free_text])
     else:  # textbook square schemes
         steps = list(scheme.steps_dep)
         c = OW.square_weights(steps, scheme.order)
