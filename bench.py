@@ -331,7 +331,7 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "leap-frog step (k_lf)",
+            "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "tiled leap-frog step (k_lf_tiled)",
             "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
             "avg_launch_ms": kms / nl if nl else None}
 

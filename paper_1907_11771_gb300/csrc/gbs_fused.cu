@@ -41,8 +41,12 @@
 namespace gbs {
 namespace fused {
 
+#ifndef GBS_FUSED_TMAX
+#define GBS_FUSED_TMAX 4           // longest pass; 4 keeps 2 CTAs per SM
+#endif
 constexpr int kThreads = 256;      // strip width including the halo: one column per thread
-constexpr int kTMax = 4;           // leap-frog levels per pass
+constexpr int kTMax = GBS_FUSED_TMAX;  // leap-frog levels per pass (even)
+constexpr int kMinBlocks = kTMax <= 4 ? 2 : 1;
 constexpr int kMaxDeps = 9;
 constexpr int kMaxPasses = GBS_MAX_STEPS / 2 + 2;
 constexpr long long kSpinLimit = 1ll << 20;   // default: about half a second of polling
@@ -325,7 +329,7 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 2) k_passes(const Params P) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P) {
   extern __shared__ float smem[];
   __shared__ int s_item;
   for (;;) {
@@ -352,6 +356,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_passes(const Params P) {
     const ProbDev& q = P.probs[it.prob];
     const PassDesc pd = P.pdesc[(q.slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
     if (pd.T == 2) run_item<R, 2>(P, it, pd, smem);
+#if GBS_FUSED_TMAX >= 6
+    else if (pd.T == 6) run_item<R, 6>(P, it, pd, smem);
+#endif
+#if GBS_FUSED_TMAX >= 8
+    else if (pd.T == 8) run_item<R, 8>(P, it, pd, smem);
+#endif
     else run_item<R, 4>(P, it, pd, smem);
     __syncthreads();
     if (threadIdx.x == 0) {
