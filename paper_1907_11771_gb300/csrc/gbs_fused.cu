@@ -1,17 +1,18 @@
 // Time-blocked FP32 macro-step for 2D acoustics: a persistent dataflow kernel.
 //
 // One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.6, Sec. 3.2) runs as
-//   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.6)
+//   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.6); the same
+//                                kernel copies y_in next to f0 and interleaves the media
 //   2. k_passes                  all Forward-Euler / leap-frog levels of all sequences
-//   3. k_combine                 y_out = sum_k c_k y*_k, an FP64 sum of the averages
+//   3. k_combine                 y_out = sum_k c_k y*_k in compensated FP32 pairs
 //
 // Work items.  Sequence k has the Forward-Euler level y_1 and N_k leap-frog
-// levels y_2 .. y_(N+1).  The leap-frog levels are cut into passes of
-// T in {2, 4, 6, 8} levels (the first pass takes N mod 8, the others 8), and
-// every pass into tiles: strips of at most 128 columns times segments of rows.
-// An item (problem, k, pass, tile) reads the two levels (y_(n-1), y_n) of the
-// previous pass over its tile plus an R*T halo, advances them T levels and
-// writes (y_(n+T-1), y_(n+T)) -- or, in the sequence's last pass, the average
+// levels y_2 .. y_(N+1).  The leap-frog levels are cut into passes of T <= kTMax
+// levels (the first pass takes N mod kTMax), and every pass into tiles: strips of
+// at most kThreads - 2 R kTMax columns times segments of rows.  An item (problem,
+// k, pass, tile) reads the two levels (y_(n-1), y_n) of the previous pass over
+// its tile plus an R*T halo, advances them T levels and writes (y_(n+T-1),
+// y_(n+T)) -- or, in the sequence's last pass, the average
 // y*_k = (y_(N-1) + 2 y_N + y_(N+1)) / 4 -- for its tile.  The first pass
 // starts from (y_0, y_1 = y_0 + h f0).  Passes alternate between two buffer
 // sets, so an item never overwrites data a neighbour may still read, and an
@@ -22,11 +23,11 @@
 //
 // Inside an item (one CTA, one grid column per thread) the tile is swept row
 // by row with a time skew: at sweep step s, level t computes local row
-// s - R T - R t.  Every level keeps the last 2R+1 rows of p and v of its
+// s - R T - R t.  Every level keeps the last 2R+1 rows of (p, v) of its
 // thread's column in registers (the y-stencils and the leap-frog "previous"
-// value) and publishes its newest row of p and u in a shared-memory ring of
-// 2R+1 rows, from which the neighbouring columns take their x-stencils.  One
-// __syncthreads per sweep step orders the ring traffic.
+// value) and publishes its newest (p, u) row in shared memory, from which the
+// neighbouring columns take their x-stencils.  Stencil sums use packed FP32-pair
+// arithmetic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,10 +84,8 @@ struct Params {
   const SlotDev* slots;
   const double* hk;
   const float2* hkf;
-  const float* kappa;
-  const float* b;
-  const float* y0;
-  const float* f0;
+  const float2* kb;      // media as (kappa, b) pairs
+  const float* init;     // [2][E]: y_0, f0
   float* lev;            // [seq][set][2][E]
   float* ystar;          // [seq][E]
   int64_t E;
@@ -118,63 +117,73 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// x-derivative sum over a ring row (shared memory), unscaled
-template <int R>
-__device__ __forceinline__ float dsum(const float* row, int xs) {
-  float s = 0.f;
-#pragma unroll
-  for (int j = 1; j <= R; ++j) s += float(fd_coef<R>(j)) * (row[xs + j] - row[xs - j]);
-  return s;
-}
-
-// y-derivative sum over a register window indexed by row mod (2R+1), unscaled
-template <int R>
-__device__ __forceinline__ float dwin(const float (&w)[2 * R + 1], int c) {
-  constexpr int U = 2 * R + 1;
-  float s = 0.f;
-#pragma unroll
-  for (int j = 1; j <= R; ++j) s += float(fd_coef<R>(j)) * (w[(c + j) % U] - w[(c + U - j) % U]);
-  return s;
-}
-
-// Shared memory of one CTA: level rings of (p, u) pairs [T_MAX][UR][kRow] followed by media
-// rings of (kappa, b) pairs [M][kRow].  Rows are padded by kPad on both sides so the
-// x-stencil of every thread (including the halo columns, whose values are discarded) stays
-// inside the row.  The CTA synchronises once every kSyncEvery sweep steps, so a ring must
-// hold 2R + kSyncEvery rows of a level (readers lag up to 2R rows behind the writer) and the
-// media ring R T_MAX + kSyncEvery + 1 rows.
+// Shared memory of one CTA (float2 words):
+//   level planes  [kTMax][U][kRow]        (p, u) of the newest U = 2R + 1 rows of levels 0..T-1,
+//                                          rows padded by kPad so every x-stencil stays inside
+//   media planes  [(kTMax+1)/2][U][kThreads]  the scaled media (-2h kappa/dx, -2h b/dx) of the
+//                                          rows being worked on; plane g serves levels 2g+1, 2g+2
+// A row's slot is its local row index mod U, a compile-time constant in a sweep unrolled by U,
+// so no ring index is computed at run time.  A level-t row is read by the x-stencils of level
+// t+1 R steps after it is written and by its own thread (the leap-frog "previous" u) 2R steps
+// after; it is overwritten U = 2R+1 steps after.  A barrier at least every R steps therefore
+// orders both the read after the write and the overwrite after the read.  Media are only read
+// by their own thread, so they need no barrier: level 2g copies the media of its row into
+// plane g, where levels 2g+1 and 2g+2 find them R and 2R steps later (the media of a row are
+// needed R T steps after they are loaded, longer than one plane keeps a row).
 constexpr int kPad = 4;
 constexpr int kRow = kThreads + 2 * kPad;
-constexpr int kSyncEvery = 2;
+
+__host__ __device__ constexpr int media_planes() { return (kTMax + 1) / 2; }
+
+// finite-difference weights c_1..c_R as (c, c) pairs for the packed sums (orders 4 and 6)
+__constant__ float2 c_fd4[2] = {{2.f / 3.f, 2.f / 3.f}, {-1.f / 12.f, -1.f / 12.f}};
+__constant__ float2 c_fd6[3] = {{0.75f, 0.75f}, {-0.15f, -0.15f}, {1.f / 60.f, 1.f / 60.f}};
 
 template <int R>
-__host__ __device__ constexpr int ring_rows() { return 2 * R + kSyncEvery; }
-template <int R>
-__host__ __device__ constexpr int media_rows() { return R * kTMax + kSyncEvery + 1; }
+__device__ __forceinline__ float2 fdc(int j) { return R == 2 ? c_fd4[j - 1] : c_fd6[j - 1]; }
 
-// x-derivative sums of p and u at once from a ring row of (p, u) pairs, unscaled
+// packed FP32 pairs (Blackwell f32x2 instructions): a - b, c * d + e, c * d
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// x-derivative sums of (p, u) over a level-plane row, unscaled: sum_j c_j (row[+j] - row[-j]),
+// the difference taken first (exact for smooth fields) and weighted in pairs
 template <int R>
-__device__ __forceinline__ float2 dsum2(const float2* row) {
-  float sp = 0.f, su = 0.f;
+__device__ __forceinline__ float2 xsum2(const float2* row) {
+  float2 acc = __fmul2_rn(fdc<R>(1), f2sub(row[1], row[-1]));
 #pragma unroll
-  for (int j = 1; j <= R; ++j) {
-    const float2 a = row[j], b = row[-j];
-    sp += float(fd_coef<R>(j)) * (a.x - b.x);
-    su += float(fd_coef<R>(j)) * (a.y - b.y);
-  }
-  return make_float2(sp, su);
+  for (int j = 2; j <= R; ++j) acc = __ffma2_rn(fdc<R>(j), f2sub(row[j], row[-j]), acc);
+  return acc;
+}
+
+// y-derivative sums of (p, v) over a register window indexed by row mod U, unscaled
+template <int R>
+__device__ __forceinline__ float2 ysum2(const float2 (&w)[2 * R + 1], int r) {
+  constexpr int U = 2 * R + 1;
+  float2 acc = __fmul2_rn(fdc<R>(1), f2sub(w[(r + 1) % U], w[(r + U - 1) % U]));
+#pragma unroll
+  for (int j = 2; j <= R; ++j) acc = __ffma2_rn(fdc<R>(j), f2sub(w[(r + j) % U], w[(r + U - j) % U]), acc);
+  return acc;
 }
 
 template <int R, int T>
-__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float* smem) {
-  constexpr int U = 2 * R + 1;       // register window rows
-  constexpr int UR = ring_rows<R>();  // shared ring rows per level
-  constexpr int M = media_rows<R>();
+__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float2* smem) {
+  constexpr int U = 2 * R + 1;       // window rows = plane slots
   constexpr int OFF = 64 * U;        // keeps compile-time slot arithmetic non-negative
   const int tid = threadIdx.x;
   const ProbDev q = P.probs[it.prob];
   const TileGeo tg = P.tgeo[it.prob];
   const int nx = q.n[0], ny = q.n[1];
+  const int PPn = nx * ny;           // points per field (< 2^31, checked at creation)
   const int sx = it.tile % tg.nst, sy = it.tile / tg.nst;
   const int x0 = (sx * nx) / tg.nst;
   const int wout = ((sx + 1) * nx) / tg.nst - x0;
@@ -182,155 +191,140 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
   const int x = wrapi(x0 - R * T + tid, nx);
   const float2 hf = P.hkf[it.prob * GBS_MAX_SEQ + it.seq];
-  const float h1 = hf.x, h2 = hf.y;
-  const float h2x = h2 * float(q.inv_dx[0]), h2y = h2 * float(q.inv_dx[1]);
-  const float rxy = float(q.inv_dx[1] / q.inv_dx[0]);   // y-stencil weight relative to x
-  const int64_t PP = q.pts;
-  const float* kap = P.kappa + q.media_off;
-  const float* bb = P.b + q.media_off;
-  const float* inA;
-  const float* inB;
-  if (pd.first) {
-    inA = P.y0 + q.state_off;   // level -1 = y_0
-    inB = P.f0 + q.state_off;   // level 0 = y_0 + h f0
-  } else {
-    const int set_in = (it.pass - 1) & 1;
-    inA = P.lev + ((int64_t)(it.seq * 2 + set_in) * 2 + 0) * P.E + q.state_off;
-    inB = P.lev + ((int64_t)(it.seq * 2 + set_in) * 2 + 1) * P.E + q.state_off;
-  }
-  float* outA;
-  float* outB = nullptr;
-  if (pd.last) {
-    outA = P.ystar + (int64_t)it.seq * P.E + q.state_off;
-  } else {
-    const int set_out = it.pass & 1;
-    outA = P.lev + ((int64_t)(it.seq * 2 + set_out) * 2 + 0) * P.E + q.state_off;
-    outB = P.lev + ((int64_t)(it.seq * 2 + set_out) * 2 + 1) * P.E + q.state_off;
-  }
+  const float h1 = hf.x;
+  const float mh = -hf.y * float(q.inv_dx[0]);            // -2h / dx
+  const float rxy = float(q.inv_dx[1] / q.inv_dx[0]);      // y-stencil weight relative to x
+  const float2* kbm = P.kb + q.media_off;
+  // the two input levels (y_(n-1), y_n) -- (y_0, f0) for a first pass -- and the two output
+  // levels (or the average) are E apart
+  const float* inA = pd.first ? P.init + q.state_off
+                              : P.lev + ((int64_t)(it.seq * 2 + ((it.pass - 1) & 1)) * 2) * P.E + q.state_off;
+  float* outA = pd.last ? P.ystar + (int64_t)it.seq * P.E + q.state_off
+                        : P.lev + ((int64_t)(it.seq * 2 + (it.pass & 1)) * 2) * P.E + q.state_off;
+  const int64_t E = P.E;
   const bool out_col = tid >= R * T && tid < R * T + wout;
-  float2* const lvl = reinterpret_cast<float2*>(smem) + kPad + tid;               // this column
-  float2* const med = reinterpret_cast<float2*>(smem) + kTMax * UR * kRow + kPad + tid;
-  auto RING = [&](int t, int slot) -> float2* { return lvl + (t * UR + slot) * kRow; };
+  float2* const lvl = smem + kPad + tid;                                  // plane t, slot r: lvl[(t U + r) kRow]
+  float2* const med = smem + kTMax * U * kRow + tid;                      // plane g, slot r: med[(g U + r) kThreads]
 
-  float wp[T][U], wv[T][U];
+  // (p, v) windows of levels 0..T-1.  Level t computes local row s - R T - R t at sweep step
+  // s.  Rows before a level's first valid row (s < 2 R t) are computed from not-yet-valid
+  // inputs and never reach a valid row: valid level-t rows start at -R (T - t) and read level
+  // t-1 rows from -R (T - t) - R on, which are valid.  So no step is guarded.
+  float2 w[T][U];
 #pragma unroll
   for (int t = 0; t < T; ++t)
 #pragma unroll
-    for (int u = 0; u < U; ++u) wp[t][u] = wv[t][u] = 0.f;
+    for (int u = 0; u < U; ++u) w[t][u] = make_float2(0.f, 0.f);
 
-  // global loads of one sweep step, issued one step ahead
   const int S = hs + 2 * R * T;
-  int gy0 = wrapf(Y0 - R * T, ny);          // grid row of level 0 at step 0
-  int gy1 = wrapf(Y0 - R * T - R, ny);      // grid row of level -1 (level 1's row) at step 0
-  float n0p, n0u, n0v, n1p = 0.f, n1u = 0.f, n1v = 0.f, nk, nb;
-  auto fetch = [&](int s) {
-    const int64_t e0 = (int64_t)gy0 * nx + x;
+  int e0 = wrapf(Y0 - R * T, ny) * nx + x;       // level 0's row at step 0
+  int e1 = wrapf(Y0 - R * T - R, ny) * nx + x;   // level -1 at level 1's row at step 0
+  int eo = (Y0 - 2 * R * T) * nx + x;            // level T's output row at step 0 (unwrapped)
+  // raw loads of the next step: level 0 (f0 in a first pass, whose level 0 is y_0 + h f0,
+  // combined at the commit so that no load is consumed in the step that issues it), y_0 at
+  // level 0's row (first pass only), level -1 at level 1's row, media
+  float n0p, n0u, n0v, y0p = 0.f, y0u = 0.f, y0v = 0.f, n1p, n1u, n1v;
+  float2 nm;
+  auto fetch = [&]() {
+    const float* a = inA + e1;
+    const float* b = inA + E + e0;
+    n0p = __ldcg(b);
+    n0u = __ldcg(b + PPn);
+    n0v = __ldcg(b + 2 * PPn);
     if (pd.first) {
-      n0p = __ldg(inA + e0) + h1 * __ldg(inB + e0);
-      n0u = __ldg(inA + PP + e0) + h1 * __ldg(inB + PP + e0);
-      n0v = __ldg(inA + 2 * PP + e0) + h1 * __ldg(inB + 2 * PP + e0);
-    } else {
-      n0p = __ldcg(inB + e0);
-      n0u = __ldcg(inB + PP + e0);
-      n0v = __ldcg(inB + 2 * PP + e0);
+      const float* y = inA + e0;
+      y0p = __ldcg(y);
+      y0u = __ldcg(y + PPn);
+      y0v = __ldcg(y + 2 * PPn);
     }
-    nk = __ldg(kap + e0);
-    nb = __ldg(bb + e0);
-    if (s >= 2 * R) {
-      const int64_t e1 = (int64_t)gy1 * nx + x;
-      if (pd.first) {
-        n1p = __ldg(inA + e1);
-        n1u = __ldg(inA + PP + e1);
-        n1v = __ldg(inA + 2 * PP + e1);
-      } else {
-        n1p = __ldcg(inA + e1);
-        n1u = __ldcg(inA + PP + e1);
-        n1v = __ldcg(inA + 2 * PP + e1);
-      }
-    }
+    n1p = __ldcg(a);
+    n1u = __ldcg(a + PPn);
+    n1v = __ldcg(a + 2 * PPn);
+    nm = __ldg(kbm + e0);
   };
-  fetch(0);
-  int ms0 = 0;   // media ring slot of level 0's row
-  int rs0 = 0;   // level ring slot of level 0's row
+  fetch();
   for (int sb = 0; sb < S; sb += U) {
 #pragma unroll
     for (int uu = 0; uu < U; ++uu) {
       const int s = sb + uu;
       if (s >= S) break;
-      // ---- commit level 0 (local row s - R T), level -1, media ----
-      const int slot0 = (uu + OFF - R * T) % U;
-      const float p0 = n0p, u0 = n0u, v0 = n0v;
-      const float am_p = n1p, am_u = n1u, am_v = n1v;
-      wp[0][slot0] = p0;
-      wv[0][slot0] = v0;
-      RING(0, rs0)[0] = make_float2(p0, u0);
-      med[ms0 * kRow] = make_float2(nk, nb);
-      // ---- prefetch step s + 1 ----
-      gy0 = gy0 + 1 == ny ? 0 : gy0 + 1;
-      gy1 = gy1 + 1 == ny ? 0 : gy1 + 1;
-      if (s + 1 < S) fetch(s + 1);
-      // ---- levels 1..T: level t computes local row s - R T - R t ----
+      // ---- level 0 (local row s - R T), level -1, media ----
+      const int r0 = (uu + OFF - R * T) % U;
+      float p0 = n0p, u0 = n0u, v0 = n0v;
+      if (pd.first) {
+        p0 = fmaf(h1, p0, y0p);
+        u0 = fmaf(h1, u0, y0u);
+        v0 = fmaf(h1, v0, y0v);
+      }
+      w[0][r0] = make_float2(p0, v0);
+      lvl[r0 * kRow] = make_float2(p0, u0);
+      med[r0 * kThreads] = __fmul2_rn(make_float2(mh, mh), nm);
+      const float2 am_pv = make_float2(n1p, n1v);
+      const float am_u = n1u;
+      // ---- prefetch step s + 1 (rows wrap, so the extra fetch after the last step is in bounds) ----
+      e0 += nx;
+      if (e0 >= PPn) e0 -= PPn;
+      e1 += nx;
+      if (e1 >= PPn) e1 -= PPn;
+      fetch();
+      const bool stT = out_col && (unsigned)(s - 2 * R * T) < (unsigned)hs;
+      const bool stT1 = out_col && (unsigned)(s - 2 * R * T + R) < (unsigned)hs;
+      // ---- levels 1..T ----
 #pragma unroll
       for (int t = 1; t <= T; ++t) {
-        if (s >= 2 * t * R) {
-          const int sl = (uu + OFF - R * T - R * t) % U;   // register window slot of this row
-          int rs = rs0 - R * t;                             // ring slot of this row
-          if (rs < 0) rs += UR;
-          if (rs < 0) rs += UR;
-          int ms = ms0 - R * t;
-          if (ms < 0) ms += M;
-          const float2 kb = med[ms * kRow];
-          const float2 sxpu = dsum2<R>(RING(t - 1, rs));
-          const float syp = dwin<R>(wp[t - 1], sl);
-          const float syv = dwin<R>(wv[t - 1], sl);
-          float pp, pu, pv;
-          if (t == 1) {
-            pp = am_p;
-            pu = am_u;
-            pv = am_v;
-          } else {
-            pp = wp[t - 2][sl];
-            pv = wv[t - 2][sl];
-            pu = RING(t - 2, rs)[0].y;
+        const int r = (uu + OFF - R * T - R * t) % U;   // slot of this level's row
+        const float2 km = med[(((t - 1) / 2) * U + r) * kThreads];
+        if (t % 2 == 0 && t < T) med[((t / 2) * U + r) * kThreads] = km;
+        const float2 sxv = xsum2<R>(lvl + ((t - 1) * U + r) * kRow);   // (sum_x p, sum_x u)
+        const float2 syv = ysum2<R>(w[t - 1], r);                       // (sum_y p, sum_y v)
+        float2 ppv;
+        float pu;
+        if (t == 1) {
+          ppv = am_pv;
+          pu = am_u;
+        } else {
+          ppv = w[t - 2][r];
+          pu = lvl[((t - 2) * U + r) * kRow].y;
+        }
+        const float np = fmaf(km.x, fmaf(rxy, syv.y, sxv.y), ppv.x);
+        const float nu = fmaf(km.y, sxv.x, pu);
+        const float nv = fmaf(km.y * rxy, syv.x, ppv.y);
+        if (t < T) {
+          w[t][r] = make_float2(np, nv);
+          lvl[(t * U + r) * kRow] = make_float2(np, nu);
+        }
+        if (!pd.last) {
+          if (t == T - 1 && stT1) {
+            float* o = outA + (eo + R * nx);
+            __stcg(o, np);
+            __stcg(o + PPn, nu);
+            __stcg(o + 2 * PPn, nv);
           }
-          const float np = fmaf(-h2x * kb.x, fmaf(rxy, syv, sxpu.y), pp);
-          const float nu = fmaf(-h2x * kb.y, sxpu.x, pu);
-          const float nv = fmaf(-h2y * kb.y, syp, pv);
-          if (t < T) {
-            wp[t][sl] = np;
-            wv[t][sl] = nv;
-            RING(t, rs)[0] = make_float2(np, nu);
+          if (t == T && stT) {
+            float* o = outA + E + eo;
+            __stcg(o, np);
+            __stcg(o + PPn, nu);
+            __stcg(o + 2 * PPn, nv);
           }
-          if (t >= T - 1 && (t == T || !pd.last)) {
-            const int rho = s - R * T - R * t;
-            if (out_col && rho >= 0 && rho < hs) {
-              const int64_t e = (int64_t)(Y0 + rho) * nx + x;
-              if (!pd.last) {
-                float* o = (t == T) ? outB : outA;
-                __stcg(o + e, np);
-                __stcg(o + PP + e, nu);
-                __stcg(o + 2 * PP + e, nv);
-              } else {
-                // y_(N-1) = prev, y_N = level T-1 at this row, y_(N+1) = new
-                const float cp = wp[T - 1][sl], cv = wv[T - 1][sl], cu = RING(T - 1, rs)[0].y;
-                __stcg(outA + e, gragg_avg(pp, cp, np));
-                __stcg(outA + PP + e, gragg_avg(pu, cu, nu));
-                __stcg(outA + 2 * PP + e, gragg_avg(pv, cv, nv));
-              }
-            }
-          }
+        } else if (t == T && stT) {
+          // y_(N-1) = previous, y_N = level T-1 at this row, y_(N+1) = new
+          const float2 cpv = w[T - 1][r];
+          const float cu = lvl[((T - 1) * U + r) * kRow].y;
+          float* o = outA + eo;
+          __stcg(o, gragg_avg(ppv.x, cpv.x, np));
+          __stcg(o + PPn, gragg_avg(pu, cu, nu));
+          __stcg(o + 2 * PPn, gragg_avg(ppv.y, cpv.y, nv));
         }
       }
-      ms0 = ms0 + 1 == M ? 0 : ms0 + 1;
-      rs0 = rs0 + 1 == UR ? 0 : rs0 + 1;
-      if ((s % kSyncEvery) == kSyncEvery - 1) __syncthreads();
+      eo += nx;
+      if (uu % R == R - 1 || uu == U - 1) __syncthreads();
     }
   }
 }
 
 template <int R>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P) {
-  extern __shared__ float smem[];
+  extern __shared__ float2 smem[];
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
@@ -405,8 +399,8 @@ __global__ void k_combine(const ProbDev* probs, int batch, const SlotDev* slots,
 }
 
 size_t ring_bytes(int R) {
-  const int ur = 2 * R + kSyncEvery, m = R * kTMax + kSyncEvery + 1;
-  return (size_t)(kTMax * ur + m) * kRow * sizeof(float2);
+  const int u = 2 * R + 1;
+  return (size_t)(kTMax * u * kRow + media_planes() * u * kThreads) * sizeof(float2);
 }
 
 }  // namespace fused
@@ -424,12 +418,14 @@ struct FusedWork {
   int hseg = 512;
   float* lev = nullptr;
   float* ystar = nullptr;
+  float* init = nullptr;   // [2][E]: copy of y_0, f0 (written by the f0 kernel)
+  float2* kb = nullptr;    // media as (kappa, b) pairs (written by the f0 kernel)
   fused::Item* items = nullptr;
   int* deps = nullptr;
   int* done = nullptr;   // n_items flags followed by the queue counter
   fused::PassDesc* pdesc = nullptr;
   fused::TileGeo* tgeo = nullptr;
-  size_t lev_cap = 0, ystar_cap = 0, items_cap = 0;
+  size_t lev_cap = 0, ystar_cap = 0, items_cap = 0, init_cap = 0, kb_cap = 0;
   double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
   long long spin_limit = fused::kSpinLimit;
   int inject_wait = 0;    // test hook: item 0 also waits on a flag that nothing sets
@@ -438,10 +434,12 @@ struct FusedWork {
 namespace {
 
 void free_work(FusedWork* w) {
-  void* ptrs[] = {w->lev, w->ystar, w->items, w->deps, w->done, w->pdesc, w->tgeo};
+  void* ptrs[] = {w->lev, w->ystar, w->init, w->kb, w->items, w->deps, w->done, w->pdesc, w->tgeo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  w->lev = w->ystar = nullptr;
+  w->lev = w->ystar = w->init = nullptr;
+  w->kb = nullptr;
+  w->init_cap = w->kb_cap = 0;
   w->items = nullptr;
   w->deps = w->done = nullptr;
   w->pdesc = nullptr;
@@ -449,7 +447,7 @@ void free_work(FusedWork* w) {
   w->lev_cap = w->ystar_cap = w->items_cap = 0;
 }
 
-// Leap-frog levels of sequence N split into passes: first N mod 8 (if nonzero), then 8s.
+// Leap-frog levels of sequence N split into passes: first N mod kTMax (if nonzero), then kTMax each.
 std::vector<int> pass_plan(int N) {
   std::vector<int> v;
   int rem = N % fused::kTMax;
@@ -597,8 +595,13 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   // device buffers
   const size_t lev_bytes = (size_t)4 * p.max_m * p.state_elems * sizeof(float);
   const size_t ys_bytes = (size_t)p.max_m * p.state_elems * sizeof(float);
-  if (grow(&w->lev, &w->lev_cap, lev_bytes) || grow(&w->ystar, &w->ystar_cap, ys_bytes)) {
-    std::snprintf(msg, msglen, "cudaMalloc of the fused level store (%zu bytes) failed", lev_bytes + ys_bytes);
+  const size_t init_bytes = (size_t)2 * p.state_elems * sizeof(float);
+  const size_t kb_bytes =
+      (size_t)(probs_h[p.batch - 1].media_off + probs_h[p.batch - 1].pts) * sizeof(float2);
+  if (grow(&w->lev, &w->lev_cap, lev_bytes) || grow(&w->ystar, &w->ystar_cap, ys_bytes) ||
+      grow(&w->init, &w->init_cap, init_bytes) || grow(&w->kb, &w->kb_cap, kb_bytes)) {
+    std::snprintf(msg, msglen, "cudaMalloc of the fused level store (%zu bytes) failed",
+                  lev_bytes + ys_bytes + init_bytes + kb_bytes);
     return -2;
   }
   if (w->items) cudaFree(w->items);
@@ -668,7 +671,12 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
 int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err) {
   using namespace fused;
   int launches = 0;
-  if (launch_f0(p, y_in, s) < 0) return -1;
+  // f0 goes next to a copy of y_0, and the media are interleaved for the passes
+  StepPlan pf = p;
+  pf.f0 = w->init + w->E;
+  pf.f0_ycopy = w->init;
+  pf.f0_kb = w->kb;
+  if (launch_f0(pf, y_in, s) < 0) return -1;
   ++launches;
   if (cudaMemsetAsync(w->done, 0, sizeof(int) * (w->n_items + 2), s) != cudaSuccess) return -1;
   Params P;
@@ -682,10 +690,8 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.slots = p.slots;
   P.hk = p.hk;
   P.hkf = p.hkf;
-  P.kappa = static_cast<const float*>(p.kappa);
-  P.b = static_cast<const float*>(p.b);
-  P.y0 = static_cast<const float*>(y_in);
-  P.f0 = static_cast<const float*>(p.f0);
+  P.kb = w->kb;
+  P.init = w->init;
   P.lev = w->lev;
   P.ystar = w->ystar;
   P.E = w->E;

@@ -60,6 +60,10 @@ struct StepPlan {
   void* L0;                    // leap-frog level buffers, F x P each
   void* L1;
   double* acc;                 // FP64 combine accumulator, F x P
+  // optional extra outputs of the f0 kernel (FP32 acoustics, time-blocked path): a copy of
+  // y_in and the media as interleaved (kappa, b) pairs
+  float* f0_ycopy;
+  float2* f0_kb;
   // host-side schedule: for sequence index k, the largest step count over problems
   int max_m;
   int max_steps_k[GBS_MAX_SEQ];

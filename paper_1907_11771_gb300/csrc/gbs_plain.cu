@@ -102,6 +102,14 @@ __global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* _
   T* f0 = static_cast<T*>(p.f0) + q.state_off;
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) f0[fl * q.pts + L.i] = f[fl];
+  if (SYS == SYS_ACOUSTIC && sizeof(T) == 4) {
+    if (p.f0_ycopy) {
+      float* yc = p.f0_ycopy + q.state_off;
+#pragma unroll
+      for (int fl = 0; fl < F; ++fl) yc[fl * q.pts + L.i] = float(y_in[q.state_off + fl * q.pts + L.i]);
+    }
+    if (p.f0_kb) p.f0_kb[q.media_off + L.i] = make_float2(float(kap), float(bb));
+  }
 }
 
 template <typename T, int SYS, int DIM>
