@@ -242,8 +242,35 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
     n1v = __ldcg(a + 2 * PPn);
     nm = __ldg(kbm + e0);
   };
+  // L2 prefetch of the rows the next block of U steps loads, so that the one-step-ahead
+  // register loads find them in L2: warps 0-2 take level 0's fields, warps 3-5 level -1's
+  // (R more rows, which also covers y_0 at level 0's rows in a first pass), warp 6 the media.
+  // A sample every 128 bytes of the CTA's 256-column row segment touches each of its lines.
+  const int xf = wrapi(x0 - R * T, nx);   // column of thread 0
+  auto prefetch_block = [&](int sn) {
+    const int wq = tid >> 5;
+    if (wq > 6) return;
+    int row0 = Y0 - R * T + sn - (wq >= 3 && wq < 6 ? R : 0);
+    row0 = wrapi(row0, ny);
+    const int nrows = (wq >= 3 && wq < 6) ? U + R : U;
+    const int nsamp = wq == 6 ? 17 : 9;        // columns 128 bytes apart, plus the last one
+    const int step = wq == 6 ? 16 : 32;
+    const char* base;
+    size_t esz;
+    if (wq < 3) { base = reinterpret_cast<const char*>(inA + E + wq * PPn); esz = 4; }
+    else if (wq < 6) { base = reinterpret_cast<const char*>(inA + (wq - 3) * PPn); esz = 4; }
+    else { base = reinterpret_cast<const char*>(kbm); esz = 8; }
+    for (int i = tid & 31; i < nrows * nsamp; i += 32) {
+      const int j = i / nsamp, c = i - j * nsamp;
+      int row = row0 + j;
+      if (row >= ny) row -= ny;
+      const int col = (xf + (c + 1 < nsamp ? c * step : kThreads - 1)) % nx;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((size_t)row * nx + col) * esz));
+    }
+  };
   fetch();
   for (int sb = 0; sb < S; sb += U) {
+    prefetch_block(sb + U);
 #pragma unroll
     for (int uu = 0; uu < U; ++uu) {
       const int s = sb + uu;
