@@ -38,9 +38,12 @@ N_GAUSS = 16
 H_FRACTION = 0.8
 
 
-def workload_desc(n=N_GRID):
+PREC_DESC = {0: "FP32 state + FP64 combine", 1: "FP64", 2: "FP64 states in FP32-pair arithmetic + FP64 combine"}
+
+
+def workload_desc(n=N_GRID, prec=0):
     return (f"2D acoustics {n}x{n} periodic, 6th-order FD, GBS_8,6 (11 sequences, 143 updates/pt), "
-            f"FP32 state + FP64 combine, H = {H_FRACTION} x stability limit")
+            f"{PREC_DESC[prec]}, H = {H_FRACTION} x stability limit")
 
 
 def peaks():
@@ -216,16 +219,16 @@ def make_workload(args, rank):
     from paper_1907_11771_gb300.solver import GBSSolver
 
     F32 = B.GBS_F32_STATE_F64_COMBINE
-    prec = B.GBS_F64 if args.f64 else F32
-    dt = np.float64 if args.f64 else np.float32
-    tdt = torch.float64 if args.f64 else torch.float32
+    prec = B.GBS_F64 if args.f64 else B.GBS_F32X2 if args.f32x2 else F32
+    dt = np.float32 if prec == F32 else np.float64
+    tdt = torch.float32 if prec == F32 else torch.float64
     wl = args.workload
     if wl == "2d":
         n = args.grid
         y0, kappa, rho = inputs.acoustic_problem((n, n), rank, N_GAUSS, SIGMA * n / N_GRID, dtype=dt)
         shapes, sch = [(n, n)], S.GBS_8_6
         order = FD_ORDER
-        desc = workload_desc(n)
+        desc = workload_desc(n, prec)
         slots = None
     elif wl == "3d":
         n = args.grid if args.grid != N_GRID else 512
@@ -363,10 +366,11 @@ def run_gpu(args):
                     "parallelism": f"replicas x{ws}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.f64 else "f32",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.f64 else "f32x2" if args.f32x2 else "f32",
                 "data": "synthetic", "config": cfg,
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
-        if ws == 1 and not args.no_cpu_baseline and args.workload == "2d" and not args.f64:
+        if ws == 1 and not args.no_cpu_baseline and args.workload == "2d" and not (args.f64 or args.f32x2):
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     sol.close()
@@ -377,7 +381,8 @@ def run_gpu(args):
 
 def run_time_to_solution(args):
     """Time to a relative L2 error of 1e-6 at t = M0 H0 (2D acoustics, same recipe on an
-    n x n grid): the fused FP32-state path and the plain FP64 path, each swept over
+    n x n grid): the fused FP32-state path, the plain FP64 path and the plain FP32-pair path,
+    each swept over
     H = H0 / 2^j (H0 = 0.8 x the GBS_8,6 stability limit), against an FP64 GBS_12,8
     reference run at a quarter of its own 0.8 x limit and checked against one at an eighth."""
     import numpy as np
@@ -395,7 +400,7 @@ def run_time_to_solution(args):
     y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, SIGMA * n / N_GRID)
 
     def solver(prec, scheme, kernel):
-        dt = np.float64 if prec == B.GBS_F64 else np.float32
+        dt = np.float32 if prec == B.GBS_F32_STATE_F64_COMBINE else np.float64
         tk = torch.tensor(kappa.astype(dt).ravel(), device="cuda")
         tr = torch.tensor(rho.astype(dt).ravel(), device="cuda")
         s = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=FD_ORDER, precision=prec, kappa=tk, rho=tr)
@@ -427,7 +432,8 @@ def run_time_to_solution(args):
     ref_err = rel(ref2)
     rows = {}
     paths = [("fused FP32 state + FP64-class combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
-             ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64)]
+             ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64),
+             ("plain FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_PLAIN, torch.float64)]
     for name, prec, kernel, dt in paths:
         sol = solver(prec, S.GBS_8_6, kernel)
         rows[name] = []
@@ -462,6 +468,7 @@ def main():
     ap.add_argument("--workload", choices=["2d", "3d", "batch"], default="2d",
                     help="2d (default, the headline workload), 3d (512^3) or batch (256 problems)")
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
+    ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-solution", action="store_true",

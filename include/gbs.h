@@ -30,7 +30,16 @@
  *    F = 1 + ndim (p, u_x, u_y[, u_z]) for acoustics.  Media arrays (kappa,
  *    rho) and gradients use [nz][ny][nx] per problem, concatenated likewise.
  *  - Element type of states and media: float for GBS_F32_STATE_F64_COMBINE,
- *    double for GBS_F64.  Gradients are always double.
+ *    double for GBS_F64 and GBS_F32X2.  Gradients are always double.
+ *  - Precisions.  GBS_F32_STATE_F64_COMBINE keeps the leap-frog levels in FP32
+ *    and sums the combine in FP64-class arithmetic (the throughput path).
+ *    GBS_F64 computes everything in FP64.  GBS_F32X2 takes FP64 states and
+ *    media, holds the levels as pairs of floats (hi + lo, about 48 significant
+ *    bits) and evaluates the right-hand sides and leap-frog updates with
+ *    error-free FP32 transformations on the FP32 units, then combines in FP64;
+ *    it reaches FP64-class accuracy (a few 1e-15 per operation) at FP32-unit
+ *    speed.  The paper fixes no arithmetic precision; the three are
+ *    implementation choices.  The adjoint of a GBS_F32X2 handle runs in FP64.
  *  - Work is enqueued asynchronously on the stream given to gbs_create.
  *    Device-side failures are latched and reported by gbs_sync().
  */
@@ -65,7 +74,7 @@ typedef enum {
 } gbs_status;
 
 enum { GBS_WAVE1D = 1, GBS_ACOUSTIC = 2 };                /* gbs_problem.system    */
-enum { GBS_F32_STATE_F64_COMBINE = 0, GBS_F64 = 1 };       /* gbs_problem.precision */
+enum { GBS_F32_STATE_F64_COMBINE = 0, GBS_F64 = 1, GBS_F32X2 = 2 }; /* gbs_problem.precision */
 enum { GBS_KERNEL_AUTO = 0, GBS_KERNEL_PLAIN = 1, GBS_KERNEL_FUSED = 2 }; /* gbs_set_option */
 
 /* Problem description.  All problems of a batch share system, ndim, fd_order
@@ -75,7 +84,7 @@ typedef struct {
                              (p_t = -kappa div u, u_t = -grad p / rho)          */
   int ndim;               /* 1 for GBS_WAVE1D; 1, 2 or 3 for GBS_ACOUSTIC        */
   int fd_order;           /* 4 or 6: periodic centred finite differences         */
-  int precision;          /* GBS_F32_STATE_F64_COMBINE or GBS_F64                */
+  int precision;          /* GBS_F32_STATE_F64_COMBINE, GBS_F64 or GBS_F32X2     */
   int batch;              /* number of independent problems, >= 1               */
   int enable_adjoint;     /* nonzero: reserve workspace for gbs_adjoint_step     */
   const int64_t* shape;   /* host, batch x 3: (nx, ny, nz), unused dims = 1      */
@@ -193,7 +202,11 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * (record CUDA events around every launch of the dominant kernel -- the
  * leap-frog step kernel, or the time-blocked pass kernel -- on the handle's
  * stream; graph replay is bypassed while it is on), "hseg" = row-segment height of
- * the time-blocked tiles (16..65536, default 256), "spin_limit" = polls of a
+ * the time-blocked tiles (16..65536, default 256), "tmax" = most leap-frog levels per
+ * time-blocked pass (0 = the kernel's largest, 4; or 2), "schedule" = order of the
+ * time-blocked work queue (0 = longest remaining chain of passes first, the default;
+ * 1 = pass by pass across all sequences) -- these three only shape the schedule and are
+ * what an autotuner varies -- "spin_limit" = polls of a
  * dependency flag in the time-blocked kernel before it gives up and latches
  * GBS_ERR_TIMEOUT (default 2^20, about half a second), and
  * "inject_unsatisfiable_wait" = 0/1, a failure-detection test hook that makes

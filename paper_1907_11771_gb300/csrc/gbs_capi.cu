@@ -44,6 +44,7 @@ struct GraphEntry {
 struct gbs_ctx {
   // problem
   int system = 0, ndim = 0, order = 0, R = 0, f64 = 0, batch = 0, F = 0, adjoint = 0;
+  int ds = 0;                             // GBS_F32X2: FP32-pair levels and right-hand sides
   size_t esz = 4;                         // state element size
   std::vector<ProbDev> probs;
   int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0;
@@ -73,6 +74,9 @@ struct gbs_ctx {
   double* acc = nullptr;
   void* stage = nullptr;
   void* levels = nullptr;
+  void* ds_y0 = nullptr;                  // GBS_F32X2: y_in, kappa, b as FP32 pairs
+  void* ds_kappa = nullptr;
+  void* ds_b = nullptr;
   int levels_steps = 0;
   void* mu0 = nullptr;
   void* mu1 = nullptr;
@@ -87,6 +91,8 @@ struct gbs_ctx {
   int opt_check_stability = 0;
   int opt_time_kernels = 0;
   int opt_hseg = 256;
+  int opt_tmax = 0;                       // 0: the kernel's largest pass depth
+  int opt_schedule = 0;
   int64_t opt_spin_limit = 1 << 20;
   int opt_inject_wait = 0;
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
@@ -148,7 +154,7 @@ gbs_status validate_problem(const gbs_problem* pb, gbs_ctx* h) {
   if (pb->system == GBS_WAVE1D && pb->ndim != 1) return fail(h, GBS_ERR_INVALID, "GBS_WAVE1D needs ndim == 1");
   if (pb->ndim < 1 || pb->ndim > 3) return fail(h, GBS_ERR_INVALID, "ndim must be 1, 2 or 3");
   if (pb->fd_order != 4 && pb->fd_order != 6) return fail(h, GBS_ERR_INVALID, "fd_order must be 4 or 6");
-  if (pb->precision != GBS_F32_STATE_F64_COMBINE && pb->precision != GBS_F64)
+  if (pb->precision != GBS_F32_STATE_F64_COMBINE && pb->precision != GBS_F64 && pb->precision != GBS_F32X2)
     return fail(h, GBS_ERR_INVALID, "unknown precision");
   if (pb->batch < 1) return fail(h, GBS_ERR_INVALID, "batch must be >= 1");
   if (!pb->shape || !pb->dx) return fail(h, GBS_ERR_INVALID, "shape and dx arrays are required");
@@ -204,7 +210,7 @@ void free_graphs(gbs_ctx* h) {
 void free_all(gbs_ctx* h) {
   free_graphs(h);
   void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
-                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared};
+                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa, h->ds_b};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -338,6 +344,11 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->ndim = h->ndim;
   p->R = h->R;
   p->f64 = h->f64;
+  p->ds = h->ds;
+  p->ds_y0 = h->ds_y0;
+  p->ds_kappa = h->ds_kappa;
+  p->ds_b = h->ds_b;
+  p->probs_media_elems = h->media_elems;
   p->F = h->F;
   p->batch = h->batch;
   p->probs = h->d_probs;
@@ -398,7 +409,8 @@ gbs_status prepare_fused(gbs_ctx* h) {
   }
   CK(h, cudaStreamSynchronize(h->stream));
   char msg[256] = {0};
-  const int r = fused_prepare(h->fw, p, h->probs.data(), sd, h->opt_hseg, msg, sizeof msg);
+  const FusedTune tune{h->opt_hseg, h->opt_tmax ? h->opt_tmax : fused_max_levels(), h->opt_schedule};
+  const int r = fused_prepare(h->fw, p, h->probs.data(), sd, tune, msg, sizeof msg);
   if (r == -2) return fail(h, GBS_ERR_NOMEM, "%s", msg);
   if (r < 0) return fail(h, GBS_ERR_CUDA, "%s", msg);
   h->fw_ready = true;
@@ -485,11 +497,12 @@ size_t gbs_state_elems(const gbs_problem* pb) {
 size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps) {
   if (validate_problem(pb, nullptr) != GBS_OK || max_steps < 0) return 0;
   const Sizes s = sizes_of(pb);
-  const size_t esz = pb->precision == GBS_F64 ? 8 : 4;
+  const size_t esz = pb->precision == GBS_F32_STATE_F64_COMBINE ? 4 : 8;
   size_t bytes = 0;
   bytes += 4 * s.state_elems * esz;       // f0, L0, L1, stage
   bytes += 8 * s.state_elems;             // acc
   bytes += s.media_elems * esz;           // b
+  if (pb->precision == GBS_F32X2) bytes += 8 * (s.state_elems + 2 * s.media_elems);   // pair copies
   if (pb->enable_adjoint) bytes += (size_t)(max_steps + 2 + 3) * s.state_elems * esz;
   bytes += sizeof(ProbDev) * pb->batch + sizeof(SlotDev) * GBS_MAX_SLOTS + 8 * pb->batch * 2 +
            8 * (4 * kNormBlocks + 4) + 64;
@@ -512,7 +525,8 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   h->ndim = pb->ndim;
   h->order = pb->fd_order;
   h->R = pb->fd_order / 2;
-  h->f64 = pb->precision == GBS_F64;
+  h->f64 = pb->precision != GBS_F32_STATE_F64_COMBINE;   // FP64 states and media in the API
+  h->ds = pb->precision == GBS_F32X2;
   h->esz = h->f64 ? 8 : 4;
   h->batch = pb->batch;
   h->F = fields_of(pb->system, pb->ndim);
@@ -565,6 +579,12 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   if ((st = dalloc(h, &h->acc, E * sizeof(double))) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->stage, E * h->esz)) != GBS_OK) return bail(st);
   if (h->system == GBS_ACOUSTIC && (st = dalloc(h, &h->b, P * h->esz)) != GBS_OK) return bail(st);
+  if (h->ds) {   // FP32 pairs take 8 bytes, like the FP64 values they are made from
+    if ((st = dalloc(h, &h->ds_y0, E * 8)) != GBS_OK) return bail(st);
+    if (h->system == GBS_ACOUSTIC && ((st = dalloc(h, &h->ds_kappa, P * 8)) != GBS_OK ||
+                                      (st = dalloc(h, &h->ds_b, P * 8)) != GBS_OK))
+      return bail(st);
+  }
   if (h->adjoint) {
     if ((st = dalloc(h, &h->mu0, E * h->esz)) != GBS_OK) return bail(st);
     if ((st = dalloc(h, &h->mu1, E * h->esz)) != GBS_OK) return bail(st);
@@ -866,6 +886,17 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
     h->opt_hseg = (int)value;
     gbs_status st = prepare_fused(h);
     if (st != GBS_OK) return st;
+  } else if (!std::strcmp(name, "tmax")) {
+    if (value != 0 && (value < 2 || value > fused_max_levels() || value % 2))
+      return fail(h, GBS_ERR_INVALID, "tmax must be 0 or even in [2, %d]", fused_max_levels());
+    h->opt_tmax = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
+  } else if (!std::strcmp(name, "schedule")) {
+    if (value != 0 && value != 1) return fail(h, GBS_ERR_INVALID, "schedule must be 0 or 1");
+    h->opt_schedule = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "spin_limit") || !std::strcmp(name, "inject_unsatisfiable_wait")) {
     if (!std::strcmp(name, "spin_limit")) {
       if (value < 1) return fail(h, GBS_ERR_INVALID, "spin_limit must be >= 1");
@@ -900,6 +931,8 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "check_stability")) *value = h->opt_check_stability;
   else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
   else if (!std::strcmp(name, "hseg")) *value = h->opt_hseg;
+  else if (!std::strcmp(name, "tmax")) *value = h->opt_tmax ? h->opt_tmax : fused_max_levels();
+  else if (!std::strcmp(name, "schedule")) *value = h->opt_schedule;
   else if (!std::strcmp(name, "spin_limit")) *value = h->opt_spin_limit;
   else if (!std::strcmp(name, "inject_unsatisfiable_wait")) *value = h->opt_inject_wait;
   else if (!std::strcmp(name, "kernel_in_use")) {

@@ -243,29 +243,24 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
     nm = __ldg(kbm + e0);
   };
   // L2 prefetch of the rows the next block of U steps loads, so that the one-step-ahead
-  // register loads find them in L2: warps 0-2 take level 0's fields, warps 3-5 level -1's
-  // (R more rows, which also covers y_0 at level 0's rows in a first pass), warp 6 the media.
-  // A sample every 128 bytes of the CTA's 256-column row segment touches each of its lines.
+  // register loads find them in L2: warps 0-2 take level 0's fields, warps 3-5 level -1's (in a
+  // first pass the same y_0 rows, R behind, that level 0 also reads).  A sample every 128
+  // bytes of the CTA's 256-column row segment touches each of its lines.  The media (a fifth
+  // of the bytes, small enough to stay in L2 across sequences) are not prefetched; measured,
+  // prefetching them or R more rows of level -1 was slower, and so were bulk range prefetches.
   const int xf = wrapi(x0 - R * T, nx);   // column of thread 0
   auto prefetch_block = [&](int sn) {
     const int wq = tid >> 5;
-    if (wq > 6) return;
-    int row0 = Y0 - R * T + sn - (wq >= 3 && wq < 6 ? R : 0);
-    row0 = wrapi(row0, ny);
-    const int nrows = (wq >= 3 && wq < 6) ? U + R : U;
-    const int nsamp = wq == 6 ? 17 : 9;        // columns 128 bytes apart, plus the last one
-    const int step = wq == 6 ? 16 : 32;
-    const char* base;
-    size_t esz;
-    if (wq < 3) { base = reinterpret_cast<const char*>(inA + E + wq * PPn); esz = 4; }
-    else if (wq < 6) { base = reinterpret_cast<const char*>(inA + (wq - 3) * PPn); esz = 4; }
-    else { base = reinterpret_cast<const char*>(kbm); esz = 8; }
-    for (int i = tid & 31; i < nrows * nsamp; i += 32) {
-      const int j = i / nsamp, c = i - j * nsamp;
+    if (wq > 5) return;   // warps 6 and 7 issue none
+    const int row0 = wrapi(Y0 - R * T + sn - (wq >= 3 ? R : 0), ny);
+    const float* base = wq < 3 ? inA + E + wq * PPn : inA + (wq - 3) * PPn;
+    constexpr int kSamp = 9;   // columns 32 floats (one line) apart, plus the last one
+    for (int i = tid & 31; i < U * kSamp; i += 32) {
+      const int j = i / kSamp, c = i - j * kSamp;
       int row = row0 + j;
       if (row >= ny) row -= ny;
-      const int col = (xf + (c + 1 < nsamp ? c * step : kThreads - 1)) % nx;
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((size_t)row * nx + col) * esz));
+      const int col = (xf + (c + 1 < kSamp ? c * 32 : kThreads - 1)) % nx;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (size_t)row * nx + col));
     }
   };
   fetch();
@@ -323,24 +318,24 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
         if (!pd.last) {
           if (t == T - 1 && stT1) {
             float* o = outA + (eo + R * nx);
-            __stcg(o, np);
-            __stcg(o + PPn, nu);
-            __stcg(o + 2 * PPn, nv);
+            __stcs(o, np);
+            __stcs(o + PPn, nu);
+            __stcs(o + 2 * PPn, nv);
           }
           if (t == T && stT) {
             float* o = outA + E + eo;
-            __stcg(o, np);
-            __stcg(o + PPn, nu);
-            __stcg(o + 2 * PPn, nv);
+            __stcs(o, np);
+            __stcs(o + PPn, nu);
+            __stcs(o + 2 * PPn, nv);
           }
         } else if (t == T && stT) {
           // y_(N-1) = previous, y_N = level T-1 at this row, y_(N+1) = new
           const float2 cpv = w[T - 1][r];
           const float cu = lvl[((T - 1) * U + r) * kRow].y;
           float* o = outA + eo;
-          __stcg(o, gragg_avg(ppv.x, cpv.x, np));
-          __stcg(o + PPn, gragg_avg(pu, cu, nu));
-          __stcg(o + 2 * PPn, gragg_avg(ppv.y, cpv.y, nv));
+          __stcs(o, gragg_avg(ppv.x, cpv.x, np));
+          __stcs(o + PPn, gragg_avg(pu, cu, nu));
+          __stcs(o + 2 * PPn, gragg_avg(ppv.y, cpv.y, nv));
         }
       }
       eo += nx;
@@ -398,30 +393,65 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P)
 // error is about 2^-48 of sum_k |c_k y*_k| -- FP64-class -- while using only FP32 units
 // (GB300 runs FP64 at a small fraction of the FP32 rate; a plain FP64 sum of 11 terms
 // per element would saturate that pipe).
-__global__ void k_combine(const ProbDev* probs, int batch, const SlotDev* slots, const float* __restrict__ ystar,
-                          int64_t E, float* __restrict__ y_out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = batch - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (probs[mid].state_off <= e) lo = mid;
-      else hi = mid - 1;
+__device__ __forceinline__ void combine_add(float c_hi, float c_lo, float y, float& sh, float& sl) {
+  // _rn intrinsics keep the compiler from contracting these into FMAs
+  const float p = __fmul_rn(c_hi, y);
+  const float pe = fmaf(c_lo, y, fmaf(c_hi, y, -p));   // c_hi*y - p exactly, plus c_lo*y
+  const float t = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(t, sh);
+  const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  sl = __fadd_rn(sl, __fadd_rn(te, pe));
+  sh = __fadd_rn(t, sl);
+  sl = __fsub_rn(sl, __fsub_rn(sh, t));
+}
+
+__device__ __forceinline__ int problem_of(const ProbDev* probs, int batch, int64_t e) {
+  int lo = 0, hi = batch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].state_off <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Four consecutive elements per thread: the loads of all sequences are issued before the sums
+// (float4 when the group is 16-byte aligned and inside one problem, else element by element).
+__global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch, const SlotDev* slots,
+                                                 const float* __restrict__ ystar, int64_t E,
+                                                 float* __restrict__ y_out) {
+  const int64_t groups = (E + 3) / 4;
+  // float4 access needs E % 4 == 0 (sequence blocks and y_out groups 16-byte aligned; ystar is
+  // a library allocation) and a 16-byte aligned caller buffer
+  const bool vec = (E % 4) == 0 && (reinterpret_cast<uintptr_t>(y_out) & 15) == 0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = 4 * g;
+    const int q0 = problem_of(probs, batch, e0);
+    const int64_t e3 = e0 + 3 < E ? e0 + 3 : E - 1;
+    if (vec && (q0 + 1 >= batch || probs[q0 + 1].state_off > e3)) {
+      const SlotDev& s = slots[probs[q0].slot];
+      float4 y[GBS_MAX_SEQ];
+#pragma unroll
+      for (int k = 0; k < GBS_MAX_SEQ; ++k)
+        if (k < s.m) y[k] = __ldcs(reinterpret_cast<const float4*>(ystar + (int64_t)k * E + e0));
+      float4 sh = make_float4(0.f, 0.f, 0.f, 0.f), sl = sh;
+#pragma unroll
+      for (int k = 0; k < GBS_MAX_SEQ; ++k)
+        if (k < s.m) {
+          combine_add(s.chi[k], s.clo[k], y[k].x, sh.x, sl.x);
+          combine_add(s.chi[k], s.clo[k], y[k].y, sh.y, sl.y);
+          combine_add(s.chi[k], s.clo[k], y[k].z, sh.z, sl.z);
+          combine_add(s.chi[k], s.clo[k], y[k].w, sh.w, sl.w);
+        }
+      *reinterpret_cast<float4*>(y_out + e0) = make_float4(sh.x + sl.x, sh.y + sl.y, sh.z + sl.z, sh.w + sl.w);
+    } else {
+      for (int64_t e = e0; e <= e3; ++e) {
+        const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
+        float sh = 0.f, sl = 0.f;
+        for (int k = 0; k < s.m; ++k) combine_add(s.chi[k], s.clo[k], __ldcs(ystar + (int64_t)k * E + e), sh, sl);
+        y_out[e] = sh + sl;
+      }
     }
-    const SlotDev& s = slots[probs[lo].slot];
-    float sh = 0.f, sl = 0.f;
-    for (int k = 0; k < s.m; ++k) {
-      const float y = __ldcg(ystar + (int64_t)k * E + e);
-      // _rn intrinsics keep the compiler from contracting these into FMAs
-      const float p = __fmul_rn(s.chi[k], y);
-      const float pe = fmaf(s.clo[k], y, fmaf(s.chi[k], y, -p));   // chi*y - p exactly, plus clo*y
-      const float t = __fadd_rn(sh, p);
-      const float bv = __fsub_rn(t, sh);
-      const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-      sl = __fadd_rn(sl, __fadd_rn(te, pe));
-      sh = __fadd_rn(t, sl);
-      sl = __fsub_rn(sl, __fsub_rn(sh, t));
-    }
-    y_out[e] = sh + sl;
   }
 }
 
@@ -474,12 +504,12 @@ void free_work(FusedWork* w) {
   w->lev_cap = w->ystar_cap = w->items_cap = 0;
 }
 
-// Leap-frog levels of sequence N split into passes: first N mod kTMax (if nonzero), then kTMax each.
-std::vector<int> pass_plan(int N) {
+// Leap-frog levels of sequence N split into passes: first N mod tmax (if nonzero), then tmax each.
+std::vector<int> pass_plan(int N, int tmax) {
   std::vector<int> v;
-  int rem = N % fused::kTMax;
+  int rem = N % tmax;
   if (rem) v.push_back(rem);
-  for (int l = rem; l < N; l += fused::kTMax) v.push_back(fused::kTMax);
+  for (int l = rem; l < N; l += tmax) v.push_back(tmax);
   return v;
 }
 
@@ -509,6 +539,8 @@ bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
 
 FusedWork* fused_create() { return new FusedWork(); }
 
+int fused_max_levels() { return fused::kTMax; }
+
 void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait) {
   w->spin_limit = spin_limit;
   w->inject_wait = inject_wait;
@@ -535,9 +567,14 @@ static int grow(T** p, size_t* cap, size_t bytes) {
   return 0;
 }
 
-int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h, int hseg,
-                  char* msg, size_t msglen) {
+int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h,
+                  const FusedTune& tune, char* msg, size_t msglen) {
   using namespace fused;
+  const int hseg = tune.hseg, tmax = tune.tmax;
+  if (tmax < 2 || tmax > kTMax || tmax % 2) {
+    std::snprintf(msg, msglen, "tmax must be even and in [2, %d]", kTMax);
+    return -1;
+  }
   w->E = p.state_elems;
   w->R = p.R;
   w->hseg = hseg;
@@ -547,7 +584,7 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   std::memset(pdesc.data(), 0, pdesc.size() * sizeof(PassDesc));
   for (int sl = 0; sl < GBS_MAX_SLOTS; ++sl)
     for (int k = 0; k < slots_h[sl].m; ++k) {
-      const std::vector<int> pl = pass_plan(slots_h[sl].steps[k]);
+      const std::vector<int> pl = pass_plan(slots_h[sl].steps[k], tmax);
       for (size_t qq = 0; qq < pl.size(); ++qq) {
         PassDesc& d = pdesc[((size_t)sl * GBS_MAX_SEQ + k) * kMaxPasses + qq];
         d.T = pl[qq];
@@ -562,19 +599,25 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   };
   std::vector<Key> keys;
   for (int q = 0; q < p.batch; ++q) {
-    tg[q] = tiles_of(probs_h[q].n[0], probs_h[q].n[1], hseg, p.R * kTMax);
+    tg[q] = tiles_of(probs_h[q].n[0], probs_h[q].n[1], hseg, p.R * tmax);
     const SlotDev& s = slots_h[probs_h[q].slot];
     for (int k = 0; k < s.m; ++k) {
-      const int np = (int)pass_plan(s.steps[k]).size();
+      const int np = (int)pass_plan(s.steps[k], tmax).size();
       for (int qq = 0; qq < np; ++qq)
         for (int t = 0; t < tg[q].nst * tg[q].nseg; ++t) keys.push_back({np - qq, q, k, qq, t});
     }
   }
-  std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
-    if (a.depth != b.depth) return a.depth > b.depth;
-    if (a.pass != b.pass) return a.pass < b.pass;
-    return false;
-  });
+  // every item's dependencies (same sequence, previous pass) come earlier in either order
+  if (tune.schedule == 0)
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+      if (a.depth != b.depth) return a.depth > b.depth;
+      return a.pass < b.pass;
+    });
+  else
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+      if (a.pass != b.pass) return a.pass < b.pass;
+      return a.depth > b.depth;
+    });
   const int n = (int)keys.size();
   std::vector<Item> items(n);
   std::vector<int> index_of;  // (prob, seq, pass, tile) -> item index via map
@@ -585,7 +628,7 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
     for (int q = 0; q < p.batch; ++q) {
       const SlotDev& s = slots_h[probs_h[q].slot];
       for (int k = 0; k < s.m; ++k) {
-        const int np = (int)pass_plan(s.steps[k]).size();
+        const int np = (int)pass_plan(s.steps[k], tmax).size();
         for (int qq = 0; qq < np; ++qq) {
           base[((size_t)q * GBS_MAX_SEQ + k) * kMaxPasses + qq] = off;
           off += tg[q].nst * tg[q].nseg;

@@ -43,7 +43,8 @@ inline void split_weights(SlotDev& s) {
 
 // Everything a macro-step launcher needs (device pointers except where noted).
 struct StepPlan {
-  int system, ndim, R, f64;    // f64: 1 = GBS_F64 path, 0 = FP32 state
+  int system, ndim, R, f64;    // f64: 1 = FP64 states and media in the API (GBS_F64, GBS_F32X2)
+  int ds;                      // 1 = GBS_F32X2: levels and right-hand sides in FP32 pairs
   int F;
   int batch;
   const ProbDev* probs;
@@ -54,6 +55,7 @@ struct StepPlan {
   int64_t total_blocks;        // point-parallel blocks over the whole batch
   int64_t total_tiles;         // x-y tiled blocks over the whole batch (2D/3D)
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
+  int64_t probs_media_elems;   // scalars in one media array (sum of pts)
   const void* kappa;           // media (state element type)
   const void* b;               // 1 / rho
   void* f0;                    // shared first RHS, F x P
@@ -64,6 +66,10 @@ struct StepPlan {
   // y_in and the media as interleaved (kappa, b) pairs
   float* f0_ycopy;
   float2* f0_kb;
+  // GBS_F32X2 workspace: y_in, kappa and b converted to FP32 pairs at the start of a step
+  void* ds_y0;
+  void* ds_kappa;
+  void* ds_b;
   // host-side schedule: for sequence index k, the largest step count over problems
   int max_m;
   int max_steps_k[GBS_MAX_SEQ];
@@ -124,8 +130,17 @@ FusedWork* fused_create();
 void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait);
 void fused_destroy(FusedWork* w);
 bool fused_supported(const StepPlan& p, const ProbDev* probs_h);
-int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h, int hseg,
-                  char* msg, size_t msglen);
+// Tunable shape of the time-blocked schedule: row-segment height of a tile, the most leap-frog
+// levels per pass (even, 2..4), and the queue order (0: longest remaining chain of passes
+// first; 1: pass by pass, all sequences' first passes first).
+struct FusedTune {
+  int hseg;
+  int tmax;
+  int schedule;
+};
+int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h,
+                  const FusedTune& tune, char* msg, size_t msglen);
+int fused_max_levels();   // largest tmax the kernel was compiled for
 int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err);
 
 // Adjoint of one macro-step with stored forward levels (plain kernels).

@@ -14,10 +14,24 @@
 // no step (k, n) leaves the launch at once.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "gbs_ds.cuh"
 #include "gbs_internal.h"
 #include "gbs_stencil.cuh"
 
 namespace gbs {
+
+// Element type of the caller's output state for a level type: FP32 pairs hand back FP64.
+template <typename T>
+struct out_of {
+  using type = T;
+};
+template <>
+struct out_of<dsf> {
+  using type = double;
+};
+
 namespace {
 
 struct Loc {
@@ -102,7 +116,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* _
   T* f0 = static_cast<T*>(p.f0) + q.state_off;
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) f0[fl * q.pts + L.i] = f[fl];
-  if (SYS == SYS_ACOUSTIC && sizeof(T) == 4) {
+  if constexpr (SYS == SYS_ACOUSTIC && std::is_same<T, float>::value) {
     if (p.f0_ycopy) {
       float* yc = p.f0_ycopy + q.state_off;
 #pragma unroll
@@ -133,7 +147,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* _
 }
 
 template <typename T, int SYS, int DIM, int R>
-__global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y_in, T* y_out, int k, int n) {
+__global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out,
+                                                     int k, int n) {
   const Loc L = locate(p);
   if (L.prob < 0) return;
   const ProbDev& q = p.probs[L.prob];
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   const double c = s.c[k];
   const bool first = (k == 0), last = (k == s.m - 1);
   double* acc = p.acc + q.state_off;
-  T* yo = y_out + q.state_off;
+  auto* yo = y_out + q.state_off;
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) {
     const int64_t e = fl * q.pts + L.i;
@@ -181,7 +196,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const T yp = ym + h2 * f[fl];
     const double ys = (double)gragg_avg(ym, y0, yp);
     const double a = first ? c * ys : fma(c, ys, acc[e]);
-    if (last) yo[e] = T(a);
+    if (last) yo[e] = static_cast<typename out_of<T>::type>(a);
     else acc[e] = a;
   }
 }
@@ -200,7 +215,8 @@ __device__ __forceinline__ int wrap_any(int a, int n) {
 }
 
 template <typename T, int DIM, int R>
-__global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_in, T* y_out, int k, int n) {
+__global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out,
+                                                   int k, int n) {
   constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
   __shared__ T sh[3][Hh][W + 1];
   // problem of this block (binary search over the tiled-grid offsets)
@@ -297,7 +313,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
       for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
     } else {
       double* acc = p.acc + q.state_off;
-      T* yo = y_out + q.state_off;
+      auto* yo = y_out + q.state_off;
 #pragma unroll
       for (int fl = 0; fl < F; ++fl) {
         const int64_t e = fl * P + pt;
@@ -306,7 +322,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
         const T yp = ym + h2 * f[fl];
         const double ys = (double)gragg_avg(ym, yc, yp);
         const double a2 = first ? c * ys : fma(c, ys, acc[e]);
-        if (last) yo[e] = T(a2);
+        if (last) yo[e] = static_cast<typename out_of<T>::type>(a2);
         else acc[e] = a2;
       }
     }
@@ -491,7 +507,7 @@ __global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid, int6
 template <typename T, int SYS, int DIM, int R>
 int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStream_t st) {
   const T* y_in = static_cast<const T*>(y_in_v);
-  T* y_out = static_cast<T*>(y_out_v);
+  auto* y_out = static_cast<typename out_of<T>::type*>(y_out_v);
   const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
   int launches = 0;
   k_f0<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in);
@@ -614,7 +630,29 @@ int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s) {
   return p.f64 ? f0_sys<double>(p, y_in, s) : f0_sys<float>(p, y_in, s);
 }
 
+// FP64 -> FP32 pairs (nearest pair) for the GBS_F32X2 path
+__global__ void k_to_ds(const double* __restrict__ a, dsf* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = dsf(a[i]);
+}
+
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
+  if (p.ds) {
+    // the step reads y_in, kappa and b as FP32 pairs converted here, and writes FP64 y_out
+    k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(y_in), static_cast<dsf*>(p.ds_y0), p.state_elems);
+    int extra = 1;
+    StepPlan q = p;
+    if (p.system == GBS_ACOUSTIC) {
+      const int64_t m = p.probs_media_elems;
+      k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.kappa), static_cast<dsf*>(p.ds_kappa), m);
+      k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.b), static_cast<dsf*>(p.ds_b), m);
+      q.kappa = p.ds_kappa;
+      q.b = p.ds_b;
+      extra += 2;
+    }
+    const int l = macro_step_sys<dsf>(q, p.ds_y0, y_out, s);
+    return l < 0 ? l : l + extra;
+  }
   return p.f64 ? macro_step_sys<double>(p, y_in, y_out, s) : macro_step_sys<float>(p, y_in, y_out, s);
 }
 

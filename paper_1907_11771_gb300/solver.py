@@ -9,7 +9,7 @@ import torch
 from . import binding as B
 from .schemes import Scheme
 
-_DTYPES = {B.GBS_F32_STATE_F64_COMBINE: torch.float32, B.GBS_F64: torch.float64}
+_DTYPES = {B.GBS_F32_STATE_F64_COMBINE: torch.float32, B.GBS_F64: torch.float64, B.GBS_F32X2: torch.float64}
 
 
 class GBSSolver:
@@ -22,6 +22,8 @@ class GBSSolver:
         self.ndim = 1 if system == B.GBS_WAVE1D else max(1, len(shapes[0]))
         self.batch = len(self.shapes)
         self.precision = precision
+        self.fd_order = fd_order
+        self.slots = [0] * len(shapes)
         self.dtype = _DTYPES[precision]
         self.F = 2 if system == B.GBS_WAVE1D else 1 + self.ndim
         self.pb = B.make_problem(system, self.ndim, fd_order, precision, self.shapes, dx, enable_adjoint)
@@ -55,6 +57,7 @@ class GBSSolver:
 
     def assign_slots(self, slots):
         B.gbs_assign_slots(self.h, slots)
+        self.slots = [int(v) for v in slots]
 
     def stability_limit(self):
         return B.gbs_stability_limit(self.h, self.batch)
@@ -91,6 +94,9 @@ class GBSSolver:
 
     def set_option(self, name, value):
         B.gbs_set_option(self.h, name, value)
+
+    def get_option(self, name):
+        return B.gbs_get_option(self.h, name)
 
     def uses_fused(self):
         return B.gbs_get_option(self.h, "kernel_in_use") == B.GBS_KERNEL_FUSED

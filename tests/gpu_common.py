@@ -50,7 +50,7 @@ class AcousticCase:
         self.ndim = len(self.shape)
         self.order = order
         self.precision = precision
-        self.np_dtype = np.float64 if precision == B.GBS_F64 else np.float32
+        self.np_dtype = np.float32 if precision == B.GBS_F32_STATE_F64_COMBINE else np.float64
         sigma = sigma if sigma is not None else max(2.0, min(self.shape) / 8.0)
         y0, kappa, rho = inputs.acoustic_problem(self.shape, seed, n_gauss, sigma, const_rho=const_rho)
         # smooth non-zero velocities (seeded Gaussian bumps) exercise every term of the operator
@@ -66,7 +66,7 @@ class AcousticCase:
         self.shape_xyz = tuple(reversed(self.shape))
 
     def solver(self, enable_adjoint=False):
-        dt = torch.float64 if self.precision == B.GBS_F64 else torch.float32
+        dt = torch.float32 if self.precision == B.GBS_F32_STATE_F64_COMBINE else torch.float64
         self.t_kappa = torch.tensor(self.kappa.ravel(), dtype=dt, device="cuda")
         self.t_rho = torch.tensor(self.rho.ravel(), dtype=dt, device="cuda")
         return GBSSolver(B.GBS_ACOUSTIC, [self.shape_xyz], [tuple(self.dx)], fd_order=self.order,
@@ -86,7 +86,7 @@ class AcousticCase:
         return OG.gbs_run(self.f, self.y0, H, steps, c, n_macro)
 
     def gpu_run(self, solver, H, n_macro):
-        dt = torch.float64 if self.precision == B.GBS_F64 else torch.float32
+        dt = torch.float32 if self.precision == B.GBS_F32_STATE_F64_COMBINE else torch.float64
         y = torch.tensor(self.y0.ravel(), dtype=dt, device="cuda")
         out = torch.empty_like(y)
         solver.step(y, out, H, n_macro)

@@ -1,0 +1,54 @@
+"""Host logic of the schedule autotuner: search, selection, cache write and reuse (a fake
+solver and a fake timer; no GPU)."""
+import json
+
+from paper_1907_11771_gb300 import autotune as A
+
+
+class FakeSolver:
+    def __init__(self, fused=True):
+        self.opts = {"hseg": 256, "tmax": 4, "schedule": 0}
+        self.fused = fused
+
+    def uses_fused(self):
+        return self.fused
+
+    def set_option(self, k, v):
+        self.opts[k] = v
+
+
+def _cost(o):
+    return abs(o["hseg"] - 192) / 100.0 + (0.5 if o["tmax"] == 2 else 0.0) + 0.1 * o["schedule"]
+
+
+def test_autotune_picks_the_fastest_applies_and_caches(tmp_path):
+    cache = str(tmp_path / "tune.json")
+    s = FakeSolver()
+    calls = []
+    timer = lambda: (calls.append(dict(s.opts)), _cost(s.opts))[1]
+    r = A.autotune(s, cache=cache, timer=timer, key="w1")
+    assert not r["cached"]
+    assert r["options"] == {"hseg": 192, "tmax": 4, "schedule": 0}
+    assert s.opts == r["options"]
+    space = A.DEFAULT_SPACE
+    assert len(calls) == len(space["hseg"]) * len(space["tmax"]) * len(space["schedule"])
+    assert len({json.dumps(c, sort_keys=True) for c in calls}) == len(calls)   # every candidate once
+    with open(cache) as f:
+        assert json.load(f)["w1"]["options"] == r["options"]
+    # same key: applied from the cache without timing
+    s2, calls2 = FakeSolver(), []
+    r2 = A.autotune(s2, cache=cache, timer=lambda: (calls2.append(1), 0.0)[1], key="w1")
+    assert r2["cached"] and not calls2 and s2.opts == r["options"]
+    # another key, a restricted space, and a forced re-tune
+    s3 = FakeSolver()
+    r3 = A.autotune(s3, space={"hseg": [64, 512], "tmax": [4], "schedule": [1]}, cache=cache,
+                    timer=lambda: _cost(s3.opts), key="w2")
+    assert r3["options"] == {"hseg": 64, "tmax": 4, "schedule": 1}
+    r4 = A.autotune(FakeSolver(), cache=cache, timer=lambda: 1.0, key="w1", retune=True)
+    assert not r4["cached"]
+    with open(cache) as f:
+        assert set(json.load(f)) == {"w1", "w2"}
+
+
+def test_autotune_skips_problems_without_the_time_blocked_kernel(tmp_path):
+    assert A.autotune(FakeSolver(fused=False), cache=str(tmp_path / "t.json"), timer=lambda: 1.0, key="k") is None

@@ -59,6 +59,11 @@ def test_invalid_problems_rejected_without_gpu(libpath):
     pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F64, [(16, 16, 2)], [(1.0, 1.0, 1.0)])
     with pytest.raises(B.GbsError):
         B.gbs_create(pb)
+    # an unknown precision
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, 3, [(16, 16, 1)], [(1.0, 1.0, 1.0)])
+    with pytest.raises(B.GbsError):
+        B.gbs_create(pb)
+    assert B.gbs_state_elems(pb) == 0
     # wave system with media is refused before any device call
     pb = B.make_problem(B.GBS_WAVE1D, 1, 4, B.GBS_F64, [(16,)], [(1.0,)])
     with pytest.raises(B.GbsError):
@@ -76,6 +81,10 @@ def test_state_and_workspace_sizes(libpath):
     pb3 = B.make_problem(B.GBS_ACOUSTIC, 3, 4, B.GBS_F64, [(8, 9, 10)], [(1, 1, 1)], enable_adjoint=True)
     assert B.gbs_state_elems(pb3) == 4 * 8 * 9 * 10
     assert B.gbs_workspace_bytes(pb3, 22) > B.gbs_workspace_bytes(pb3, 2)
+    # FP32-pair precision: FP64-sized levels plus pair copies of y_in, kappa and b
+    pbx = B.make_problem(B.GBS_ACOUSTIC, 2, 6, B.GBS_F32X2, [(128, 64)], [(1, 1)])
+    pbd = B.make_problem(B.GBS_ACOUSTIC, 2, 6, B.GBS_F64, [(128, 64)], [(1, 1)])
+    assert B.gbs_workspace_bytes(pbx, 22) == B.gbs_workspace_bytes(pbd, 22) + 8 * (3 + 2) * 128 * 64
 
 
 def test_product_scheme_table_matches_printed_values():
