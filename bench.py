@@ -288,8 +288,15 @@ def run_gpu(args):
     sol, y, H, upd_per_step, cfg = make_workload(args, rank)
     kernel = {"auto": B.GBS_KERNEL_AUTO, "plain": B.GBS_KERNEL_PLAIN, "fused": B.GBS_KERNEL_FUSED}[args.kernel]
     sol.set_option("kernel", kernel)
+    tuned = None
     if args.hseg:
         sol.set_option("hseg", args.hseg)
+    elif not args.no_autotune:
+        from paper_1907_11771_gb300 import autotune as AT
+        r = AT.autotune(sol, y, H, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
+        if r is not None:
+            tuned = {"options": r["options"], "from_cache": r["cached"], "macro_step_s": r["seconds"],
+                     "candidates": len(r.get("table", []))}
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
@@ -361,6 +368,8 @@ def run_gpu(args):
     line = None
     if rank == 0:
         fused = sol_kernel_is_fused(sol, B)
+        if tuned is not None:
+            cfg["autotuned_schedule"] = tuned
         cfg.update({"combine_dtype": ("f32 pairs (double-single, ~48-bit)" if fused else "f64"),
                     "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
                     "parallelism": f"replicas x{ws}"})
@@ -471,6 +480,8 @@ def main():
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default time-blocked schedule instead of autotuning it first")
     ap.add_argument("--time-to-solution", action="store_true",
                     help="run the time-to-1e-6 study (fused FP32 vs plain FP64) instead of the throughput bench")
     ap.add_argument("--tts-grid", type=int, default=1024)

@@ -66,3 +66,70 @@ __device__ __forceinline__ dsf gragg_avg(dsf ym, dsf y0, dsf yp) {
 }
 
 }  // namespace gbs
+
+namespace gbs {
+
+// Two independent pair values processed together with packed FP32-pair instructions
+// (f32x2): lane x is one value, lane y the other.  Same algorithms as dsf, lane by lane.
+struct ds2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// TwoSum lane by lane, then the low parts, then Fast2Sum
+__device__ __forceinline__ ds2 operator+(const ds2& a, const ds2& b) {
+  const float2 s = f2_add(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);
+  const float2 e = f2_add(f2_sub(a.hi, f2_sub(s, bb)), f2_sub(b.hi, bb));
+  const float2 t = f2_add(e, f2_add(a.lo, b.lo));
+  const float2 h = f2_add(s, t);
+  return ds2{h, f2_sub(t, f2_sub(h, s))};
+}
+__device__ __forceinline__ ds2 operator-(const ds2& a, const ds2& b) {
+  const float2 s = f2_sub(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);                 // the rounded -b.hi
+  const float2 e = f2_sub(f2_sub(a.hi, f2_sub(s, bb)), f2_add(b.hi, bb));
+  const float2 t = f2_add(e, f2_sub(a.lo, b.lo));
+  const float2 h = f2_add(s, t);
+  return ds2{h, f2_sub(t, f2_sub(h, s))};
+}
+
+// (value pair) times one pair constant c = chi + clo on both lanes (FMA TwoProd)
+__device__ __forceinline__ ds2 ds2_mul(const ds2& a, float chi, float clo) {
+  const float2 ch = make_float2(chi, chi), nch = make_float2(-chi, -chi);
+  const float2 q = __fmul2_rn(nch, a.hi);             // -(chi * a.hi) rounded
+  float2 e = __ffma2_rn(ch, a.hi, q);                 // its exact error
+  e = __ffma2_rn(ch, a.lo, e);
+  if (clo != 0.f) e = __ffma2_rn(make_float2(clo, clo), a.hi, e);
+  const float2 h = f2_sub(e, q);                       // p + e with p = -q
+  return ds2{h, f2_sub(e, f2_add(h, q))};
+}
+
+// lane-wise product with a per-lane pair multiplier (m.hi, m.lo lanes)
+__device__ __forceinline__ ds2 ds2_mul(const ds2& a, const ds2& m) {
+  const float2 nmh = make_float2(-m.hi.x, -m.hi.y);
+  const float2 q = __fmul2_rn(nmh, a.hi);
+  float2 e = __ffma2_rn(m.hi, a.hi, q);
+  e = __ffma2_rn(m.hi, a.lo, e);
+  e = __ffma2_rn(m.lo, a.hi, e);
+  const float2 h = f2_sub(e, q);
+  return ds2{h, f2_sub(e, f2_add(h, q))};
+}
+
+__device__ __forceinline__ dsf lane_x(const ds2& a) { return dsf(a.hi.x, a.lo.x); }
+__device__ __forceinline__ dsf lane_y(const ds2& a) { return dsf(a.hi.y, a.lo.y); }
+__device__ __forceinline__ ds2 make_ds2(dsf x, dsf y) { return ds2{make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+
+}  // namespace gbs

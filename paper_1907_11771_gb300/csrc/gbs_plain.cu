@@ -329,6 +329,143 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   }
 }
 
+// Tiled leap-frog step for 2D/3D acoustics in FP32 pairs (GBS_F32X2), two pair values per
+// packed instruction: the x-stencils of (p, u) and the y-stencils of (p, v) run lane by lane
+// on f32x2 (ds2).  The tile holds (p.hi, u.hi, p.lo, u.lo) and (p.hi, v.hi, p.lo, v.lo) per
+// point so that each stencil operand is one 16-byte shared load.  Same steps, averaging and
+// FP64 combine as k_lf_tiled.
+template <int R>
+__device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 2 * R + 1], int r, int cc, bool along_x) {
+  ds2 s{};
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const float4 a = along_x ? row[r][cc + j] : row[r + j][cc];
+    const float4 b = along_x ? row[r][cc - j] : row[r - j][cc];
+    const double c = fd_coef<R>(j);
+    const float chi = float(c), clo = float(c - double(float(c)));
+    const ds2 d = ds2_mul(ds2{make_float2(a.x, a.y), make_float2(a.z, a.w)} -
+                              ds2{make_float2(b.x, b.y), make_float2(b.z, b.w)},
+                          chi, clo);
+    s = j == 1 ? d : s + d;
+  }
+  return s;
+}
+
+template <int DIM, int R>
+__global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf* y_in, double* y_out, int k, int n) {
+  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
+  __shared__ float4 spu[Hh][W + 1];   // (p.hi, u.hi, p.lo, u.lo)
+  __shared__ float4 spv[Hh][W + 1];   // (p.hi, v.hi, p.lo, v.lo)
+  int lo = 0, hi = p.batch - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.probs[mid].tblk_begin <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const ProbDev& q = p.probs[lo];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  const int tile = (int)(blk - q.tblk_begin);
+  const int tx = tile % q.tiles_x;
+  const int rest = tile / q.tiles_x;
+  const int ty = rest % q.tiles_y;
+  const int z = rest / q.tiles_y;
+  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  const int64_t P = q.pts;
+  const int64_t plane = (int64_t)z * nx * ny;
+  dsf h, h2;
+  step_sizes(p, lo, k, h, h2);
+  dsf* const L0 = static_cast<dsf*>(p.L0) + q.state_off;
+  dsf* const L1 = static_cast<dsf*>(p.L1) + q.state_off;
+  const dsf* cur = (n & 1) ? L1 : L0;
+  dsf* dst = (n & 1) ? L0 : L1;
+  const dsf* prev = (n == 1) ? (y_in + q.state_off) : dst;
+  for (int r = threadIdx.y; r < Hh; r += 8) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    const dsf* rowp = cur + plane + (int64_t)gy * nx;
+    for (int c = threadIdx.x; c < W; c += kTileX) {
+      int gx = x0 - R + c;
+      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+      const dsf pp = ldg(rowp + gx), uu = ldg(rowp + P + gx), vv = ldg(rowp + 2 * P + gx);
+      spu[r][c] = make_float4(pp.hi, uu.hi, pp.lo, uu.lo);
+      spv[r][c] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
+    }
+  }
+  __syncthreads();
+  const bool unit = q.inv_dx[0] == 1.0 && q.inv_dx[1] == 1.0 && (DIM < 3 || q.inv_dx[2] == 1.0);
+  const dsf idx = dsf(q.inv_dx[0]), idy = dsf(q.inv_dx[1]), idz = dsf(q.inv_dx[2]);
+  const dsf* kap = static_cast<const dsf*>(p.kappa) + q.media_off;
+  const dsf* bmed = static_cast<const dsf*>(p.b) + q.media_off;
+  const int x = x0 + threadIdx.x;
+  if (x >= nx) return;
+  const double c = s.c[k];
+  const bool first = (k == 0), last = (k == s.m - 1);
+#pragma unroll
+  for (int i = 0; i < kTileRows; ++i) {
+    const int ly = threadIdx.y + 8 * i;
+    const int y = y0 + ly;
+    if (y >= ny) break;
+    const int r = ly + R, cc = threadIdx.x + R;
+    ds2 sx = xstencil2<R>(spu, r, cc, true);    // (D_x p, D_x u), unscaled
+    ds2 sy = xstencil2<R>(spv, r, cc, false);   // (D_y p, D_y v), unscaled
+    const int64_t pt = plane + (int64_t)y * nx + x;
+    ds2 sz{};                                    // (D_z p, D_z w), 3D only
+    if (DIM == 3) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const int zp = z + j >= nz ? z + j - nz : z + j;
+        const int zm = z - j < 0 ? z - j + nz : z - j;
+        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
+        const double cj = fd_coef<R>(j);
+        const ds2 d = make_ds2(ldg(cur + pt + op), ldg(cur + 3 * P + pt + op)) -
+                      make_ds2(ldg(cur + pt + om), ldg(cur + 3 * P + pt + om));
+        const ds2 t = ds2_mul(d, float(cj), float(cj - double(float(cj))));
+        sz = j == 1 ? t : sz + t;
+      }
+    }
+    if (!unit) {
+      sx = ds2_mul(sx, idx.hi, idx.lo);
+      sy = ds2_mul(sy, idy.hi, idy.lo);
+      if (DIM == 3) sz = ds2_mul(sz, idz.hi, idz.lo);
+    }
+    dsf div = lane_y(sx) + lane_y(sy);
+    if (DIM == 3) div += lane_y(sz);
+    const dsf kv = ldg(kap + pt), bv = ldg(bmed + pt);
+    const dsf fp = -(kv * div);
+    const ds2 fuv = ds2_mul(make_ds2(lane_x(sx), lane_x(sy)), make_ds2(-bv, -bv));   // (f_u, f_v)
+    dsf fw = dsf(0);
+    if (DIM == 3) fw = -(bv * lane_x(sz));
+    if (n < N) {
+      dst[pt] = prev[pt] + h2 * fp;
+      const ds2 nuv = make_ds2(prev[P + pt], prev[2 * P + pt]) + ds2_mul(fuv, h2.hi, h2.lo);
+      dst[P + pt] = lane_x(nuv);
+      dst[2 * P + pt] = lane_y(nuv);
+      if (DIM == 3) dst[3 * P + pt] = prev[3 * P + pt] + h2 * fw;
+    } else {
+      double* acc = p.acc + q.state_off;
+      double* yo = y_out + q.state_off;
+      const float4 a = spu[r][cc], b = spv[r][cc];
+      const dsf cur_f[4] = {dsf(a.x, a.z), dsf(a.y, a.w), dsf(b.y, b.w), DIM == 3 ? ldg(cur + 3 * P + pt) : dsf(0)};
+      const dsf f[4] = {fp, lane_x(fuv), lane_y(fuv), fw};
+#pragma unroll
+      for (int fl = 0; fl < 1 + DIM; ++fl) {
+        const int64_t e = fl * P + pt;
+        const dsf ym = prev[e];
+        const dsf yp = ym + h2 * f[fl];
+        const double ys = (double)gragg_avg(ym, cur_f[fl], yp);
+        const double a2 = first ? c * ys : fma(c, ys, acc[e]);
+        if (last) yo[e] = a2;
+        else acc[e] = a2;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint kernels (acoustics)
 // ---------------------------------------------------------------------------
@@ -517,7 +654,9 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
     ++launches;
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
       const int u = timing_begin(p, st);
-      if (SYS == SYS_ACOUSTIC && DIM >= 2)
+      if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
+        k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+      else if (SYS == SYS_ACOUSTIC && DIM >= 2)
         k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else
         k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
