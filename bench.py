@@ -46,6 +46,12 @@ def workload_desc(n=N_GRID, prec=0):
             f"{PREC_DESC[prec]}, H = {H_FRACTION} x stability limit")
 
 
+# DRAM bytes (read + write) of one time-blocked pass-kernel launch, from the ncu capture in
+# profiles/k_passes_2d2048.md (2D 2048^2, FP32, default schedule hseg 256, tmax 4, schedule 0).
+# It describes that kernel build only: set to None when the kernel changes until re-measured.
+PASSES_2D2048_TRAFFIC = 4.77e9 + 3.06e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -338,8 +344,14 @@ def run_gpu(args):
     sol.set_option("time_kernels", 0)
     peak, peak_kind = peaks()
     achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
+    traffic = None
+    if (PASSES_2D2048_TRAFFIC and args.workload == "2d" and args.grid == N_GRID and not (args.f64 or args.f32x2)
+            and sol_kernel_is_fused(sol, B)
+            and [sol.get_option(k) for k in ("hseg", "tmax", "schedule")] == [256, 4, 0]):
+        traffic = PASSES_2D2048_TRAFFIC
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "traffic_source": "profiles/k_passes_2d2048.md (ncu, same kernel and schedule)" if traffic else None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
             "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "tiled leap-frog step (k_lf_tiled)",
             "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
@@ -385,6 +397,114 @@ def run_gpu(args):
     sol.close()
     if ws > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_adjoint(args):
+    """Misfit-gradient throughput: one step = J and dJ/dkappa over M macro-steps (forward sweep with
+    a checkpoint every C, then the backward sweep recomputing each segment and running the
+    adjoint macro-steps), 2D acoustics n x n (default 1024^2), 4th-order FD, rho = 1, 16-Gaussian
+    kappa, Gaussian pressure source sigma = 8, 64 receivers on the row 3n/4, GBS_8,6 in FP32.
+    Counted work: M forward plus M adjoint macro-steps of P x 143 updates; the checkpoint
+    recomputation is overhead.  Observed data: a forward run of the same solver with a perturbed
+    kappa (kappa + 0.05 x one more seeded Gaussian)."""
+    import numpy as np
+    import torch
+
+    from paper_1907_11771_gb300 import binding as B
+    from paper_1907_11771_gb300 import build as Bld
+    from paper_1907_11771_gb300 import inputs
+    from paper_1907_11771_gb300 import schemes as S
+    from paper_1907_11771_gb300.autograd import gbs_misfit_and_grad
+    from paper_1907_11771_gb300.solver import GBSSolver
+
+    torch.cuda.set_device(0)
+    Bld.build()
+    n = args.grid if args.grid != N_GRID else 1024
+    M, C = args.adj_macro, args.adj_checkpoint
+    y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, 8.0, const_rho=True, dtype=np.float32)
+    bump = inputs.smooth_media((n, n), 1, 7, 1.0) - 1.0        # one more seeded Gaussian
+    tk = torch.tensor(kappa.ravel(), device="cuda")
+    tr = torch.tensor(rho.ravel(), device="cuda")
+    sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=4, precision=B.GBS_F32_STATE_F64_COMBINE,
+                    kappa=tk, rho=tr, enable_adjoint=True)
+    sol.set_scheme(S.GBS_8_6)
+    H = H_FRACTION * sol.stability_limit()[0]
+    rcv = torch.tensor(inputs.line_receivers(n, 64), device="cuda")
+    y = torch.tensor(y0.ravel(), device="cuda")
+    # observed data from the perturbed medium
+    k_true = torch.tensor((kappa + 0.05 * np.asarray(bump, dtype=np.float32)).ravel(), device="cuda")
+    sol.set_media(k_true, tr)
+    data = torch.empty(M, rcv.numel(), dtype=torch.float32, device="cuda")
+    yy = y.clone()
+    for m in range(M):
+        sol.step(yy, yy, H, 1)
+        data[m] = yy[rcv]
+    sol.set_media(tk, tr)
+    P = n * n
+    upd = 2 * M * P * S.GBS_8_6.updates_per_point
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+    torch.cuda.synchronize()
+    l0 = sol.kernel_launches
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record()
+            J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+            evs[i][1].record()
+        torch.cuda.synchronize()
+    launches = sol.kernel_launches - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = upd * args.steps / (ms / 1e3) / 1e9
+    # roofline of the adjoint's reverse leap-frog kernel: library events around its launches
+    lam = torch.zeros_like(y)
+    grad = torch.zeros(P, dtype=torch.float64, device="cuda")
+    sol.set_option("time_kernels", 1)
+    sol.kernel_time()
+    for i in range(3):
+        flush.fill_(float(i))
+        sol.adjoint_step(y, lam, lam, grad, H)
+    nl, kms, kbytes = sol.kernel_time()
+    sol.set_option("time_kernels", 0)
+    peak, peak_kind = peaks()
+    achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth", "kernel": "adjoint reverse leap-frog step (k_adj_rev)",
+            "algorithmic_bytes_per_launch": kbytes / nl if nl else None, "avg_launch_ms": kms / nl if nl else None}
+    # end to end: inputs from pinned host memory, gradient back to the host, every step
+    hy = y.cpu().pin_memory()
+    hk = tk.cpu().pin_memory()
+    hd = data.cpu().pin_memory()
+    hg = torch.empty(P, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        y.copy_(hy, non_blocking=True)
+        tk.copy_(hk, non_blocking=True)
+        data.copy_(hd, non_blocking=True)
+        J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+        hg.copy_(g, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e = {"value": upd * args.steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": hy.numel() * 4 + hk.numel() * 4 + hd.numel() * 4, "d2h_bytes_per_step": hg.numel() * 8}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"misfit gradient: 2D acoustics {n}x{n}, 4th-order FD, rho = 1, 64 receivers, "
+                                    f"GBS_8,6 FP32, {M} macro-steps, checkpoint every {C}; one step = forward + "
+                                    f"checkpointed backward; updates counted: {M} forward + {M} adjoint macro-steps"),
+                       "shapes": [[n, n]], "scheme": "GBS_8,6", "updates_per_step_per_gpu": upd,
+                       "macro_steps": M, "checkpoint_every": C, "misfit_J": J,
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas x1"},
+            "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
+    print(json.dumps(line), flush=True)
+    sol.close()
     return 0
 
 
@@ -474,8 +594,11 @@ def main():
     ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
     ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--workload", choices=["2d", "3d", "batch"], default="2d",
-                    help="2d (default, the headline workload), 3d (512^3) or batch (256 problems)")
+    ap.add_argument("--workload", choices=["2d", "3d", "batch", "adjoint"], default="2d",
+                    help="2d (default, the headline workload), 3d (512^3), batch (256 problems) or "
+                         "adjoint (misfit gradient, 1024^2)")
+    ap.add_argument("--adj-macro", type=int, default=100, help="macro-steps of one misfit gradient (adjoint workload)")
+    ap.add_argument("--adj-checkpoint", type=int, default=50, help="checkpoint interval (adjoint workload)")
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
@@ -494,6 +617,8 @@ def main():
         return run_reference(args)
     if args.time_to_solution:
         return run_time_to_solution(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_gpu(args)
 
 

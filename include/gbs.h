@@ -218,7 +218,9 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value);
 gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value);
 
 /* Launch count and summed device time (ms, CUDA events) of the dominant
- * kernel since the previous call, recorded while "time_kernels" is on; also
+ * kernel since the previous call, recorded while "time_kernels" is on (the
+ * forward step's leap-frog or pass kernel in gbs_step, the reverse leap-frog
+ * kernel in gbs_adjoint_step); also
  * reports the algorithmic bytes those launches move (*bytes, may be NULL), the
  * per-launch figure being the unit cost of the kernel times the grid-point
  * updates it performs.  Waits for the stream; resets the counters. */

@@ -81,6 +81,7 @@ struct StepPlan {
   int* tev_used;
   const int64_t* active_pts;   // [k * (GBS_MAX_STEPS + 1) + n]: points updated by step (k, n)
   double unit_bytes;           // algorithmic bytes per grid-point update of the dominant kernel
+  double adj_unit_bytes;       // the same for the adjoint's reverse step (k_adj_rev)
 };
 
 // Record the start of a timed launch; returns the slot index or -1.

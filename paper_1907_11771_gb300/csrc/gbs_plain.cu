@@ -352,7 +352,7 @@ __device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 2 * R + 1]
 }
 
 template <int DIM, int R>
-__global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf* y_in, double* y_out, int k, int n) {
+__global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const StepPlan p, const dsf* y_in, double* y_out, int k, int n) {
   constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
   __shared__ float4 spu[Hh][W + 1];   // (p.hi, u.hi, p.lo, u.lo)
   __shared__ float4 spv[Hh][W + 1];   // (p.hi, v.hi, p.lo, v.lo)
@@ -396,12 +396,25 @@ __global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf
       spv[r][c] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
     }
   }
-  __syncthreads();
-  const bool unit = q.inv_dx[0] == 1.0 && q.inv_dx[1] == 1.0 && (DIM < 3 || q.inv_dx[2] == 1.0);
-  const dsf idx = dsf(q.inv_dx[0]), idy = dsf(q.inv_dx[1]), idz = dsf(q.inv_dx[2]);
   const dsf* kap = static_cast<const dsf*>(p.kappa) + q.media_off;
   const dsf* bmed = static_cast<const dsf*>(p.b) + q.media_off;
   const int x = x0 + threadIdx.x;
+  // point-wise operands of a row (previous level, media), loaded one row ahead of their use;
+  // the first row's before the tile barrier
+  dsf nprev[4], nkv, nbv;
+  auto fetch_row = [&](int i) {
+    const int y = y0 + threadIdx.y + 8 * i;
+    if (x >= nx || y >= ny) return;
+    const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+    for (int fl = 0; fl < 1 + DIM; ++fl) nprev[fl] = ldg(prev + fl * P + pt);
+    nkv = ldg(kap + pt);
+    nbv = ldg(bmed + pt);
+  };
+  fetch_row(0);
+  __syncthreads();
+  const bool unit = q.inv_dx[0] == 1.0 && q.inv_dx[1] == 1.0 && (DIM < 3 || q.inv_dx[2] == 1.0);
+  const dsf idx = dsf(q.inv_dx[0]), idy = dsf(q.inv_dx[1]), idz = dsf(q.inv_dx[2]);
   if (x >= nx) return;
   const double c = s.c[k];
   const bool first = (k == 0), last = (k == s.m - 1);
@@ -411,6 +424,11 @@ __global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf
     const int y = y0 + ly;
     if (y >= ny) break;
     const int r = ly + R, cc = threadIdx.x + R;
+    dsf pv[4];
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) pv[fl] = nprev[fl];
+    const dsf kv = nkv, bv = nbv;
+    if (i + 1 < kTileRows) fetch_row(i + 1);
     ds2 sx = xstencil2<R>(spu, r, cc, true);    // (D_x p, D_x u), unscaled
     ds2 sy = xstencil2<R>(spv, r, cc, false);   // (D_y p, D_y v), unscaled
     const int64_t pt = plane + (int64_t)y * nx + x;
@@ -435,17 +453,16 @@ __global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf
     }
     dsf div = lane_y(sx) + lane_y(sy);
     if (DIM == 3) div += lane_y(sz);
-    const dsf kv = ldg(kap + pt), bv = ldg(bmed + pt);
     const dsf fp = -(kv * div);
     const ds2 fuv = ds2_mul(make_ds2(lane_x(sx), lane_x(sy)), make_ds2(-bv, -bv));   // (f_u, f_v)
     dsf fw = dsf(0);
     if (DIM == 3) fw = -(bv * lane_x(sz));
     if (n < N) {
-      dst[pt] = prev[pt] + h2 * fp;
-      const ds2 nuv = make_ds2(prev[P + pt], prev[2 * P + pt]) + ds2_mul(fuv, h2.hi, h2.lo);
+      dst[pt] = pv[0] + h2 * fp;
+      const ds2 nuv = make_ds2(pv[1], pv[2]) + ds2_mul(fuv, h2.hi, h2.lo);
       dst[P + pt] = lane_x(nuv);
       dst[2 * P + pt] = lane_y(nuv);
-      if (DIM == 3) dst[3 * P + pt] = prev[3 * P + pt] + h2 * fw;
+      if (DIM == 3) dst[3 * P + pt] = pv[3] + h2 * fw;
     } else {
       double* acc = p.acc + q.state_off;
       double* yo = y_out + q.state_off;
@@ -455,7 +472,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled_x2(const StepPlan p, const dsf
 #pragma unroll
       for (int fl = 0; fl < 1 + DIM; ++fl) {
         const int64_t e = fl * P + pt;
-        const dsf ym = prev[e];
+        const dsf ym = pv[fl];
         const dsf yp = ym + h2 * f[fl];
         const double ys = (double)gragg_avg(ym, cur_f[fl], yp);
         const double a2 = first ? c * ys : fma(c, ys, acc[e]);
@@ -692,7 +709,10 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
       ++launches;
     }
     for (int t = 0; t <= Nk; ++t) {
+      const int u = t > 0 ? timing_begin(p, st) : -1;
       k_adj_rev<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, lam_out, mA, mB, grad, k, t);
+      if (t > 0)
+        timing_end(p, u, st, p.tev ? p.adj_unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + t] : 0.0);
       ++launches;
     }
     k_adj_gather<T, DIM><<<grid, block, 0, st>>>(p, mA, mB, shared, k);
