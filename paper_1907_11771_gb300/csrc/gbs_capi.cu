@@ -47,7 +47,7 @@ struct gbs_ctx {
   int ds = 0;                             // GBS_F32X2: FP32-pair levels and right-hand sides
   size_t esz = 4;                         // state element size
   std::vector<ProbDev> probs;
-  int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0;
+  int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0, total_sblocks = 0;
   std::vector<double> cmax;               // per problem max sqrt(kappa b)
   // media
   const void* kappa = nullptr;
@@ -81,6 +81,7 @@ struct gbs_ctx {
   void* mu0 = nullptr;
   void* mu1 = nullptr;
   void* mu_shared = nullptr;
+  float2* gpair = nullptr;                // FP32 path: per-sequence gradient sums as (hi, lo) pairs
   FusedWork* fw = nullptr;                // time-blocked path: schedule and level store
   bool fw_ready = false;
   // execution
@@ -210,7 +211,8 @@ void free_graphs(gbs_ctx* h) {
 void free_all(gbs_ctx* h) {
   free_graphs(h);
   void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
-                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa, h->ds_b};
+                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa, h->ds_b,
+                  h->gpair};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -358,6 +360,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->hkf = h->d_hkf;
   p->total_blocks = h->total_blocks;
   p->total_tiles = h->total_tiles;
+  p->total_sblocks = h->total_sblocks;
   p->state_elems = h->state_elems;
   p->kappa = h->kappa;
   p->b = h->b;
@@ -506,7 +509,10 @@ size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps) {
   bytes += 8 * s.state_elems;             // acc
   bytes += s.media_elems * esz;           // b
   if (pb->precision == GBS_F32X2) bytes += 8 * (s.state_elems + 2 * s.media_elems);   // pair copies
-  if (pb->enable_adjoint) bytes += (size_t)(max_steps + 2 + 3) * s.state_elems * esz;
+  if (pb->enable_adjoint) {
+    bytes += (size_t)(max_steps + 2 + 3) * s.state_elems * esz;
+    if (pb->precision == GBS_F32_STATE_F64_COMBINE) bytes += 8 * s.media_elems;   // gradient pairs
+  }
   bytes += sizeof(ProbDev) * pb->batch + sizeof(SlotDev) * GBS_MAX_SLOTS + 8 * pb->batch * 2 +
            8 * (4 * kNormBlocks + 4) + 64;
   return bytes;
@@ -556,7 +562,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   h->state_elems = soff;
   h->media_elems = moff;
   h->total_blocks = blk;
-  h->total_tiles = assign_tiles(h->probs.data(), h->batch, h->ndim);
+  h->total_tiles = assign_tiles(h->probs.data(), h->batch, h->ndim, &h->total_sblocks);
   if (blk > 0x7fffffff) {
     delete h;
     return fail(nullptr, GBS_ERR_INVALID, "problem too large for one launch grid");
@@ -592,6 +598,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
     if ((st = dalloc(h, &h->mu0, E * h->esz)) != GBS_OK) return bail(st);
     if ((st = dalloc(h, &h->mu1, E * h->esz)) != GBS_OK) return bail(st);
     if ((st = dalloc(h, &h->mu_shared, E * h->esz)) != GBS_OK) return bail(st);
+    if (!h->f64 && (st = dalloc(h, &h->gpair, P * sizeof(float2))) != GBS_OK) return bail(st);
   }
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
     fail(h, GBS_ERR_CUDA, "cudaStreamCreate failed");
@@ -825,6 +832,7 @@ gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out,
   a.mu0 = h->mu0;
   a.mu1 = h->mu1;
   a.shared = h->mu_shared;
+  a.gpair = h->gpair;
   a.max_steps = h->levels_steps;
   a.rcv_pts = h->probs[0].pts;
   a.err = h->d_err;

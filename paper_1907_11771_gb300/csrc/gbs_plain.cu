@@ -329,6 +329,144 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   }
 }
 
+// 3D leap-frog step for FP32 acoustics, streaming along z (2.5D blocking).  A block of 32 x 8
+// threads owns a 32 x 16 x-y tile (2 rows per thread) and a chunk of up to kZChunk planes.  It
+// walks z keeping the last 2R+1 planes of p and w of its own columns in registers (the
+// z-stencils; compile-time slots, the walk unrolled by 2R+1) and stages each plane's p, u, v
+// with the x-y halo in shared memory (the x- and y-stencils).  Every point is loaded once per
+// plane instead of once per z-neighbour.  Same arithmetic, averaging and FP64 combine as
+// k_lf_tiled.
+template <int R>
+__global__ void __launch_bounds__(256) k_lf_stream3d(const StepPlan p, const float* y_in, float* y_out, int k, int n) {
+  constexpr int U = 2 * R + 1;
+  constexpr int OFF = 64 * U;
+  constexpr int RPT = kSTileY / 8;
+  constexpr int W = kTileX + 2 * R, Hh = kSTileY + 2 * R;
+  __shared__ float sp[Hh][W + 1], su[Hh][W + 1], sv[Hh][W + 1];
+  int lo = 0, hi = p.batch - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.probs[mid].sblk_begin <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const ProbDev& q = p.probs[lo];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  const int tile = (int)(blk - q.sblk_begin);
+  const int tx = tile % q.tiles_x;
+  const int rest = tile / q.tiles_x;
+  const int ty = rest % q.stiles_y;
+  const int zc = rest / q.stiles_y;
+  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
+  const int x0 = tx * kTileX, y0 = ty * kSTileY;
+  const int za = zc * kZChunk, zb = min(nz, za + kZChunk);
+  const int64_t P = q.pts, PL = (int64_t)nx * ny;
+  float h, h2;
+  step_sizes(p, lo, k, h, h2);
+  float* const L0 = static_cast<float*>(p.L0) + q.state_off;
+  float* const L1 = static_cast<float*>(p.L1) + q.state_off;
+  const float* cur = (n & 1) ? L1 : L0;
+  float* dst = (n & 1) ? L0 : L1;
+  const float* prev = (n == 1) ? (y_in + q.state_off) : dst;
+  const float* kap = static_cast<const float*>(p.kappa) + q.media_off;
+  const float* bmed = static_cast<const float*>(p.b) + q.media_off;
+  const float idx = float(q.inv_dx[0]), idy = float(q.inv_dx[1]), idz = float(q.inv_dx[2]);
+  const int x = x0 + threadIdx.x;
+  const bool xin = x < nx;
+  int yr[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) yr[i] = y0 + threadIdx.y + 8 * i;
+  float wp[RPT][U], ww[RPT][U];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int u = 0; u < U; ++u) wp[i][u] = ww[i][u] = 0.f;
+  const double c = s.c[k];
+  const bool first = (k == 0), last = (k == s.m - 1);
+  const int S = (zb - za) + 2 * R;   // plane loads: za - R .. zb + R - 1
+  for (int sb = 0; sb < S; sb += U) {
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) {
+      const int st = sb + uu;
+      if (st >= S) break;
+      int zl = za - R + st;                      // within [-R, nz + R): one wrap at most
+      if (zl < 0) zl += nz;
+      else if (zl >= nz) zl -= nz;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+        if (xin && yr[i] < ny) {
+          const int64_t e = (int64_t)zl * PL + (int64_t)yr[i] * nx + x;
+          wp[i][uu] = ldg(cur + e);
+          ww[i][uu] = ldg(cur + 3 * P + e);
+        }
+      if (st < 2 * R) continue;
+      const int z = za - 2 * R + st;             // the plane computed now, in [za, zb)
+      __syncthreads();                           // the previous plane's readers are done
+      for (int r = threadIdx.y; r < Hh; r += 8) {
+        int gy = y0 - R + r;
+        if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+        const float* rowp = cur + (int64_t)z * PL + (int64_t)gy * nx;
+        for (int cx = threadIdx.x; cx < W; cx += kTileX) {
+          int gx = x0 - R + cx;
+          if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+          sp[r][cx] = ldg(rowp + gx);
+          su[r][cx] = ldg(rowp + P + gx);
+          sv[r][cx] = ldg(rowp + 2 * P + gx);
+        }
+      }
+      __syncthreads();
+      if (!xin) continue;
+      const int sc = (uu + OFF - R) % U;         // window slot of plane z
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int y = yr[i];
+        if (y >= ny) continue;
+        const int rr = threadIdx.y + 8 * i + R, cc = threadIdx.x + R;
+        float sxp = 0.f, sxu = 0.f, syp = 0.f, syv = 0.f, szp = 0.f, szw = 0.f;
+#pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          const float a = float(fd_coef<R>(j));
+          sxp += a * (sp[rr][cc + j] - sp[rr][cc - j]);
+          sxu += a * (su[rr][cc + j] - su[rr][cc - j]);
+          syp += a * (sp[rr + j][cc] - sp[rr - j][cc]);
+          syv += a * (sv[rr + j][cc] - sv[rr - j][cc]);
+          szp += a * (wp[i][(uu + OFF - R + j) % U] - wp[i][(uu + OFF - R - j) % U]);
+          szw += a * (ww[i][(uu + OFF - R + j) % U] - ww[i][(uu + OFF - R - j) % U]);
+        }
+        const int64_t pt = (int64_t)z * PL + (int64_t)y * nx + x;
+        const float div = sxu * idx + syv * idy + szw * idz;
+        const float kv = ldg(kap + pt), bv = ldg(bmed + pt);
+        float f[4];
+        f[0] = -kv * div;
+        f[1] = -bv * (sxp * idx);
+        f[2] = -bv * (syp * idy);
+        f[3] = -bv * (szp * idz);
+        if (n < N) {
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
+        } else {
+          double* acc = p.acc + q.state_off;
+          float* yo = y_out + q.state_off;
+          const float ycur[4] = {sp[rr][cc], su[rr][cc], sv[rr][cc], ww[i][sc]};
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) {
+            const int64_t e = fl * P + pt;
+            const float ym = prev[e];
+            const float yp = ym + h2 * f[fl];
+            const double ys = (double)gragg_avg(ym, ycur[fl], yp);
+            const double a2 = first ? c * ys : fma(c, ys, acc[e]);
+            if (last) yo[e] = float(a2);
+            else acc[e] = a2;
+          }
+        }
+      }
+    }
+  }
+}
+
 // Tiled leap-frog step for 2D/3D acoustics in FP32 pairs (GBS_F32X2), two pair values per
 // packed instruction: the x-stencils of (p, u) and the y-stencils of (p, v) run lane by lane
 // on f32x2 (ds2).  The tile holds (p.hi, u.hi, p.lo, u.lo) and (p.hi, v.hi, p.lo, v.lo) per
@@ -586,7 +724,294 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_rev(const StepPlan p, const
   grad[q.media_off + L.i] += 2.0 * hd * (double)src[L.i] * (-(double)dv);
 }
 
-// After the reverse sweep of sequence k: acc (+)= M[1] + M[2], shared (+)= h_k M[1].
+// ---------------------------------------------------------------------------
+// Tiled adjoint kernels for 2D/3D acoustics: the same tiles as k_lf_tiled (32 x 32 x-y tiles
+// of one z plane, 32 x 8 threads, 4 rows each, periodic halo staged in shared memory).
+// ---------------------------------------------------------------------------
+
+struct TileLoc {
+  int prob, tx, ty, z;
+};
+
+__device__ __forceinline__ TileLoc tile_of(const StepPlan& p) {
+  int lo = 0, hi = p.batch - 1;
+  const int64_t blk = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.probs[mid].tblk_begin <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const ProbDev& q = p.probs[lo];
+  const int tile = (int)(blk - q.tblk_begin);
+  TileLoc t;
+  t.prob = lo;
+  t.tx = tile % q.tiles_x;
+  const int rest = tile / q.tiles_x;
+  t.ty = rest % q.tiles_y;
+  t.z = rest / q.tiles_y;
+  return t;
+}
+
+// Forward level store, tiled: lev[n+1] = lev[n-1] + 2h f(lev[n]) (n >= 1), lev[1] = y_in + h f0.
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T* __restrict__ y_in, T* lev,
+                                                       int64_t lev_stride, int k, int n) {
+  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
+  __shared__ T sh[3][Hh][W + 1];
+  const TileLoc tl = tile_of(p);
+  const ProbDev& q = p.probs[tl.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  if (n > N) return;
+  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
+  const int x0 = tl.tx * kTileX, y0 = tl.ty * kTileY, z = tl.z;
+  const int64_t P = q.pts;
+  const int64_t plane = (int64_t)z * nx * ny;
+  const double hd = p.hk[tl.prob * GBS_MAX_SEQ + k];
+  const T* yi = y_in + q.state_off;
+  auto level = [&](int j) -> T* { return lev + (int64_t)j * lev_stride + q.state_off; };
+  constexpr int F = 1 + DIM;
+  const int x = x0 + threadIdx.x;
+  if (n == 0) {
+    if (x >= nx) return;
+    const T h = T(hd);
+    const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
+    T* d = level(1);
+#pragma unroll
+    for (int i = 0; i < kTileRows; ++i) {
+      const int y = y0 + threadIdx.y + 8 * i;
+      if (y >= ny) break;
+      const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+      for (int fl = 0; fl < F; ++fl) d[fl * P + pt] = yi[fl * P + pt] + h * f0[fl * P + pt];
+    }
+    return;
+  }
+  const T* cur = level(n);
+  const T* prev = (n == 1) ? yi : level(n - 1);
+  T* dst = level(n + 1);
+  for (int r = threadIdx.y; r < Hh; r += 8) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    const T* rowp = cur + plane + (int64_t)gy * nx;
+    for (int c = threadIdx.x; c < W; c += kTileX) {
+      int gx = x0 - R + c;
+      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+      sh[0][r][c] = ldg(rowp + gx);
+      sh[1][r][c] = ldg(rowp + P + gx);
+      sh[2][r][c] = ldg(rowp + 2 * P + gx);
+    }
+  }
+  __syncthreads();
+  if (x >= nx) return;
+  const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
+  const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  const T h2 = T(2.0 * hd);
+#pragma unroll
+  for (int i = 0; i < kTileRows; ++i) {
+    const int ly = threadIdx.y + 8 * i;
+    const int y = y0 + ly;
+    if (y >= ny) break;
+    const int r = ly + R, cc = threadIdx.x + R;
+    T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      const T a = T(fd_coef<R>(j));
+      sxp += a * (sh[0][r][cc + j] - sh[0][r][cc - j]);
+      sxu += a * (sh[1][r][cc + j] - sh[1][r][cc - j]);
+      syp += a * (sh[0][r + j][cc] - sh[0][r - j][cc]);
+      syv += a * (sh[2][r + j][cc] - sh[2][r - j][cc]);
+    }
+    const int64_t pt = plane + (int64_t)y * nx + x;
+    T div = sxu * idx + syv * idy, szp = T(0);
+    if (DIM == 3) {
+      T szw = T(0);
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const int zp = z + j >= nz ? z + j - nz : z + j;
+        const int zm = z - j < 0 ? z - j + nz : z - j;
+        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
+        const T a = T(fd_coef<R>(j));
+        szp += a * (ldg(cur + pt + op) - ldg(cur + pt + om));
+        szw += a * (ldg(cur + 3 * P + pt + op) - ldg(cur + 3 * P + pt + om));
+      }
+      div += szw * idz;
+    }
+    const T kv = ldg(kap + pt), bv = ldg(bmed + pt);
+    T f[kMaxFields];
+    f[0] = -kv * div;
+    f[1] = -bv * (sxp * idx);
+    f[2] = -bv * (syp * idy);
+    if (DIM == 3) f[3] = -bv * (szp * idz);
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
+  }
+}
+
+// Reverse step, tiled (same recursion as k_adj_rev):
+//   M[j] = M[j+2] + init_j + 2h A^T M[j+1],  g += 2h mu_p (-div y_j),  mu = M[j+1],
+// with A^T mu = (D.(b mu_vel), grad(kappa mu_p)).  The tile holds kappa mu_p, b mu_u, b mu_v
+// of M[j+1] and, in FP32, y_j's u, v (the FP64 build takes div y_j through the cache to stay
+// within 48 KB of static shared memory).
+template <typename T, int DIM, int R>
+__global__ void __launch_bounds__(256) k_adj_rev_tiled(const StepPlan p, const T* __restrict__ lev,
+                                                       int64_t lev_stride, const T* __restrict__ lam_out, T* mA,
+                                                       T* mB, double* grad, float2* gpair, int k, int jrev) {
+  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
+  constexpr bool kStageY = sizeof(T) == 4;
+  constexpr int NS = kStageY ? 5 : 3;
+  __shared__ T sh[NS][Hh][W + 1];
+  const TileLoc tl = tile_of(p);
+  const ProbDev& q = p.probs[tl.prob];
+  const SlotDev& s = p.slots[q.slot];
+  if (k >= s.m) return;
+  const int N = s.steps[k];
+  const int j = N + 1 - jrev;
+  if (j < 1) return;
+  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
+  const int x0 = tl.tx * kTileX, y0 = tl.ty * kTileY, z = tl.z;
+  const int64_t P = q.pts;
+  const int64_t plane = (int64_t)z * nx * ny;
+  constexpr int F = 1 + DIM;
+  const double hd = p.hk[tl.prob * GBS_MAX_SEQ + k];
+  const double c = s.c[k];
+  T* dst = (((N + 1 - j) & 1) == 0 ? mA : mB) + q.state_off;
+  const T* src = (((N + 1 - j) & 1) == 0 ? mB : mA) + q.state_off;   // M[j+1]
+  const T* lo = lam_out + q.state_off;
+  const int x = x0 + threadIdx.x;
+  // per-thread constants (FP64 arithmetic is a small fraction of GB300's FP32 rate: none per point)
+  const T wq = T(0.25 * c), wh = T(0.5 * c);               // seeds c/4 and c/2 of lam_out
+  const T seed = j == N ? wh : j == N - 1 ? wq : T(0);
+  const float h2hi = (float)(2.0 * hd), h2lo = (float)(2.0 * hd - (double)h2hi);
+  if (j == N + 1) {
+    if (x >= nx) return;
+#pragma unroll
+    for (int i = 0; i < kTileRows; ++i) {
+      const int y = y0 + threadIdx.y + 8 * i;
+      if (y >= ny) break;
+      const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+      for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = wq * lo[fl * P + pt];
+      if (kStageY && k == 0) gpair[q.media_off + pt] = make_float2(0.f, 0.f);   // start of the macro-step
+    }
+    return;
+  }
+  const T* kappa = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  const T* yj = lev + (int64_t)j * lev_stride + q.state_off;
+  for (int r = threadIdx.y; r < Hh; r += 8) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    const int64_t row = plane + (int64_t)gy * nx;
+    for (int cc = threadIdx.x; cc < W; cc += kTileX) {
+      int gx = x0 - R + cc;
+      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+      const int64_t e = row + gx;
+      const T kv = ldg(kappa + e), bv = ldg(bmed + e);
+      sh[0][r][cc] = kv * ldg(src + e);
+      sh[1][r][cc] = bv * ldg(src + P + e);
+      sh[2][r][cc] = bv * ldg(src + 2 * P + e);
+      if constexpr (kStageY) {
+        sh[3][r][cc] = ldg(yj + P + e);
+        sh[4][r][cc] = ldg(yj + 2 * P + e);
+      }
+    }
+  }
+  __syncthreads();
+  if (x >= nx) return;
+  const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
+  const T h2 = T(2.0 * hd);
+#pragma unroll
+  for (int i = 0; i < kTileRows; ++i) {
+    const int ly = threadIdx.y + 8 * i;
+    const int y = y0 + ly;
+    if (y >= ny) break;
+    const int r = ly + R, cc = threadIdx.x + R;
+    const int64_t pt = plane + (int64_t)y * nx + x;
+    T sx_bu = T(0), sy_bv = T(0), sx_kp = T(0), sy_kp = T(0), sdx = T(0), sdy = T(0);
+#pragma unroll
+    for (int jj = 1; jj <= R; ++jj) {
+      const T a = T(fd_coef<R>(jj));
+      sx_kp += a * (sh[0][r][cc + jj] - sh[0][r][cc - jj]);
+      sy_kp += a * (sh[0][r + jj][cc] - sh[0][r - jj][cc]);
+      sx_bu += a * (sh[1][r][cc + jj] - sh[1][r][cc - jj]);
+      sy_bv += a * (sh[2][r + jj][cc] - sh[2][r - jj][cc]);
+      if constexpr (kStageY) {
+        sdx += a * (sh[3][r][cc + jj] - sh[3][r][cc - jj]);
+        sdy += a * (sh[4][r + jj][cc] - sh[4][r - jj][cc]);
+      }
+    }
+    T at[kMaxFields];
+    at[0] = sx_bu * idx + sy_bv * idy;
+    at[1] = sx_kp * idx;
+    at[2] = sy_kp * idy;
+    T dv;
+    if constexpr (kStageY) {
+      dv = sdx * idx + sdy * idy;
+    } else {
+      const PointGeo g = geo_of(q, pt);
+      T inv_dx[3] = {idx, idy, idz};
+      dv = div_point<T, DIM, R>(yj, P, g, inv_dx);
+    }
+    if (DIM == 3) {
+      T sz_bw = T(0), sz_kp = T(0), sdz = T(0);
+#pragma unroll
+      for (int jj = 1; jj <= R; ++jj) {
+        const int zp = z + jj >= nz ? z + jj - nz : z + jj;
+        const int zm = z - jj < 0 ? z - jj + nz : z - jj;
+        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
+        const T a = T(fd_coef<R>(jj));
+        sz_bw += a * (ldg(bmed + pt + op) * ldg(src + 3 * P + pt + op) - ldg(bmed + pt + om) * ldg(src + 3 * P + pt + om));
+        sz_kp += a * (ldg(kappa + pt + op) * ldg(src + pt + op) - ldg(kappa + pt + om) * ldg(src + pt + om));
+        if constexpr (kStageY) sdz += a * (ldg(yj + 3 * P + pt + op) - ldg(yj + 3 * P + pt + om));
+      }
+      at[0] += sz_bw * idz;
+      at[3] = sz_kp * idz;
+      if constexpr (kStageY) dv += sdz * idz;
+    }
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * P + pt;
+      T base = (j <= N - 1) ? dst[e] : T(0);          // M[j+2]
+      if (j >= N - 1) base += seed * lo[e];
+      dst[e] = base + h2 * at[fl];
+    }
+    if constexpr (kStageY) {
+      // FP32: gpair += 2h mu_p (-div y_j) in FP32 pairs (TwoProd by FMA, TwoSum); the finish
+      // kernel folds the macro-step's sum into the FP64 gradient once.  GB300's FP64 pipe
+      // would otherwise bound this kernel.
+      const float mu = (float)ldg(src + pt), dvf = -(float)dv;
+      const float pr = __fmul_rn(mu, dvf);
+      const float pe = fmaf(mu, dvf, -pr);                        // mu * dvf = pr + pe exactly
+      const float th = __fmul_rn(h2hi, pr);
+      const float te = fmaf(h2hi, pe, fmaf(h2lo, pr, fmaf(h2hi, pr, -th)));
+      float2 acc = gpair[q.media_off + pt];
+      const float sh = __fadd_rn(acc.x, th);
+      const float bv = __fsub_rn(sh, acc.x);
+      const float se = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sh, bv)), __fsub_rn(th, bv));
+      const float lo2 = __fadd_rn(acc.y, __fadd_rn(se, te));
+      const float hi2 = __fadd_rn(sh, lo2);
+      gpair[q.media_off + pt] = make_float2(hi2, __fsub_rn(lo2, __fsub_rn(hi2, sh)));
+    } else {
+      grad[q.media_off + pt] += 2.0 * hd * (double)ldg(src + pt) * (-(double)dv);
+    }
+  }
+}
+
+// After the reverse sweep of sequence k: acc (+)= M[1] + M[2], shared (+)= h_k M[1].  The FP32
+// build keeps acc as (hi, lo) float pairs in the same 8-byte slots (TwoSum accumulation), the
+// FP64 build as doubles.
+__device__ __forceinline__ float2 pair_add_f(float2 a, float b) {
+  const float s = __fadd_rn(a.x, b);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  const float lo = __fadd_rn(a.y, e);
+  const float hi = __fadd_rn(s, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kPlainBlock) k_adj_gather(const StepPlan p, const T* mA, const T* mB,
                                                             T* shared, int k) {
@@ -600,15 +1025,22 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_gather(const StepPlan p, co
   // M[1]: (N + 1 - 1) = N even -> buffer A; M[2] -> buffer B
   const T* m1 = mA + q.state_off;
   const T* m2 = mB + q.state_off;
-  double* acc = p.acc + q.state_off;
   T* sh = shared + q.state_off;
   const bool first = (k == 0);
+  const T hT = T(hd);
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) {
     const int64_t e = fl * q.pts + L.i;
-    const double v = (double)m1[e] + (double)m2[e];
-    acc[e] = first ? v : acc[e] + v;
-    const T hv = T(hd) * m1[e];
+    if constexpr (sizeof(T) == 4) {
+      float2* acc = reinterpret_cast<float2*>(p.acc) + q.state_off;
+      const float2 v = pair_add_f(make_float2(m1[e], 0.f), m2[e]);
+      acc[e] = first ? v : pair_add_f(pair_add_f(acc[e], v.x), v.y);
+    } else {
+      double* acc = p.acc + q.state_off;
+      const double v = (double)m1[e] + (double)m2[e];
+      acc[e] = first ? v : acc[e] + v;
+    }
+    const T hv = hT * m1[e];
     sh[e] = first ? hv : sh[e] + hv;
   }
 }
@@ -617,7 +1049,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_gather(const StepPlan p, co
 template <typename T, int DIM, int R>
 __global__ void __launch_bounds__(kPlainBlock) k_adj_finish(const StepPlan p, const T* __restrict__ y_in,
                                                             const T* __restrict__ shared, T* lam_in,
-                                                            double* grad) {
+                                                            double* grad, const float2* gpair) {
   const Loc L = locate(p);
   if (L.prob < 0) return;
   const ProbDev& q = p.probs[L.prob];
@@ -630,15 +1062,24 @@ __global__ void __launch_bounds__(kPlainBlock) k_adj_finish(const StepPlan p, co
   const T* sh = shared + q.state_off;
   T at[kMaxFields];
   rhs_T_point<T, DIM, R>(sh, q.pts, g, inv_dx, kappa, bmed, at);
-  const double* acc = p.acc + q.state_off;
   T* li = lam_in + q.state_off;
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) {
     const int64_t e = fl * q.pts + L.i;
-    li[e] = T(acc[e] + (double)at[fl]);
+    if constexpr (sizeof(T) == 4) {
+      const float2 a = reinterpret_cast<const float2*>(p.acc)[q.state_off + e];
+      li[e] = (a.x + at[fl]) + a.y;
+    } else {
+      li[e] = T(p.acc[q.state_off + e] + (double)at[fl]);
+    }
   }
   const T dv = div_point<T, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx);
-  grad[q.media_off + L.i] += (double)sh[L.i] * (-(double)dv);
+  double gsum = (double)sh[L.i] * (-(double)dv);
+  if (gpair) {   // the macro-step's reverse-step gradient terms (FP32 pairs, tiled kernels)
+    const float2 gp = gpair[q.media_off + L.i];
+    gsum += (double)gp.x + (double)gp.y;
+  }
+  grad[q.media_off + L.i] += gsum;
 }
 
 // Receiver injection; an index outside [0, n_pts) latches GBS_ERR_INVALID and is skipped.
@@ -671,7 +1112,9 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
     ++launches;
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
       const int u = timing_begin(p, st);
-      if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
+      if constexpr (SYS == SYS_ACOUSTIC && DIM == 3 && std::is_same<T, float>::value)
+        k_lf_stream3d<R><<<(unsigned)p.total_sblocks, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+      else if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
         k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else if (SYS == SYS_ACOUSTIC && DIM >= 2)
         k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
@@ -699,18 +1142,25 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
   T* mB = static_cast<T*>(a.mu1);
   T* shared = static_cast<T*>(a.shared);
   const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
+  const dim3 tgrid((unsigned)p.total_tiles), tblock(kTileX, 8);
   int launches = 0;
   k_f0<T, SYS_ACOUSTIC, DIM, R><<<grid, block, 0, st>>>(p, y_in);
   ++launches;
   for (int k = 0; k < p.max_m; ++k) {
     const int Nk = p.max_steps_k[k];
     for (int n = 0; n <= Nk; ++n) {
-      k_adj_fwd<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, k, n);
+      if (DIM >= 2)
+        k_adj_fwd_tiled<T, DIM, R><<<tgrid, tblock, 0, st>>>(p, y_in, lev, lev_stride, k, n);
+      else
+        k_adj_fwd<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, k, n);
       ++launches;
     }
     for (int t = 0; t <= Nk; ++t) {
       const int u = t > 0 ? timing_begin(p, st) : -1;
-      k_adj_rev<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, lam_out, mA, mB, grad, k, t);
+      if (DIM >= 2)
+        k_adj_rev_tiled<T, DIM, R><<<tgrid, tblock, 0, st>>>(p, lev, lev_stride, lam_out, mA, mB, grad, a.gpair, k, t);
+      else
+        k_adj_rev<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, lam_out, mA, mB, grad, k, t);
       if (t > 0)
         timing_end(p, u, st, p.tev ? p.adj_unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + t] : 0.0);
       ++launches;
@@ -718,7 +1168,8 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
     k_adj_gather<T, DIM><<<grid, block, 0, st>>>(p, mA, mB, shared, k);
     ++launches;
   }
-  k_adj_finish<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, shared, lam_in, grad);
+  k_adj_finish<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, shared, lam_in, grad,
+                                                  (DIM >= 2 && sizeof(T) == 4) ? a.gpair : nullptr);
   ++launches;
   if (n_rcv > 0) {
     k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid),

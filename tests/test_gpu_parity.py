@@ -239,15 +239,17 @@ def test_stability_limit_bounds_spectral_radius():
 
 
 @pytest.mark.parametrize("precision", [F64, F32])
-def test_adjoint_parity(precision):
-    case = AcousticCase((20, 23), 4, precision, seed=6)
+@pytest.mark.parametrize("shape,order", [((20, 23), 4), ((45, 70), 6), ((9, 10, 11), 4)])
+def test_adjoint_parity(precision, shape, order):
+    # one tile; several 32 x 32 tiles with ragged edges; 3D (z-stencils through the cache)
+    case = AcousticCase(shape, order, precision, seed=6)
     sol = case.solver(enable_adjoint=True)
     sol.set_scheme(S.GBS_8_6)
     H = 0.8 * sol.stability_limit()[0]
     steps, c = oracle_scheme(S.GBS_8_6)
     rng = np.random.default_rng(1)
     lam = rng.standard_normal(case.y0.shape).astype(case.np_dtype).astype(np.float64)
-    rcv = np.array([5, 77, 300, 301], dtype=np.int64)
+    rcv = np.array([5, 77, 300, 301], dtype=np.int64) % case.y0[0].size
     resid = rng.standard_normal(4).astype(case.np_dtype).astype(np.float64)
     o_lam, o_g = OG.gbs_macro_step_adjoint(case.f, case.fT, case.pair, case.y0, lam, H, steps, c)
     o_lam = o_lam + OG.inject_receivers(case.y0.shape, rcv, resid)
