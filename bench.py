@@ -353,9 +353,7 @@ def run_gpu(args):
             "frac": achieved / peak if achieved else None, "traffic": traffic,
             "traffic_source": "profiles/k_passes_2d2048.md (ncu, same kernel and schedule)" if traffic else None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "kernel": ("fused pass" if sol_kernel_is_fused(sol, B) else
-                       "streaming leap-frog step (k_lf_stream3d)" if args.workload == "3d" and not (args.f64 or args.f32x2)
-                       else "tiled leap-frog step (k_lf_tiled)"),
+            "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "tiled leap-frog step (k_lf_tiled)",
             "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
             "avg_launch_ms": kms / nl if nl else None}
 

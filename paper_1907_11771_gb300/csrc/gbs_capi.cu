@@ -47,7 +47,7 @@ struct gbs_ctx {
   int ds = 0;                             // GBS_F32X2: FP32-pair levels and right-hand sides
   size_t esz = 4;                         // state element size
   std::vector<ProbDev> probs;
-  int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0, total_sblocks = 0;
+  int64_t state_elems = 0, media_elems = 0, total_blocks = 0, total_tiles = 0;
   std::vector<double> cmax;               // per problem max sqrt(kappa b)
   // media
   const void* kappa = nullptr;
@@ -360,7 +360,6 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->hkf = h->d_hkf;
   p->total_blocks = h->total_blocks;
   p->total_tiles = h->total_tiles;
-  p->total_sblocks = h->total_sblocks;
   p->state_elems = h->state_elems;
   p->kappa = h->kappa;
   p->b = h->b;
@@ -562,7 +561,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   h->state_elems = soff;
   h->media_elems = moff;
   h->total_blocks = blk;
-  h->total_tiles = assign_tiles(h->probs.data(), h->batch, h->ndim, &h->total_sblocks);
+  h->total_tiles = assign_tiles(h->probs.data(), h->batch, h->ndim);
   if (blk > 0x7fffffff) {
     delete h;
     return fail(nullptr, GBS_ERR_INVALID, "problem too large for one launch grid");

@@ -387,24 +387,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P)
   }
 }
 
-// y_out = sum_k c_k y*_k (per problem, its slot's weights), accumulated in FP32 pairs:
-// c_k = chi + clo, the product chi*y is split exactly by one FMA (TwoProd), clo*y is added
-// to its error, and the running sum is kept as (hi, lo) with TwoSum.  The accumulated
-// error is about 2^-48 of sum_k |c_k y*_k| -- FP64-class -- while using only FP32 units
-// (GB300 runs FP64 at a small fraction of the FP32 rate; a plain FP64 sum of 11 terms
-// per element would saturate that pipe).
-__device__ __forceinline__ void combine_add(float c_hi, float c_lo, float y, float& sh, float& sl) {
-  // _rn intrinsics keep the compiler from contracting these into FMAs
-  const float p = __fmul_rn(c_hi, y);
-  const float pe = fmaf(c_lo, y, fmaf(c_hi, y, -p));   // c_hi*y - p exactly, plus c_lo*y
-  const float t = __fadd_rn(sh, p);
-  const float bv = __fsub_rn(t, sh);
-  const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-  sl = __fadd_rn(sl, __fadd_rn(te, pe));
-  sh = __fadd_rn(t, sl);
-  sl = __fsub_rn(sl, __fsub_rn(sh, t));
-}
-
 __device__ __forceinline__ int problem_of(const ProbDev* probs, int batch, int64_t e) {
   int lo = 0, hi = batch - 1;
   while (lo < hi) {
@@ -415,8 +397,12 @@ __device__ __forceinline__ int problem_of(const ProbDev* probs, int batch, int64
   return lo;
 }
 
-// Four consecutive elements per thread: the loads of all sequences are issued before the sums
-// (float4 when the group is 16-byte aligned and inside one problem, else element by element).
+// y_out = sum_k c_k y*_k (per problem, its slot's weights), accumulated in FP32 pairs
+// (pair_combine_add: error about 2^-48 of sum_k |c_k y*_k|, FP64-class, on FP32 units only;
+// GB300 runs FP64 at a small fraction of the FP32 rate and a plain FP64 sum of 11 terms per
+// element would saturate that pipe).  Four consecutive elements per thread: the loads of all
+// sequences are issued before the sums (float4 when the group is 16-byte aligned and inside
+// one problem, else element by element).
 __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch, const SlotDev* slots,
                                                  const float* __restrict__ ystar, int64_t E,
                                                  float* __restrict__ y_out) {
@@ -438,17 +424,17 @@ __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch
 #pragma unroll
       for (int k = 0; k < GBS_MAX_SEQ; ++k)
         if (k < s.m) {
-          combine_add(s.chi[k], s.clo[k], y[k].x, sh.x, sl.x);
-          combine_add(s.chi[k], s.clo[k], y[k].y, sh.y, sl.y);
-          combine_add(s.chi[k], s.clo[k], y[k].z, sh.z, sl.z);
-          combine_add(s.chi[k], s.clo[k], y[k].w, sh.w, sl.w);
+          pair_combine_add(s.chi[k], s.clo[k], y[k].x, sh.x, sl.x);
+          pair_combine_add(s.chi[k], s.clo[k], y[k].y, sh.y, sl.y);
+          pair_combine_add(s.chi[k], s.clo[k], y[k].z, sh.z, sl.z);
+          pair_combine_add(s.chi[k], s.clo[k], y[k].w, sh.w, sl.w);
         }
       *reinterpret_cast<float4*>(y_out + e0) = make_float4(sh.x + sl.x, sh.y + sl.y, sh.z + sl.z, sh.w + sl.w);
     } else {
       for (int64_t e = e0; e <= e3; ++e) {
         const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
         float sh = 0.f, sl = 0.f;
-        for (int k = 0; k < s.m; ++k) combine_add(s.chi[k], s.clo[k], __ldcs(ystar + (int64_t)k * E + e), sh, sl);
+        for (int k = 0; k < s.m; ++k) pair_combine_add(s.chi[k], s.clo[k], __ldcs(ystar + (int64_t)k * E + e), sh, sl);
         y_out[e] = sh + sl;
       }
     }

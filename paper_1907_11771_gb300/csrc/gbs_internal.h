@@ -20,8 +20,6 @@ struct ProbDev {
   int64_t blk_begin;   // first block of this problem in a point-parallel grid
   int64_t tblk_begin;  // first block of this problem in the x-y tiled grid
   int tiles_x, tiles_y;  // x-y tiles per z plane (kTileX x kTileY points each)
-  int stiles_y, zchunks; // 3D streaming grid: kTileX x kSTileY tiles, z in chunks of kZChunk
-  int64_t sblk_begin;    // first block of this problem in the 3D streaming grid
   double inv_dx[3];
 };
 
@@ -56,7 +54,6 @@ struct StepPlan {
   const float2* hkf;           // the same as FP32 pairs (h_k, 2 h_k)
   int64_t total_blocks;        // point-parallel blocks over the whole batch
   int64_t total_tiles;         // x-y tiled blocks over the whole batch (2D/3D)
-  int64_t total_sblocks;       // 3D streaming blocks over the whole batch
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   int64_t probs_media_elems;   // scalars in one media array (sum of pts)
   const void* kappa;           // media (state element type)
@@ -101,27 +98,20 @@ inline void timing_end(const StepPlan& p, int u, cudaStream_t s, double bytes) {
 }
 
 constexpr int kPlainBlock = 256;
-constexpr int kSTileY = 16;   // 3D streaming step: 32 x 16 x-y tiles, 2 rows per thread
-constexpr int kZChunk = 64;   // z planes swept by one streaming block
 constexpr int kTileX = 32;   // tiled step kernels: 32 x 8 threads, 4 rows per thread
 constexpr int kTileRows = 4;
 constexpr int kTileY = 8 * kTileRows;
 
 // Fill the tiled-grid fields of a problem table (host); returns the total tile count.
-inline int64_t assign_tiles(ProbDev* probs, int batch, int ndim, int64_t* stream_blocks = nullptr) {
-  int64_t t = 0, sb = 0;
+inline int64_t assign_tiles(ProbDev* probs, int batch, int ndim) {
+  int64_t t = 0;
   for (int i = 0; i < batch; ++i) {
     ProbDev& q = probs[i];
     q.tiles_x = (q.n[0] + kTileX - 1) / kTileX;
     q.tiles_y = ndim >= 2 ? (q.n[1] + kTileY - 1) / kTileY : 1;
     q.tblk_begin = t;
     t += (int64_t)q.tiles_x * q.tiles_y * q.n[2];
-    q.stiles_y = ndim >= 2 ? (q.n[1] + kSTileY - 1) / kSTileY : 1;
-    q.zchunks = (q.n[2] + kZChunk - 1) / kZChunk;
-    q.sblk_begin = sb;
-    sb += (int64_t)q.tiles_x * q.stiles_y * q.zchunks;
   }
-  if (stream_blocks) *stream_blocks = sb;
   return t;
 }
 
@@ -161,7 +151,7 @@ struct AdjPlan {
   void* mu0;                   // two adjoint level buffers, F x P each
   void* mu1;
   void* shared;                // sum_k h_k mu_1^k, F x P (state type)
-  float2* gpair;               // FP32 path: one sequence's gradient terms, (hi, lo) per media point
+  float2* gpair;               // FP32 path: the macro-step's reverse-step gradient terms, (hi, lo) per point
   int max_steps;
   int64_t rcv_pts;             // valid receiver indices: [0, rcv_pts)
   int* err;                    // device error flag

@@ -176,8 +176,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
     moff += d.pts;
     blk += (d.pts + kPlainBlock - 1) / kPlainBlock;
   }
-  int64_t sblocks = 0;
-  const int64_t tiles = assign_tiles(probs, pb->batch, pb->ndim, &sblocks);
+  const int64_t tiles = assign_tiles(probs, pb->batch, pb->ndim);
   const size_t o_probs = 0;
   const size_t o_slot = align256(o_probs + sizeof(ProbDev) * pb->batch);
   const size_t o_H = align256(o_slot + sizeof(SlotDev));
@@ -247,7 +246,6 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.hkf = reinterpret_cast<const float2*>(sc + o_hkf);
   p.total_blocks = blk;
   p.total_tiles = tiles;
-  p.total_sblocks = sblocks;
   p.state_elems = soff;
   p.kappa = kappa;
   p.b = sc + o_b;

@@ -194,10 +194,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const T ym = prev[e];
     const T y0 = cur[e];
     const T yp = ym + h2 * f[fl];
-    const double ys = (double)gragg_avg(ym, y0, yp);
-    const double a = first ? c * ys : fma(c, ys, acc[e]);
-    if (last) yo[e] = static_cast<typename out_of<T>::type>(a);
-    else acc[e] = a;
+    combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(ym, y0, yp), yo);
   }
 }
 
@@ -320,148 +317,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
         const T ym = prev[e];
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
         const T yp = ym + h2 * f[fl];
-        const double ys = (double)gragg_avg(ym, yc, yp);
-        const double a2 = first ? c * ys : fma(c, ys, acc[e]);
-        if (last) yo[e] = static_cast<typename out_of<T>::type>(a2);
-        else acc[e] = a2;
-      }
-    }
-  }
-}
-
-// 3D leap-frog step for FP32 acoustics, streaming along z (2.5D blocking).  A block of 32 x 8
-// threads owns a 32 x 16 x-y tile (2 rows per thread) and a chunk of up to kZChunk planes.  It
-// walks z keeping the last 2R+1 planes of p and w of its own columns in registers (the
-// z-stencils; compile-time slots, the walk unrolled by 2R+1) and stages each plane's p, u, v
-// with the x-y halo in shared memory (the x- and y-stencils).  Every point is loaded once per
-// plane instead of once per z-neighbour.  Same arithmetic, averaging and FP64 combine as
-// k_lf_tiled.
-template <int R>
-__global__ void __launch_bounds__(256) k_lf_stream3d(const StepPlan p, const float* y_in, float* y_out, int k, int n) {
-  constexpr int U = 2 * R + 1;
-  constexpr int OFF = 64 * U;
-  constexpr int RPT = kSTileY / 8;
-  constexpr int W = kTileX + 2 * R, Hh = kSTileY + 2 * R;
-  __shared__ float sp[Hh][W + 1], su[Hh][W + 1], sv[Hh][W + 1];
-  int lo = 0, hi = p.batch - 1;
-  const int64_t blk = blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (p.probs[mid].sblk_begin <= blk) lo = mid;
-    else hi = mid - 1;
-  }
-  const ProbDev& q = p.probs[lo];
-  const SlotDev& s = p.slots[q.slot];
-  if (k >= s.m) return;
-  const int N = s.steps[k];
-  if (n > N) return;
-  const int tile = (int)(blk - q.sblk_begin);
-  const int tx = tile % q.tiles_x;
-  const int rest = tile / q.tiles_x;
-  const int ty = rest % q.stiles_y;
-  const int zc = rest / q.stiles_y;
-  const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
-  const int x0 = tx * kTileX, y0 = ty * kSTileY;
-  const int za = zc * kZChunk, zb = min(nz, za + kZChunk);
-  const int64_t P = q.pts, PL = (int64_t)nx * ny;
-  float h, h2;
-  step_sizes(p, lo, k, h, h2);
-  float* const L0 = static_cast<float*>(p.L0) + q.state_off;
-  float* const L1 = static_cast<float*>(p.L1) + q.state_off;
-  const float* cur = (n & 1) ? L1 : L0;
-  float* dst = (n & 1) ? L0 : L1;
-  const float* prev = (n == 1) ? (y_in + q.state_off) : dst;
-  const float* kap = static_cast<const float*>(p.kappa) + q.media_off;
-  const float* bmed = static_cast<const float*>(p.b) + q.media_off;
-  const float idx = float(q.inv_dx[0]), idy = float(q.inv_dx[1]), idz = float(q.inv_dx[2]);
-  const int x = x0 + threadIdx.x;
-  const bool xin = x < nx;
-  int yr[RPT];
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) yr[i] = y0 + threadIdx.y + 8 * i;
-  float wp[RPT][U], ww[RPT][U];
-#pragma unroll
-  for (int i = 0; i < RPT; ++i)
-#pragma unroll
-    for (int u = 0; u < U; ++u) wp[i][u] = ww[i][u] = 0.f;
-  const double c = s.c[k];
-  const bool first = (k == 0), last = (k == s.m - 1);
-  const int S = (zb - za) + 2 * R;   // plane loads: za - R .. zb + R - 1
-  for (int sb = 0; sb < S; sb += U) {
-#pragma unroll
-    for (int uu = 0; uu < U; ++uu) {
-      const int st = sb + uu;
-      if (st >= S) break;
-      int zl = za - R + st;                      // within [-R, nz + R): one wrap at most
-      if (zl < 0) zl += nz;
-      else if (zl >= nz) zl -= nz;
-#pragma unroll
-      for (int i = 0; i < RPT; ++i)
-        if (xin && yr[i] < ny) {
-          const int64_t e = (int64_t)zl * PL + (int64_t)yr[i] * nx + x;
-          wp[i][uu] = ldg(cur + e);
-          ww[i][uu] = ldg(cur + 3 * P + e);
-        }
-      if (st < 2 * R) continue;
-      const int z = za - 2 * R + st;             // the plane computed now, in [za, zb)
-      __syncthreads();                           // the previous plane's readers are done
-      for (int r = threadIdx.y; r < Hh; r += 8) {
-        int gy = y0 - R + r;
-        if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-        const float* rowp = cur + (int64_t)z * PL + (int64_t)gy * nx;
-        for (int cx = threadIdx.x; cx < W; cx += kTileX) {
-          int gx = x0 - R + cx;
-          if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-          sp[r][cx] = ldg(rowp + gx);
-          su[r][cx] = ldg(rowp + P + gx);
-          sv[r][cx] = ldg(rowp + 2 * P + gx);
-        }
-      }
-      __syncthreads();
-      if (!xin) continue;
-      const int sc = (uu + OFF - R) % U;         // window slot of plane z
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int y = yr[i];
-        if (y >= ny) continue;
-        const int rr = threadIdx.y + 8 * i + R, cc = threadIdx.x + R;
-        float sxp = 0.f, sxu = 0.f, syp = 0.f, syv = 0.f, szp = 0.f, szw = 0.f;
-#pragma unroll
-        for (int j = 1; j <= R; ++j) {
-          const float a = float(fd_coef<R>(j));
-          sxp += a * (sp[rr][cc + j] - sp[rr][cc - j]);
-          sxu += a * (su[rr][cc + j] - su[rr][cc - j]);
-          syp += a * (sp[rr + j][cc] - sp[rr - j][cc]);
-          syv += a * (sv[rr + j][cc] - sv[rr - j][cc]);
-          szp += a * (wp[i][(uu + OFF - R + j) % U] - wp[i][(uu + OFF - R - j) % U]);
-          szw += a * (ww[i][(uu + OFF - R + j) % U] - ww[i][(uu + OFF - R - j) % U]);
-        }
-        const int64_t pt = (int64_t)z * PL + (int64_t)y * nx + x;
-        const float div = sxu * idx + syv * idy + szw * idz;
-        const float kv = ldg(kap + pt), bv = ldg(bmed + pt);
-        float f[4];
-        f[0] = -kv * div;
-        f[1] = -bv * (sxp * idx);
-        f[2] = -bv * (syp * idy);
-        f[3] = -bv * (szp * idz);
-        if (n < N) {
-#pragma unroll
-          for (int fl = 0; fl < 4; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
-        } else {
-          double* acc = p.acc + q.state_off;
-          float* yo = y_out + q.state_off;
-          const float ycur[4] = {sp[rr][cc], su[rr][cc], sv[rr][cc], ww[i][sc]};
-#pragma unroll
-          for (int fl = 0; fl < 4; ++fl) {
-            const int64_t e = fl * P + pt;
-            const float ym = prev[e];
-            const float yp = ym + h2 * f[fl];
-            const double ys = (double)gragg_avg(ym, ycur[fl], yp);
-            const double a2 = first ? c * ys : fma(c, ys, acc[e]);
-            if (last) yo[e] = float(a2);
-            else acc[e] = a2;
-          }
-        }
+        combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(ym, yc, yp), yo);
       }
     }
   }
@@ -1112,9 +968,7 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
     ++launches;
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
       const int u = timing_begin(p, st);
-      if constexpr (SYS == SYS_ACOUSTIC && DIM == 3 && std::is_same<T, float>::value)
-        k_lf_stream3d<R><<<(unsigned)p.total_sblocks, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
-      else if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
+      if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
         k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else if (SYS == SYS_ACOUSTIC && DIM >= 2)
         k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);

@@ -49,6 +49,45 @@ __device__ __forceinline__ double gragg_avg(double ym, double y0, double yp) {
   return (ym + 2.0 * y0 + yp) * 0.25;
 }
 
+// (sh, sl) += (c_hi + c_lo) * y in FP32 pairs: TwoProd of c_hi * y by one FMA, c_lo * y added to
+// its error, TwoSum into the running pair.  Error about 2^-48 of the sum of |c y| terms, using
+// FP32 units only (the _rn intrinsics keep the compiler from contracting the error terms).
+__device__ __forceinline__ void pair_combine_add(float c_hi, float c_lo, float y, float& sh, float& sl) {
+  const float p = __fmul_rn(c_hi, y);
+  const float pe = fmaf(c_lo, y, fmaf(c_hi, y, -p));
+  const float t = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(t, sh);
+  const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  sl = __fadd_rn(sl, __fadd_rn(te, pe));
+  sh = __fadd_rn(t, sl);
+  sl = __fsub_rn(sl, __fsub_rn(sh, t));
+}
+
+// The combine of the plain path's last leap-frog step of sequence k: y_out (+)= c_k y*_k.  FP32
+// states accumulate in FP32 pairs held in the accumulator's 8-byte slots; FP64 (and FP32-pair)
+// states in FP64.
+template <typename T, typename O>
+__device__ __forceinline__ void combine_last(double* acc, int64_t e, bool first, bool last, double c, float chi,
+                                             float clo, T ystar, O* yo) {
+  if constexpr (sizeof(T) == 4 && sizeof(O) == 4) {
+    float2* a = reinterpret_cast<float2*>(acc);
+    float sh = 0.f, sl = 0.f;
+    if (!first) {
+      const float2 v = a[e];
+      sh = v.x;
+      sl = v.y;
+    }
+    pair_combine_add(chi, clo, (float)ystar, sh, sl);
+    if (last) yo[e] = O(sh + sl);
+    else a[e] = make_float2(sh, sl);
+  } else {
+    const double ys = (double)ystar;
+    const double a2 = first ? c * ys : fma(c, ys, acc[e]);
+    if (last) yo[e] = static_cast<O>(a2);
+    else acc[e] = a2;
+  }
+}
+
 // Geometry of one point inside one problem.
 struct PointGeo {
   int64_t i;        // flat point index inside the problem
