@@ -18,6 +18,9 @@ Systems
 * 1D wave:   u_t = v_x, v_t = u_x                  fields (u, v)
 * acoustics: p_t = -kappa div(u), u_d,t = -b d_d p  fields (p, u_x, u_y[, u_z]),
   b = 1/rho.
+* one-way wave with a spectral derivative (Sec. 4): u_t = -u_x, field (u), the derivative
+  taken exactly on every resolved Fourier mode (FFT, multiply by i k, inverse FFT; the Nyquist
+  mode, whose derivative the grid cannot represent, is set to zero).
 
 The transposes (used by the discrete adjoint) are formed literally: the
 transpose of "shift by +j" is "shift by -j"; no antisymmetry is assumed.
@@ -112,6 +115,19 @@ def dA_dkappa_pairing(mu, y, dx, order):
 
 # --------------------------------------------------------------------------
 # Spectral information
+def rhs_oneway_spectral(y, dx):
+    """f(u) = -u_x for u_t + u_x = 0 on a periodic grid of n points, spacing dx (Sec. 4).
+
+    Mode m of the discrete Fourier transform (m = -n/2+1 .. n/2-1) has wavenumber
+    k = 2 pi m / (n dx) and derivative i k; the Nyquist mode m = n/2 gets 0."""
+    n = y.shape[-1]
+    m = np.fft.fftfreq(n, d=1.0 / n)              # 0, 1, .., n/2-1, -n/2, .., -1
+    k = 2.0 * np.pi * m / (n * dx)
+    if n % 2 == 0:
+        k[n // 2] = 0.0
+    return -np.real(np.fft.ifft(1j * k * np.fft.fft(y, axis=-1), axis=-1))
+
+
 # --------------------------------------------------------------------------
 
 def symbol_max(order):
