@@ -508,6 +508,97 @@ def run_adjoint(args):
     return 0
 
 
+def run_oneway(args):
+    """Sec. 4's test problem on the GPU: the one-way wave u_t + u_x = 0 with spectral derivatives.
+    Throughput: a batch of 256 problems of n = 1024, GBS_8,6 at 0.99 x the stability limit.  The
+    FFTs run in FP64, so the kernel is bound by GB300's FP64 rate: its roofline counts
+    algorithmic FP64 flops (per right-hand side two radix-2 FFTs, 10 flops per butterfly, n/2
+    log2 n butterflies each, plus 2 n for the -i k multiply) against the nominal FP64 rate
+    (1.25 TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz).  The config also
+    carries Sec. 4's convergence study: the error after one trip around the interval at
+    lambda = dt/dx = 0.99 ISB / pi for GBS_8,6 and GBS_12,8, n = 16 .. 1024."""
+    import numpy as np
+    import torch
+
+    from paper_1907_11771_gb300 import binding as B
+    from paper_1907_11771_gb300 import build as Bld
+    from paper_1907_11771_gb300 import schemes as S
+    from paper_1907_11771_gb300.solver import GBSSolver
+
+    torch.cuda.set_device(0)
+    Bld.build()
+    study = {}
+    for sch in (S.GBS_8_6, S.GBS_12_8):
+        rows = []
+        for n in (16, 32, 64, 128, 256, 512, 1024):
+            sol = GBSSolver(B.GBS_ONEWAY_SPECTRAL, [(n,)], [(1.0 / n,)], fd_order=0, precision=B.GBS_F64)
+            sol.set_scheme(sch)
+            isb = sol.weights()[2]
+            M = int(np.ceil(1.0 / (0.99 / np.pi * isb / n)))
+            u0 = 0.5 * (1 - np.cos(2 * np.pi * np.arange(n) / n))
+            y = torch.tensor(u0, dtype=torch.float64, device="cuda")
+            sol.step(y, y, 1.0 / M, M)
+            sol.sync()
+            rows.append({"n": n, "macro_steps": M, "max_error": float(np.max(np.abs(y.cpu().numpy() - u0)))})
+            sol.close()
+        study[sch.name] = rows
+    nb, n = 256, 1024
+    sol = GBSSolver(B.GBS_ONEWAY_SPECTRAL, [(n,)] * nb, [(1.0 / n,)] * nb, fd_order=0, precision=B.GBS_F64)
+    sol.set_scheme(S.GBS_8_6)
+    H = 0.99 * sol.stability_limit()[0]
+    rng = np.random.default_rng(0)
+    y = torch.tensor(rng.standard_normal(nb * n), dtype=torch.float64, device="cuda")
+    upd = nb * n * S.GBS_8_6.updates_per_point
+    for _ in range(args.warmup):
+        sol.step(y, y, H, 1)
+    torch.cuda.synchronize()
+    l0 = sol.kernel_launches
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            evs[i][0].record()
+            sol.step(y, y, H, 1)
+            evs[i][1].record()
+        torch.cuda.synchronize()
+    launches = sol.kernel_launches - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = upd * args.steps / (ms / 1e3) / 1e9
+    logn = int(np.log2(n))
+    rhs_flops = 2 * (n // 2) * logn * 10 + 2 * n
+    evals = 1 + sum(S.GBS_8_6.steps)                     # shared f0 plus one per leap-frog step
+    flops = nb * evals * rhs_flops * args.steps
+    peak_tf = 152 * 2 * 2 * 2.07e9 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    hy = y.cpu().pin_memory()
+    ho = torch.empty_like(hy).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        y.copy_(hy, non_blocking=True)
+        sol.step(y, y, H, 1)
+        ho.copy_(y, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e = {"value": upd * args.steps / (e0.elapsed_time(e1) / 1e3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": hy.numel() * 8, "d2h_bytes_per_step": ho.numel() * 8}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": (f"Sec. 4 one-way wave u_t + u_x = 0, spectral derivatives, {nb} problems of "
+                                    f"n = {n}, GBS_8,6 FP64, H = 0.99 x stability limit"),
+                       "shapes": f"{nb} x [{n}]", "scheme": "GBS_8,6", "updates_per_step_per_gpu": upd,
+                       "section4_convergence": study, "parallelism": "replicas x1"},
+            "clocks": clk.summary(), "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tf, "traffic": None,
+                         "peak_kind": "FP64 from unit counts and clock (152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz)",
+                         "kernel": "spectral macro-step (k_spectral_macro)"},
+            "e2e": e2e}
+    print(json.dumps(line), flush=True)
+    sol.close()
+    return 0
+
+
 def run_time_to_solution(args):
     """Time to a relative L2 error of 1e-6 at t = M0 H0 (2D acoustics, same recipe on an
     n x n grid): the fused FP32-state path, the plain FP64 path and the plain FP32-pair path,
@@ -594,9 +685,9 @@ def main():
     ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
     ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--workload", choices=["2d", "3d", "batch", "adjoint"], default="2d",
-                    help="2d (default, the headline workload), 3d (512^3), batch (256 problems) or "
-                         "adjoint (misfit gradient, 1024^2)")
+    ap.add_argument("--workload", choices=["2d", "3d", "batch", "adjoint", "oneway"], default="2d",
+                    help="2d (default, the headline workload), 3d (512^3), batch (256 problems), "
+                         "adjoint (misfit gradient, 1024^2) or oneway (Sec. 4 spectral test problem)")
     ap.add_argument("--adj-macro", type=int, default=100, help="macro-steps of one misfit gradient (adjoint workload)")
     ap.add_argument("--adj-checkpoint", type=int, default=50, help="checkpoint interval (adjoint workload)")
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
@@ -619,6 +710,8 @@ def main():
         return run_time_to_solution(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "oneway":
+        return run_oneway(args)
     return run_gpu(args)
 
 

@@ -73,7 +73,12 @@ typedef enum {
   GBS_ERR_STATE = 8      /* call out of order (e.g. stepping before weights set) */
 } gbs_status;
 
-enum { GBS_WAVE1D = 1, GBS_ACOUSTIC = 2 };                /* gbs_problem.system    */
+/* gbs_problem.system.  GBS_ONEWAY_SPECTRAL is the test problem of Sec. 4: u_t + u_x = 0 on a
+ * periodic 1D grid with the derivative taken spectrally (exact on every resolved Fourier mode,
+ * zero on the Nyquist mode), so that errors come from the time stepping alone.  It takes
+ * fd_order = 0, precision GBS_F64, a power-of-two size n in [8, 2048] per problem, no media and
+ * no adjoint; one field u.  Its stability bound uses |lambda| <= pi / dx. */
+enum { GBS_WAVE1D = 1, GBS_ACOUSTIC = 2, GBS_ONEWAY_SPECTRAL = 3 };
 enum { GBS_F32_STATE_F64_COMBINE = 0, GBS_F64 = 1, GBS_F32X2 = 2 }; /* gbs_problem.precision */
 enum { GBS_KERNEL_AUTO = 0, GBS_KERNEL_PLAIN = 1, GBS_KERNEL_FUSED = 2 }; /* gbs_set_option */
 
@@ -83,7 +88,8 @@ typedef struct {
   int system;             /* GBS_WAVE1D (u_t = v_x, v_t = u_x) or GBS_ACOUSTIC
                              (p_t = -kappa div u, u_t = -grad p / rho)          */
   int ndim;               /* 1 for GBS_WAVE1D; 1, 2 or 3 for GBS_ACOUSTIC        */
-  int fd_order;           /* 4 or 6: periodic centred finite differences         */
+  int fd_order;           /* 4 or 6: periodic centred finite differences (0 for
+                             GBS_ONEWAY_SPECTRAL)                                */
   int precision;          /* GBS_F32_STATE_F64_COMBINE, GBS_F64 or GBS_F32X2     */
   int batch;              /* number of independent problems, >= 1               */
   int enable_adjoint;     /* nonzero: reserve workspace for gbs_adjoint_step     */

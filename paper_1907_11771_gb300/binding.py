@@ -16,7 +16,7 @@ GBS_OK = 0
 STATUS_NAMES = {0: "GBS_OK", 1: "GBS_ERR_INVALID", 2: "GBS_ERR_ORDER", 3: "GBS_ERR_UNSTABLE",
                 4: "GBS_ERR_CUDA", 5: "GBS_ERR_NOMEM", 6: "GBS_ERR_TIMEOUT", 7: "GBS_ERR_NONFINITE",
                 8: "GBS_ERR_STATE"}
-GBS_WAVE1D, GBS_ACOUSTIC = 1, 2
+GBS_WAVE1D, GBS_ACOUSTIC, GBS_ONEWAY_SPECTRAL = 1, 2, 3
 GBS_F32_STATE_F64_COMBINE, GBS_F64, GBS_F32X2 = 0, 1, 2
 GBS_KERNEL_AUTO, GBS_KERNEL_PLAIN, GBS_KERNEL_FUSED = 0, 1, 2
 GBS_MAX_SLOTS, GBS_MAX_SEQ, GBS_MAX_STEPS = 8, 16, 64

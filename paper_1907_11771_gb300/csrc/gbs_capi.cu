@@ -125,7 +125,9 @@ gbs_status fail(gbs_ctx* h, gbs_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail((h), GBS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-int fields_of(int system, int ndim) { return system == GBS_WAVE1D ? 2 : 1 + ndim; }
+int fields_of(int system, int ndim) {
+  return system == GBS_WAVE1D ? 2 : system == GBS_ONEWAY_SPECTRAL ? 1 : 1 + ndim;
+}
 
 double symbol_max(int R) {
   // max over theta of |sum_j a_j 2 sin(j theta)| -- sampled densely, then refined
@@ -150,11 +152,21 @@ double symbol_max(int R) {
 
 gbs_status validate_problem(const gbs_problem* pb, gbs_ctx* h) {
   if (!pb) return fail(h, GBS_ERR_INVALID, "problem description is NULL");
-  if (pb->system != GBS_WAVE1D && pb->system != GBS_ACOUSTIC)
-    return fail(h, GBS_ERR_INVALID, "system must be GBS_WAVE1D or GBS_ACOUSTIC");
-  if (pb->system == GBS_WAVE1D && pb->ndim != 1) return fail(h, GBS_ERR_INVALID, "GBS_WAVE1D needs ndim == 1");
+  if (pb->system != GBS_WAVE1D && pb->system != GBS_ACOUSTIC && pb->system != GBS_ONEWAY_SPECTRAL)
+    return fail(h, GBS_ERR_INVALID, "system must be GBS_WAVE1D, GBS_ACOUSTIC or GBS_ONEWAY_SPECTRAL");
+  if (pb->system != GBS_ACOUSTIC && pb->ndim != 1) return fail(h, GBS_ERR_INVALID, "this system needs ndim == 1");
   if (pb->ndim < 1 || pb->ndim > 3) return fail(h, GBS_ERR_INVALID, "ndim must be 1, 2 or 3");
-  if (pb->fd_order != 4 && pb->fd_order != 6) return fail(h, GBS_ERR_INVALID, "fd_order must be 4 or 6");
+  if (pb->system == GBS_ONEWAY_SPECTRAL) {
+    if (pb->fd_order != 0) return fail(h, GBS_ERR_INVALID, "GBS_ONEWAY_SPECTRAL takes fd_order = 0 (spectral)");
+    if (pb->precision != GBS_F64) return fail(h, GBS_ERR_INVALID, "GBS_ONEWAY_SPECTRAL runs in GBS_F64");
+    for (int p = 0; p < pb->batch && pb->shape; ++p) {
+      const int64_t n = pb->shape[3 * p];
+      if (n < 8 || n > kSpectralMaxN || (n & (n - 1)))
+        return fail(h, GBS_ERR_INVALID, "problem %d: spectral size must be a power of two in [8, %d]", p, kSpectralMaxN);
+    }
+  } else if (pb->fd_order != 4 && pb->fd_order != 6) {
+    return fail(h, GBS_ERR_INVALID, "fd_order must be 4 or 6");
+  }
   if (pb->precision != GBS_F32_STATE_F64_COMBINE && pb->precision != GBS_F64 && pb->precision != GBS_F32X2)
     return fail(h, GBS_ERR_INVALID, "unknown precision");
   if (pb->batch < 1) return fail(h, GBS_ERR_INVALID, "batch must be >= 1");
@@ -351,6 +363,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->ds_kappa = h->ds_kappa;
   p->ds_b = h->ds_b;
   p->probs_media_elems = h->media_elems;
+  for (const ProbDev& q : h->probs) p->max_nx = std::max<int64_t>(p->max_nx, q.n[0]);
   p->F = h->F;
   p->batch = h->batch;
   p->probs = h->d_probs;
@@ -524,8 +537,8 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   *out = nullptr;
   gbs_status st = validate_problem(pb, nullptr);
   if (st != GBS_OK) return st;
-  if (pb->system == GBS_WAVE1D && (kappa || rho))
-    return fail(nullptr, GBS_ERR_INVALID, "GBS_WAVE1D takes no media (kappa and rho must be NULL)");
+  if (pb->system != GBS_ACOUSTIC && (kappa || rho))
+    return fail(nullptr, GBS_ERR_INVALID, "only GBS_ACOUSTIC takes media (kappa and rho must be NULL)");
   if (pb->system == GBS_ACOUSTIC && (!is_device_ptr(kappa) || !is_device_ptr(rho)))
     return fail(nullptr, GBS_ERR_INVALID, "kappa and rho must be device pointers");
   gbs_ctx* h = new gbs_ctx();
@@ -610,6 +623,10 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   }
   h->cmax.assign(h->batch, 1.0);
   h->fw = fused_create();
+  if (h->system == GBS_ONEWAY_SPECTRAL && spectral_setup() < 0) {
+    fail(h, GBS_ERR_CUDA, "the spectral kernel cannot get its shared memory");
+    return bail(GBS_ERR_CUDA);
+  }
   *out = h;
   if (h->system == GBS_ACOUSTIC) {
     st = gbs_set_media(h, kappa, rho);
@@ -752,10 +769,14 @@ gbs_status gbs_assign_slots(gbs_handle h, const int* slot_per_problem) {
 gbs_status gbs_stability_limit(gbs_handle h, double* H_max) {
   if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
   if (!H_max) return fail(h, GBS_ERR_INVALID, "H_max is NULL");
-  const double smax = symbol_max(h->R);
+  const double smax = h->system == GBS_ONEWAY_SPECTRAL ? 0.0 : symbol_max(h->R);
   for (int p = 0; p < h->batch; ++p) {
     const Slot& s = h->slots[h->slot_of[p]];
     if (!s.set) return fail(h, GBS_ERR_STATE, "problem %d: slot %d has no weights", p, h->slot_of[p]);
+    if (h->system == GBS_ONEWAY_SPECTRAL) {   // |i k| <= pi / dx on the grid (Sec. 4)
+      H_max[p] = s.isb / (M_PI * h->probs[p].inv_dx[0]);
+      continue;
+    }
     double q = 0;
     for (int d = 0; d < h->ndim; ++d) q += (smax * h->probs[p].inv_dx[d]) * (smax * h->probs[p].inv_dx[d]);
     const double rho_hat = h->cmax[p] * std::sqrt(q);

@@ -56,6 +56,7 @@ struct StepPlan {
   int64_t total_tiles;         // x-y tiled blocks over the whole batch (2D/3D)
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   int64_t probs_media_elems;   // scalars in one media array (sum of pts)
+  int64_t max_nx;              // largest nx over the problems
   const void* kappa;           // media (state element type)
   const void* b;               // 1 / rho
   void* f0;                    // shared first RHS, F x P
@@ -98,6 +99,12 @@ inline void timing_end(const StepPlan& p, int u, cudaStream_t s, double bytes) {
 }
 
 constexpr int kPlainBlock = 256;
+constexpr int kSpectralMaxN = 2048;   // GBS_ONEWAY_SPECTRAL: one problem's macro-step per block
+
+// One-way wave with spectral derivatives (gbs_spectral.cu): one macro-step of every problem,
+// one block per problem; returns the number of kernels launched or -1.
+int spectral_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s);
+int spectral_setup();   // opt the kernel into its shared memory (handle creation, not in a capture)
 constexpr int kTileX = 32;   // tiled step kernels: 32 x 8 threads, 4 rows per thread
 constexpr int kTileRows = 4;
 constexpr int kTileY = 8 * kTileRows;

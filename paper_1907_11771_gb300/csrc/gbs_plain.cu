@@ -1101,6 +1101,7 @@ __global__ void k_to_ds(const double* __restrict__ a, dsf* __restrict__ o, int64
 }
 
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
+  if (p.system == GBS_ONEWAY_SPECTRAL) return spectral_macro_step(p, y_in, y_out, s);
   if (p.ds) {
     // the step reads y_in, kappa and b as FP32 pairs converted here, and writes FP64 y_out
     k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(y_in), static_cast<dsf*>(p.ds_y0), p.state_elems);

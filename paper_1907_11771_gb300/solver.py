@@ -19,13 +19,13 @@ class GBSSolver:
         concatenated media tensors on the GPU (None for the 1D wave system)."""
         self.system = system
         self.shapes = [tuple(s) + (1,) * (3 - len(s)) for s in shapes]
-        self.ndim = 1 if system == B.GBS_WAVE1D else max(1, len(shapes[0]))
+        self.ndim = 1 if system != B.GBS_ACOUSTIC else max(1, len(shapes[0]))
         self.batch = len(self.shapes)
         self.precision = precision
         self.fd_order = fd_order
         self.slots = [0] * len(shapes)
         self.dtype = _DTYPES[precision]
-        self.F = 2 if system == B.GBS_WAVE1D else 1 + self.ndim
+        self.F = 2 if system == B.GBS_WAVE1D else 1 if system == B.GBS_ONEWAY_SPECTRAL else 1 + self.ndim
         self.pb = B.make_problem(system, self.ndim, fd_order, precision, self.shapes, dx, enable_adjoint)
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream().cuda_stream

@@ -59,6 +59,14 @@ def test_invalid_problems_rejected_without_gpu(libpath):
     pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F64, [(16, 16, 2)], [(1.0, 1.0, 1.0)])
     with pytest.raises(B.GbsError):
         B.gbs_create(pb)
+    # the spectral one-way wave: fd_order 0, FP64, power-of-two sizes up to 2048
+    for prec, order, n in ((B.GBS_F64, 4, 64), (B.GBS_F32_STATE_F64_COMBINE, 0, 64), (B.GBS_F64, 0, 48),
+                           (B.GBS_F64, 0, 4096)):
+        pb = B.make_problem(B.GBS_ONEWAY_SPECTRAL, 1, order, prec, [(n, 1, 1)], [(1.0 / n, 1.0, 1.0)])
+        with pytest.raises(B.GbsError):
+            B.gbs_create(pb)
+    pb = B.make_problem(B.GBS_ONEWAY_SPECTRAL, 1, 0, B.GBS_F64, [(256, 1, 1)], [(1.0 / 256, 1.0, 1.0)])
+    assert B.gbs_state_elems(pb) == 256
     # an unknown precision
     pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, 3, [(16, 16, 1)], [(1.0, 1.0, 1.0)])
     with pytest.raises(B.GbsError):
