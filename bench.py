@@ -654,8 +654,15 @@ def run_time_to_solution(args):
     paths = [("fused FP32 state + FP64-class combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
              ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64),
              ("plain FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_PLAIN, torch.float64)]
+    tuned = {}
     for name, prec, kernel, dt in paths:
         sol = solver(prec, S.GBS_8_6, kernel)
+        if kernel == B.GBS_KERNEL_FUSED and not args.no_autotune:
+            from paper_1907_11771_gb300 import autotune as AT
+            yt = torch.tensor(y0.ravel(), dtype=dt, device="cuda")
+            r = AT.autotune(sol, yt, T / M0, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
+            if r is not None:
+                tuned[name] = r["options"]
         rows[name] = []
         for j in range(args.tts_levels):
             M = M0 * 2 ** j
@@ -666,7 +673,8 @@ def run_time_to_solution(args):
     best = {k: min((r["seconds"] for r in v if r["rel_l2"] <= 1e-6), default=None) for k, v in rows.items()}
     print(json.dumps({"study": "time to relative L2 error 1e-6", "grid": [n, n], "t_final": T, "H0": H0,
                       "macro_steps_at_H0": M0, "reference": f"GBS_12,8 FP64, {Mref} macro-steps",
-                      "reference_self_check_rel_l2": ref_err, "paths": rows, "time_to_1e-6_s": best}), flush=True)
+                      "reference_self_check_rel_l2": ref_err, "paths": rows, "time_to_1e-6_s": best,
+                      "autotuned_schedule": tuned}), flush=True)
     return 0
 
 

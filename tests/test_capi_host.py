@@ -67,6 +67,11 @@ def test_invalid_problems_rejected_without_gpu(libpath):
             B.gbs_create(pb)
     pb = B.make_problem(B.GBS_ONEWAY_SPECTRAL, 1, 0, B.GBS_F64, [(256, 1, 1)], [(1.0 / 256, 1.0, 1.0)])
     assert B.gbs_state_elems(pb) == 256
+    # 2^31 grid points in one problem (32-bit point indices inside the kernels)
+    pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F32_STATE_F64_COMBINE, [(65536, 32768, 1)], [(1.0, 1.0, 1.0)])
+    with pytest.raises(B.GbsError):
+        B.gbs_create(pb)
+    assert B.gbs_state_elems(pb) == 0
     # an unknown precision
     pb = B.make_problem(B.GBS_ACOUSTIC, 2, 4, 3, [(16, 16, 1)], [(1.0, 1.0, 1.0)])
     with pytest.raises(B.GbsError):

@@ -348,3 +348,24 @@ def test_workspace_allocation_failure_is_reported():
         B.gbs_create(pb, k, k)
     assert e.value.status == 5
     assert "cudaMalloc" in B.gbs_last_error(None)
+
+
+@pytest.mark.parametrize("kernel", ["plain", "fused"])
+@pytest.mark.parametrize("steps", [(2,), (4,), (2, 4)])
+def test_degenerate_schemes(kernel, steps):
+    """One sequence with c = 1 (order 2: plain GBS, no extrapolation) and the smallest square
+    scheme {2, 4} (order 4, Richardson weights -1/3, 4/3), on the FP64 plain kernels and on the
+    FP32 time-blocked kernel (whose first pass is then also its last)."""
+    prec = F64 if kernel == "plain" else F32
+    case = AcousticCase((64, 72), 6, prec, seed=21)
+    sol = case.solver()
+    order = 2 * len(steps)
+    B.gbs_set_weights(sol.h, 0, order, list(steps), [], [])
+    if kernel == "fused":
+        sol.set_option("kernel", B.GBS_KERNEL_FUSED)
+        assert sol.uses_fused()
+    H = 0.5 * sol.stability_limit()[0] if sol.weights()[2] > 0 else 0.05
+    c = OW.to_fp64(OW.square_weights(list(steps), order))
+    err = rel_l2(case.gpu_run(sol, H, 3), case.oracle_run(list(steps), c, H, 3))
+    assert err <= TOL[prec], err
+    sol.close()
