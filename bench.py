@@ -116,6 +116,21 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(value, ws, device):
+    """The slowest rank's value (a time): a MAX all-reduce over the process group when ws > 1."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_rank, seconds):
+    """Units processed by all ranks per second of the slowest rank, in G/s (weak scaling)."""
+    return ws * units_per_rank / seconds / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,11 +343,8 @@ def run_gpu(args):
         barrier()
     launches = sol.kernel_launches - l0
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * upd_per_step * args.steps / (ms_max / 1e3) / 1e9
+    ms_max = max_over_ranks(ms, ws, "cuda")
+    value = whole_job_rate(ws, upd_per_step * args.steps, ms_max / 1e3)
 
     # dominant-kernel roofline: CUDA events recorded by the library around each launch
     sol.set_option("time_kernels", 1)
@@ -368,12 +380,9 @@ def run_gpu(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             sol.step_host(hbuf, hout, H, 1)
-        e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
         nbytes = y.numel() * y.element_size()
-        e2e = {"value": ws * upd_per_step * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(ws, upd_per_step * args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     sol.sync()
