@@ -245,27 +245,69 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   const T* cur = (n & 1) ? L1 : L0;
   T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
   const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
-  // stage p, u, v of the current level (tile + halo, periodic): rows by threadIdx.y,
-  // columns by threadIdx.x, one wrap per row and only halo columns wrapping
-  for (int r = threadIdx.y; r < Hh; r += 8) {
-    int gy = y0 - R + r;
-    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-    const T* rowp = cur + plane + (int64_t)gy * nx;
-    for (int c = threadIdx.x; c < W; c += kTileX) {
-      int gx = x0 - R + c;
+  // stage p, u, v of the current level (tile + halo, periodic): the W x Hh points are spread
+  // over the 256 threads in a fully unrolled loop that issues all of a thread's loads before
+  // its shared-memory stores, so they are in flight together
+  constexpr int NE = W * Hh, NIT = (NE + 255) / 256;
+  const int ltid = threadIdx.y * kTileX + threadIdx.x;
+  T stg[3][NIT];
+#pragma unroll
+  for (int it = 0; it < NIT; ++it) {
+    const int e = ltid + 256 * it;
+    if (e < NE) {
+      const int r = e / W, cl = e - r * W;
+      int gy = y0 - R + r;
+      if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+      int gx = x0 - R + cl;
       if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-      sh[0][r][c] = ldg(rowp + gx);
-      sh[1][r][c] = ldg(rowp + P + gx);
-      sh[2][r][c] = ldg(rowp + 2 * P + gx);
+      const T* a = cur + plane + (int64_t)gy * nx + gx;
+      stg[0][it] = ldg(a);
+      stg[1][it] = ldg(a + P);
+      stg[2][it] = ldg(a + 2 * P);
+    }
+  }
+  const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
+  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
+  const int x = x0 + threadIdx.x;
+  constexpr int F = 1 + DIM;
+  // point-wise operands of a row (previous level, media, and in 3D the z-neighbours of p and
+  // w), loaded one row ahead of their use; the first row's before the tile barrier
+  T nprev[F], nkv = T(0), nbv = T(0), nzp[R][2], nzm[R][2];
+  auto fetch_row = [&](int i) {
+    const int y = y0 + threadIdx.y + 8 * i;
+    if (x >= nx || y >= ny) return;
+    const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) nprev[fl] = prev[fl * P + pt];
+    nkv = ldg(kap + pt);
+    nbv = ldg(bmed + pt);
+    if (DIM == 3) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        const int zp = z + j >= nz ? z + j - nz : z + j;
+        const int zm = z - j < 0 ? z - j + nz : z - j;
+        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
+        nzp[j - 1][0] = ldg(cur + pt + op);
+        nzp[j - 1][1] = ldg(cur + 3 * P + pt + op);
+        nzm[j - 1][0] = ldg(cur + pt + om);
+        nzm[j - 1][1] = ldg(cur + 3 * P + pt + om);
+      }
+    }
+  };
+  fetch_row(0);
+#pragma unroll
+  for (int it = 0; it < NIT; ++it) {
+    const int e = ltid + 256 * it;
+    if (e < NE) {
+      const int r = e / W, cl = e - r * W;
+      sh[0][r][cl] = stg[0][it];
+      sh[1][r][cl] = stg[1][it];
+      sh[2][r][cl] = stg[2][it];
     }
   }
   __syncthreads();
   const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
-  const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
-  const T* bmed = static_cast<const T*>(p.b) + q.media_off;
-  const int x = x0 + threadIdx.x;
   if (x >= nx) return;
-  constexpr int F = 1 + DIM;
   const double c = s.c[k];
   const bool first = (k == 0), last = (k == s.m - 1);
 #pragma unroll
@@ -273,6 +315,20 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
     const int ly = threadIdx.y + 8 * i;
     const int y = y0 + ly;
     if (y >= ny) break;
+    T pv[F], zpv[R][2], zmv[R][2];
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) pv[fl] = nprev[fl];
+    const T kv = nkv, bv = nbv;
+    if (DIM == 3) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        zpv[j][0] = nzp[j][0];
+        zpv[j][1] = nzp[j][1];
+        zmv[j][0] = nzm[j][0];
+        zmv[j][1] = nzm[j][1];
+      }
+    }
+    if (i + 1 < kTileRows) fetch_row(i + 1);
     const int r = ly + R, cc = threadIdx.x + R;
     T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
 #pragma unroll
@@ -290,16 +346,12 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
       T szw = T(0);
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
-        const int zp = z + j >= nz ? z + j - nz : z + j;
-        const int zm = z - j < 0 ? z - j + nz : z - j;
-        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
         const T a = T(fd_coef<R>(j));
-        szp += a * (ldg(cur + pt + op) - ldg(cur + pt + om));
-        szw += a * (ldg(cur + 3 * P + pt + op) - ldg(cur + 3 * P + pt + om));
+        szp += a * (zpv[j - 1][0] - zmv[j - 1][0]);
+        szw += a * (zpv[j - 1][1] - zmv[j - 1][1]);
       }
       div += szw * idz;
     }
-    const T kv = ldg(kap + pt), bv = ldg(bmed + pt);
     T f[kMaxFields];
     f[0] = -kv * div;
     f[1] = -bv * (sxp * idx);
@@ -307,17 +359,16 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
     if (DIM == 3) f[3] = -bv * (szp * idz);
     if (n < N) {
 #pragma unroll
-      for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
+      for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = pv[fl] + h2 * f[fl];
     } else {
       double* acc = p.acc + q.state_off;
       auto* yo = y_out + q.state_off;
 #pragma unroll
       for (int fl = 0; fl < F; ++fl) {
         const int64_t e = fl * P + pt;
-        const T ym = prev[e];
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
-        const T yp = ym + h2 * f[fl];
-        combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(ym, yc, yp), yo);
+        const T yp = pv[fl] + h2 * f[fl];
+        combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(pv[fl], yc, yp), yo);
       }
     }
   }
