@@ -211,6 +211,31 @@ __device__ __forceinline__ int wrap_any(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
+// Tile staging: the (kTileX + 2R) x (kTileY + 2R) points of a tile and its halo are spread over
+// the 256 threads of a block, iteration it of thread t taking point t + 256 it (row r, column cl
+// of the staged tile).  Kernels run the iterations in fully unrolled loops that issue all of a
+// thread's loads before its shared-memory stores, so that they are in flight together.
+template <int R>
+struct TileStage {
+  static constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R, NE = W * Hh, NIT = (NE + 255) / 256;
+  // row and column of iteration it, false past the tile
+  static __device__ __forceinline__ bool rc(int it, int& r, int& cl) {
+    const int e = threadIdx.y * kTileX + threadIdx.x + 256 * it;
+    if (e >= NE) return false;
+    r = e / W;
+    cl = e - r * W;
+    return true;
+  }
+  // point offset (periodic) of staged row r, column cl, within z plane `plane`
+  static __device__ __forceinline__ int64_t at(int r, int cl, int x0, int y0, int nx, int ny, int64_t plane) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    int gx = x0 - R + cl;
+    if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+    return plane + (int64_t)gy * nx + gx;
+  }
+};
+
 template <typename T, int DIM, int R>
 __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out,
                                                    int k, int n) {
@@ -245,22 +270,14 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   const T* cur = (n & 1) ? L1 : L0;
   T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
   const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
-  // stage p, u, v of the current level (tile + halo, periodic): the W x Hh points are spread
-  // over the 256 threads in a fully unrolled loop that issues all of a thread's loads before
-  // its shared-memory stores, so they are in flight together
-  constexpr int NE = W * Hh, NIT = (NE + 255) / 256;
-  const int ltid = threadIdx.y * kTileX + threadIdx.x;
-  T stg[3][NIT];
+  // stage p, u, v of the current level (tile + halo, periodic)
+  using TS = TileStage<R>;
+  T stg[3][TS::NIT];
 #pragma unroll
-  for (int it = 0; it < NIT; ++it) {
-    const int e = ltid + 256 * it;
-    if (e < NE) {
-      const int r = e / W, cl = e - r * W;
-      int gy = y0 - R + r;
-      if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-      int gx = x0 - R + cl;
-      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-      const T* a = cur + plane + (int64_t)gy * nx + gx;
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      const T* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
       stg[0][it] = ldg(a);
       stg[1][it] = ldg(a + P);
       stg[2][it] = ldg(a + 2 * P);
@@ -296,10 +313,9 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   };
   fetch_row(0);
 #pragma unroll
-  for (int it = 0; it < NIT; ++it) {
-    const int e = ltid + 256 * it;
-    if (e < NE) {
-      const int r = e / W, cl = e - r * W;
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
       sh[0][r][cl] = stg[0][it];
       sh[1][r][cl] = stg[1][it];
       sh[2][r][cl] = stg[2][it];
@@ -429,16 +445,16 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
   const dsf* cur = (n & 1) ? L1 : L0;
   dsf* dst = (n & 1) ? L0 : L1;
   const dsf* prev = (n == 1) ? (y_in + q.state_off) : dst;
-  for (int r = threadIdx.y; r < Hh; r += 8) {
-    int gy = y0 - R + r;
-    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-    const dsf* rowp = cur + plane + (int64_t)gy * nx;
-    for (int c = threadIdx.x; c < W; c += kTileX) {
-      int gx = x0 - R + c;
-      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-      const dsf pp = ldg(rowp + gx), uu = ldg(rowp + P + gx), vv = ldg(rowp + 2 * P + gx);
-      spu[r][c] = make_float4(pp.hi, uu.hi, pp.lo, uu.lo);
-      spv[r][c] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
+  using TS = TileStage<R>;
+  dsf stg[3][TS::NIT];
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      const dsf* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
+      stg[0][it] = ldg(a);
+      stg[1][it] = ldg(a + P);
+      stg[2][it] = ldg(a + 2 * P);
     }
   }
   const dsf* kap = static_cast<const dsf*>(p.kappa) + q.media_off;
@@ -457,6 +473,15 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
     nbv = ldg(bmed + pt);
   };
   fetch_row(0);
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      const dsf pp = stg[0][it], uu = stg[1][it], vv = stg[2][it];
+      spu[r][cl] = make_float4(pp.hi, uu.hi, pp.lo, uu.lo);
+      spv[r][cl] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
+    }
+  }
   __syncthreads();
   const bool unit = q.inv_dx[0] == 1.0 && q.inv_dx[1] == 1.0 && (DIM < 3 || q.inv_dx[2] == 1.0);
   const dsf idx = dsf(q.inv_dx[0]), idy = dsf(q.inv_dx[1]), idz = dsf(q.inv_dx[2]);
@@ -698,16 +723,25 @@ __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T
   const T* cur = level(n);
   const T* prev = (n == 1) ? yi : level(n - 1);
   T* dst = level(n + 1);
-  for (int r = threadIdx.y; r < Hh; r += 8) {
-    int gy = y0 - R + r;
-    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-    const T* rowp = cur + plane + (int64_t)gy * nx;
-    for (int c = threadIdx.x; c < W; c += kTileX) {
-      int gx = x0 - R + c;
-      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-      sh[0][r][c] = ldg(rowp + gx);
-      sh[1][r][c] = ldg(rowp + P + gx);
-      sh[2][r][c] = ldg(rowp + 2 * P + gx);
+  using TS = TileStage<R>;
+  T stg[3][TS::NIT];
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      const T* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
+      stg[0][it] = ldg(a);
+      stg[1][it] = ldg(a + P);
+      stg[2][it] = ldg(a + 2 * P);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      sh[0][r][cl] = stg[0][it];
+      sh[1][r][cl] = stg[1][it];
+      sh[2][r][cl] = stg[2][it];
     }
   }
   __syncthreads();
@@ -808,21 +842,34 @@ __global__ void __launch_bounds__(256) k_adj_rev_tiled(const StepPlan p, const T
   const T* kappa = static_cast<const T*>(p.kappa) + q.media_off;
   const T* bmed = static_cast<const T*>(p.b) + q.media_off;
   const T* yj = lev + (int64_t)j * lev_stride + q.state_off;
-  for (int r = threadIdx.y; r < Hh; r += 8) {
-    int gy = y0 - R + r;
-    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
-    const int64_t row = plane + (int64_t)gy * nx;
-    for (int cc = threadIdx.x; cc < W; cc += kTileX) {
-      int gx = x0 - R + cc;
-      if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
-      const int64_t e = row + gx;
-      const T kv = ldg(kappa + e), bv = ldg(bmed + e);
-      sh[0][r][cc] = kv * ldg(src + e);
-      sh[1][r][cc] = bv * ldg(src + P + e);
-      sh[2][r][cc] = bv * ldg(src + 2 * P + e);
+  using TS = TileStage<R>;
+  T stg[NS + 2][TS::NIT];   // kappa, b, M[j+1] p, u, v, (y_j u, v)
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      const int64_t e = TS::at(r, cl, x0, y0, nx, ny, plane);
+      stg[0][it] = ldg(kappa + e);
+      stg[1][it] = ldg(bmed + e);
+      stg[2][it] = ldg(src + e);
+      stg[3][it] = ldg(src + P + e);
+      stg[4][it] = ldg(src + 2 * P + e);
       if constexpr (kStageY) {
-        sh[3][r][cc] = ldg(yj + P + e);
-        sh[4][r][cc] = ldg(yj + 2 * P + e);
+        stg[5][it] = ldg(yj + P + e);
+        stg[6][it] = ldg(yj + 2 * P + e);
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < TS::NIT; ++it) {
+    int r, cl;
+    if (TS::rc(it, r, cl)) {
+      sh[0][r][cl] = stg[0][it] * stg[2][it];
+      sh[1][r][cl] = stg[1][it] * stg[3][it];
+      sh[2][r][cl] = stg[1][it] * stg[4][it];
+      if constexpr (kStageY) {
+        sh[3][r][cl] = stg[5][it];
+        sh[4][r][cl] = stg[6][it];
       }
     }
   }
