@@ -234,11 +234,24 @@ struct TileStage {
     if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
     return plane + (int64_t)gy * nx + gx;
   }
+  // the same as a 32-bit offset (a problem has fewer than 2^31 points per field)
+  static __device__ __forceinline__ int at32(int r, int cl, int x0, int y0, int nx, int ny, int plane) {
+    int gy = y0 - R + r;
+    if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+    int gx = x0 - R + cl;
+    if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+    return plane + gy * nx + gx;
+  }
 };
 
+// resident blocks per SM the register budget of k_lf_tiled aims at (measured best: FP32 2D 5,
+// FP32 3D 4, 8-byte states 3 in 2D; 2 in 3D, where fewer registers spill)
+template <typename T, int DIM>
+constexpr int lf_min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 5 : 4) : (DIM == 2 ? 3 : 2); }
+
 template <typename T, int DIM, int R>
-__global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out,
-                                                   int k, int n) {
+__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM>())
+    k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n) {
   constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
   __shared__ T sh[3][Hh][W + 1];
   // problem of this block (binary search over the tiled-grid offsets)
@@ -262,7 +275,11 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   const int nx = q.n[0], ny = q.n[1], nz = q.n[2];
   const int x0 = tx * kTileX, y0 = ty * kTileY;
   const int64_t P = q.pts;
-  const int64_t plane = (int64_t)z * nx * ny;
+  // 3D: offsets within one field (fewer than 2^31 points per field, checked at creation) are
+  // 32-bit and every field has its own base pointer; 2D: 64-bit element offsets, which need
+  // fewer registers (each measured faster for its case)
+  using Off = typename std::conditional<DIM == 3, int, int64_t>::type;
+  const Off plane = (Off)z * nx * ny;
   T h, h2;
   step_sizes(p, lo, k, h, h2);
   T* const L0 = static_cast<T*>(p.L0) + q.state_off;
@@ -270,6 +287,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   const T* cur = (n & 1) ? L1 : L0;
   T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
   const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
+  constexpr int F = 1 + DIM;
   // stage p, u, v of the current level (tile + halo, periodic)
   using TS = TileStage<R>;
   T stg[3][TS::NIT];
@@ -277,37 +295,45 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
   for (int it = 0; it < TS::NIT; ++it) {
     int r, cl;
     if (TS::rc(it, r, cl)) {
-      const T* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
-      stg[0][it] = ldg(a);
-      stg[1][it] = ldg(a + P);
-      stg[2][it] = ldg(a + 2 * P);
+      Off o;
+      if constexpr (DIM == 3) o = TS::at32(r, cl, x0, y0, nx, ny, plane);
+      else o = TS::at(r, cl, x0, y0, nx, ny, plane);
+      stg[0][it] = ldg(cur + o);
+      stg[1][it] = ldg(cur + P + o);
+      stg[2][it] = ldg(cur + 2 * P + o);
     }
   }
   const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
   const T* bmed = static_cast<const T*>(p.b) + q.media_off;
   const int x = x0 + threadIdx.x;
-  constexpr int F = 1 + DIM;
+  const Off o0 = plane + (Off)(y0 + (int)threadIdx.y) * nx + x;   // this thread's point in row 0
+  // z-neighbour plane offsets (3D, periodic)
+  int dzp[R], dzm[R];
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const int zp = z + j >= nz ? z + j - nz : z + j;
+    const int zm = z - j < 0 ? z - j + nz : z - j;
+    dzp[j - 1] = (zp - z) * nx * ny;
+    dzm[j - 1] = (zm - z) * nx * ny;
+  }
   // point-wise operands of a row (previous level, media, and in 3D the z-neighbours of p and
   // w), loaded one row ahead of their use; the first row's before the tile barrier
   T nprev[F], nkv = T(0), nbv = T(0), nzp[R][2], nzm[R][2];
   auto fetch_row = [&](int i) {
     const int y = y0 + threadIdx.y + 8 * i;
     if (x >= nx || y >= ny) return;
-    const int64_t pt = plane + (int64_t)y * nx + x;
+    const Off o = o0 + (Off)(8 * i) * nx;
 #pragma unroll
-    for (int fl = 0; fl < F; ++fl) nprev[fl] = prev[fl * P + pt];
-    nkv = ldg(kap + pt);
-    nbv = ldg(bmed + pt);
+    for (int fl = 0; fl < F; ++fl) nprev[fl] = DIM == 3 ? (prev + fl * P)[o] : prev[fl * P + o];
+    nkv = ldg(kap + o);
+    nbv = ldg(bmed + o);
     if (DIM == 3) {
 #pragma unroll
-      for (int j = 1; j <= R; ++j) {
-        const int zp = z + j >= nz ? z + j - nz : z + j;
-        const int zm = z - j < 0 ? z - j + nz : z - j;
-        const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
-        nzp[j - 1][0] = ldg(cur + pt + op);
-        nzp[j - 1][1] = ldg(cur + 3 * P + pt + op);
-        nzm[j - 1][0] = ldg(cur + pt + om);
-        nzm[j - 1][1] = ldg(cur + 3 * P + pt + om);
+      for (int j = 0; j < R; ++j) {
+        nzp[j][0] = ldg(cur + (o + dzp[j]));
+        nzp[j][1] = ldg(cur + 3 * P + (o + dzp[j]));
+        nzm[j][0] = ldg(cur + (o + dzm[j]));
+        nzm[j][1] = ldg(cur + 3 * P + (o + dzm[j]));
       }
     }
   };
@@ -355,7 +381,7 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
       syp += a * (sh[0][r + j][cc] - sh[0][r - j][cc]);
       syv += a * (sh[2][r + j][cc] - sh[2][r - j][cc]);
     }
-    const int64_t pt = plane + (int64_t)y * nx + x;
+    const Off o = o0 + (Off)(8 * i) * nx;
     T div = sxu * idx + syv * idy;
     T szp = T(0);
     if (DIM == 3) {
@@ -375,13 +401,16 @@ __global__ void __launch_bounds__(256) k_lf_tiled(const StepPlan p, const T* y_i
     if (DIM == 3) f[3] = -bv * (szp * idz);
     if (n < N) {
 #pragma unroll
-      for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = pv[fl] + h2 * f[fl];
+      for (int fl = 0; fl < F; ++fl) {
+        if (DIM == 3) (dst + fl * P)[o] = pv[fl] + h2 * f[fl];
+        else dst[fl * P + o] = pv[fl] + h2 * f[fl];
+      }
     } else {
       double* acc = p.acc + q.state_off;
       auto* yo = y_out + q.state_off;
 #pragma unroll
       for (int fl = 0; fl < F; ++fl) {
-        const int64_t e = fl * P + pt;
+        const int64_t e = fl * P + o;
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
         const T yp = pv[fl] + h2 * f[fl];
         combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(pv[fl], yc, yp), yo);
