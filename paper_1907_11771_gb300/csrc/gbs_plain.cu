@@ -779,11 +779,28 @@ __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T
   const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
   const T* bmed = static_cast<const T*>(p.b) + q.media_off;
   const T h2 = T(2.0 * hd);
+  // previous level and media of a row, loaded one row ahead of their use
+  T nprev[F], nkv = T(0), nbv = T(0);
+  auto fetch_row = [&](int i) {
+    const int y = y0 + threadIdx.y + 8 * i;
+    if (y >= ny) return;
+    const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) nprev[fl] = prev[fl * P + pt];
+    nkv = ldg(kap + pt);
+    nbv = ldg(bmed + pt);
+  };
+  fetch_row(0);
 #pragma unroll
   for (int i = 0; i < kTileRows; ++i) {
     const int ly = threadIdx.y + 8 * i;
     const int y = y0 + ly;
     if (y >= ny) break;
+    T pv[F];
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) pv[fl] = nprev[fl];
+    const T kv = nkv, bv = nbv;
+    if (i + 1 < kTileRows) fetch_row(i + 1);
     const int r = ly + R, cc = threadIdx.x + R;
     T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
 #pragma unroll
@@ -809,14 +826,13 @@ __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T
       }
       div += szw * idz;
     }
-    const T kv = ldg(kap + pt), bv = ldg(bmed + pt);
     T f[kMaxFields];
     f[0] = -kv * div;
     f[1] = -bv * (sxp * idx);
     f[2] = -bv * (syp * idy);
     if (DIM == 3) f[3] = -bv * (szp * idz);
 #pragma unroll
-    for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = prev[fl * P + pt] + h2 * f[fl];
+    for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = pv[fl] + h2 * f[fl];
   }
 }
 
@@ -906,11 +922,38 @@ __global__ void __launch_bounds__(256) k_adj_rev_tiled(const StepPlan p, const T
   if (x >= nx) return;
   const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
   const T h2 = T(2.0 * hd);
+  // point-wise operands of a row, loaded one row ahead of their use: M[j+2] plus the seeds of
+  // lam_out, and (FP32) mu_p and the gradient pair
+  T nbase[F], nmu = T(0);
+  float2 ngp = make_float2(0.f, 0.f);
+  auto fetch_row = [&](int i) {
+    const int y = y0 + threadIdx.y + 8 * i;
+    if (y >= ny) return;
+    const int64_t pt = plane + (int64_t)y * nx + x;
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * P + pt;
+      T base = (j <= N - 1) ? dst[e] : T(0);          // M[j+2]
+      if (j >= N - 1) base += seed * lo[e];
+      nbase[fl] = base;
+    }
+    if constexpr (kStageY) {
+      nmu = ldg(src + pt);
+      ngp = gpair[q.media_off + pt];
+    }
+  };
+  fetch_row(0);
 #pragma unroll
   for (int i = 0; i < kTileRows; ++i) {
     const int ly = threadIdx.y + 8 * i;
     const int y = y0 + ly;
     if (y >= ny) break;
+    T base[F];
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) base[fl] = nbase[fl];
+    const T mu_p = nmu;
+    const float2 gp = ngp;
+    if (i + 1 < kTileRows) fetch_row(i + 1);
     const int r = ly + R, cc = threadIdx.x + R;
     const int64_t pt = plane + (int64_t)y * nx + x;
     T sx_bu = T(0), sy_bv = T(0), sx_kp = T(0), sy_kp = T(0), sdx = T(0), sdy = T(0);
@@ -955,22 +998,17 @@ __global__ void __launch_bounds__(256) k_adj_rev_tiled(const StepPlan p, const T
       if constexpr (kStageY) dv += sdz * idz;
     }
 #pragma unroll
-    for (int fl = 0; fl < F; ++fl) {
-      const int64_t e = fl * P + pt;
-      T base = (j <= N - 1) ? dst[e] : T(0);          // M[j+2]
-      if (j >= N - 1) base += seed * lo[e];
-      dst[e] = base + h2 * at[fl];
-    }
+    for (int fl = 0; fl < F; ++fl) dst[fl * P + pt] = base[fl] + h2 * at[fl];
     if constexpr (kStageY) {
       // FP32: gpair += 2h mu_p (-div y_j) in FP32 pairs (TwoProd by FMA, TwoSum); the finish
       // kernel folds the macro-step's sum into the FP64 gradient once.  GB300's FP64 pipe
       // would otherwise bound this kernel.
-      const float mu = (float)ldg(src + pt), dvf = -(float)dv;
+      const float mu = (float)mu_p, dvf = -(float)dv;
       const float pr = __fmul_rn(mu, dvf);
       const float pe = fmaf(mu, dvf, -pr);                        // mu * dvf = pr + pe exactly
       const float th = __fmul_rn(h2hi, pr);
       const float te = fmaf(h2hi, pe, fmaf(h2lo, pr, fmaf(h2hi, pr, -th)));
-      float2 acc = gpair[q.media_off + pt];
+      const float2 acc = gp;
       const float sh = __fadd_rn(acc.x, th);
       const float bv = __fsub_rn(sh, acc.x);
       const float se = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sh, bv)), __fsub_rn(th, bv));
