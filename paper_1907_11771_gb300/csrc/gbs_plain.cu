@@ -244,13 +244,16 @@ struct TileStage {
   }
 };
 
-// resident blocks per SM the register budget of k_lf_tiled aims at (measured best: FP32 2D 5,
-// FP32 3D 4, 8-byte states 3 in 2D; 2 in 3D, where fewer registers spill)
-template <typename T, int DIM>
-constexpr int lf_min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 5 : 4) : (DIM == 2 ? 3 : 2); }
+// resident blocks per SM the register budget of k_lf_tiled aims at, each measured best against
+// its neighbours: FP32 2D 6; FP32 3D 6 at R = 2 and 5 at R = 3 (6 spills there); 8-byte states
+// 3 in 2D and 2 in 3D
+template <typename T, int DIM, int R>
+constexpr int lf_min_blocks() {
+  return sizeof(T) == 4 ? (DIM == 2 ? 6 : (R == 2 ? 6 : 5)) : (DIM == 2 ? 3 : 2);
+}
 
 template <typename T, int DIM, int R>
-__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM>())
+__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n) {
   constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
   __shared__ T sh[3][Hh][W + 1];
