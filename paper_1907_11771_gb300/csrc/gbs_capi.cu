@@ -364,6 +364,8 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->ds_b = h->ds_b;
   p->probs_media_elems = h->media_elems;
   for (const ProbDev& q : h->probs) p->max_nx = std::max<int64_t>(p->max_nx, q.n[0]);
+  p->nx_vec = 1;
+  for (const ProbDev& q : h->probs) p->nx_vec &= (q.n[0] % 4 == 0) ? 1 : 0;
   p->F = h->F;
   p->batch = h->batch;
   p->probs = h->d_probs;

@@ -57,6 +57,8 @@ struct StepPlan {
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)
   int64_t probs_media_elems;   // scalars in one media array (sum of pts)
   int64_t max_nx;              // largest nx over the problems
+  int nx_vec;                  // 1 = every problem's nx is a multiple of 4, so every row of every
+                               // state buffer starts on a 16-byte boundary (vector staging)
   const void* kappa;           // media (state element type)
   const void* b;               // 1 / rho
   void* f0;                    // shared first RHS, F x P

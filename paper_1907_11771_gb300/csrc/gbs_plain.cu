@@ -244,19 +244,36 @@ struct TileStage {
   }
 };
 
+// 16-byte vector of a state type (4 floats, 2 doubles, 2 FP32 pairs)
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+template <>
+struct Vec16<dsf> {
+  using type = float4;
+};
+
 // resident blocks per SM the register budget of k_lf_tiled aims at, each measured best against
-// its neighbours: FP32 2D 6; FP32 3D 6 at R = 2 and 5 at R = 3 (6 spills there); 8-byte states
-// 3 in 2D and 2 in 3D
+// its neighbours: FP32 2D 6, FP32 3D 5; 8-byte states 3 in 2D and 2 in 3D
 template <typename T, int DIM, int R>
 constexpr int lf_min_blocks() {
-  return sizeof(T) == 4 ? (DIM == 2 ? 6 : (R == 2 ? 6 : 5)) : (DIM == 2 ? 3 : 2);
+  return sizeof(T) == 4 ? (DIM == 2 ? 6 : 5) : (DIM == 2 ? 3 : 2);
 }
 
-template <typename T, int DIM, int R>
+template <typename T, int DIM, int R, bool kVec>
 __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n) {
-  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
-  __shared__ T sh[3][Hh][W + 1];
+  constexpr int Hh = kTileY + 2 * R;
+  // staged columns: HX on each side of the tile (>= R and a whole number of 16-byte vectors)
+  constexpr int HX = 4, WS = kTileX + 2 * HX;
+  __shared__ __align__(16) T sh[3][Hh][WS];
   // problem of this block (binary search over the tiled-grid offsets)
   int lo = 0, hi = p.batch - 1;
   const int64_t blk = blockIdx.x;
@@ -291,21 +308,6 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
   const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
   constexpr int F = 1 + DIM;
-  // stage p, u, v of the current level (tile + halo, periodic)
-  using TS = TileStage<R>;
-  T stg[3][TS::NIT];
-#pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      Off o;
-      if constexpr (DIM == 3) o = TS::at32(r, cl, x0, y0, nx, ny, plane);
-      else o = TS::at(r, cl, x0, y0, nx, ny, plane);
-      stg[0][it] = ldg(cur + o);
-      stg[1][it] = ldg(cur + P + o);
-      stg[2][it] = ldg(cur + 2 * P + o);
-    }
-  }
   const T* kap = static_cast<const T*>(p.kappa) + q.media_off;
   const T* bmed = static_cast<const T*>(p.b) + q.media_off;
   const int x = x0 + threadIdx.x;
@@ -340,14 +342,66 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       }
     }
   };
-  fetch_row(0);
+  // stage p, u, v of the current level (tile + halo, periodic) with all of a thread's loads issued
+  // before its shared stores; the first row's point-wise operands are fetched in between.  kVec
+  // (every problem's nx a multiple of 4, so every row and every problem offset is a whole number
+  // of 16-byte vectors; the tile's columns start at multiples of 32 and HX is whole vectors, so
+  // every vector stays inside one period): the WS staged columns move as 16-byte vectors; else
+  // the tile's W = kTileX + 2 R columns move point by point.
+  constexpr int VW = 16 / sizeof(T);
+  using V = typename Vec16<T>::type;
+  if constexpr (kVec) {
+    constexpr int GR = WS / VW, NV = Hh * GR, NITV = (NV + 255) / 256;
+    const int ltid = threadIdx.y * kTileX + threadIdx.x;
+    V vs[3][NITV];
 #pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      sh[0][r][cl] = stg[0][it];
-      sh[1][r][cl] = stg[1][it];
-      sh[2][r][cl] = stg[2][it];
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+        int gy = y0 - R + r;
+        if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+        int gx = x0 - HX + g * VW;
+        if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+        const Off o = plane + (Off)gy * nx + gx;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) vs[f][it] = __ldg(reinterpret_cast<const V*>(cur + f * P + o));
+      }
+    }
+    fetch_row(0);
+#pragma unroll
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) *reinterpret_cast<V*>(&sh[f][r][g * VW]) = vs[f][it];
+      }
+    }
+  } else {
+    using TS = TileStage<R>;
+    T stg[3][TS::NIT];
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        Off o;
+        if constexpr (DIM == 3) o = TS::at32(r, cl, x0, y0, nx, ny, plane);
+        else o = TS::at(r, cl, x0, y0, nx, ny, plane);
+        stg[0][it] = ldg(cur + o);
+        stg[1][it] = ldg(cur + P + o);
+        stg[2][it] = ldg(cur + 2 * P + o);
+      }
+    }
+    fetch_row(0);
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        sh[0][r][cl + HX - R] = stg[0][it];
+        sh[1][r][cl + HX - R] = stg[1][it];
+        sh[2][r][cl + HX - R] = stg[2][it];
+      }
     }
   }
   __syncthreads();
@@ -374,7 +428,7 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       }
     }
     if (i + 1 < kTileRows) fetch_row(i + 1);
-    const int r = ly + R, cc = threadIdx.x + R;
+    const int r = ly + R, cc = threadIdx.x + HX;
     T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
@@ -1138,8 +1192,10 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
       const int u = timing_begin(p, st);
       if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
         k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+      else if (SYS == SYS_ACOUSTIC && DIM >= 2 && p.nx_vec)
+        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else if (SYS == SYS_ACOUSTIC && DIM >= 2)
-        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else
         k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
       timing_end(p, u, st, p.tev ? p.unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + n] : 0.0);
