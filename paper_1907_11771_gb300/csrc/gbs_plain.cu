@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
 // point so that each stencil operand is one 16-byte shared load.  Same steps, averaging and
 // FP64 combine as k_lf_tiled.
 template <int R>
-__device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 2 * R + 1], int r, int cc, bool along_x) {
+__device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 8], int r, int cc, bool along_x) {
   ds2 s{};
 #pragma unroll
   for (int j = 1; j <= R; ++j) {
@@ -498,11 +498,12 @@ __device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 2 * R + 1]
   return s;
 }
 
-template <int DIM, int R>
+template <int DIM, int R, bool kVec>
 __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const StepPlan p, const dsf* y_in, double* y_out, int k, int n) {
-  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
-  __shared__ float4 spu[Hh][W + 1];   // (p.hi, u.hi, p.lo, u.lo)
-  __shared__ float4 spv[Hh][W + 1];   // (p.hi, v.hi, p.lo, v.lo)
+  // staged columns: HX = 4 on each side of the tile (>= R, whole 16-byte vectors of two pairs)
+  constexpr int Hh = kTileY + 2 * R, HX = 4, WS = kTileX + 2 * HX;
+  __shared__ float4 spu[Hh][WS];   // (p.hi, u.hi, p.lo, u.lo)
+  __shared__ float4 spv[Hh][WS];   // (p.hi, v.hi, p.lo, v.lo)
   int lo = 0, hi = p.batch - 1;
   const int64_t blk = blockIdx.x;
   while (lo < hi) {
@@ -531,18 +532,6 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
   const dsf* cur = (n & 1) ? L1 : L0;
   dsf* dst = (n & 1) ? L0 : L1;
   const dsf* prev = (n == 1) ? (y_in + q.state_off) : dst;
-  using TS = TileStage<R>;
-  dsf stg[3][TS::NIT];
-#pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      const dsf* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
-      stg[0][it] = ldg(a);
-      stg[1][it] = ldg(a + P);
-      stg[2][it] = ldg(a + 2 * P);
-    }
-  }
   const dsf* kap = static_cast<const dsf*>(p.kappa) + q.media_off;
   const dsf* bmed = static_cast<const dsf*>(p.b) + q.media_off;
   const int x = x0 + threadIdx.x;
@@ -558,14 +547,62 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
     nkv = ldg(kap + pt);
     nbv = ldg(bmed + pt);
   };
-  fetch_row(0);
+  // stage the tile and its halo with all of a thread's loads issued before its shared stores (the
+  // first row's point-wise operands in between): as 16-byte vectors of two pairs when kVec
+  // (every nx a multiple of 4, the staged rows widened to WS columns), else point by point
+  if constexpr (kVec) {
+    constexpr int GR = WS / 2, NV = Hh * GR, NITV = (NV + 255) / 256;
+    const int ltid = threadIdx.y * kTileX + threadIdx.x;
+    float4 vs[3][NITV];   // (hi, lo) of two consecutive points of p, u, v
 #pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      const dsf pp = stg[0][it], uu = stg[1][it], vv = stg[2][it];
-      spu[r][cl] = make_float4(pp.hi, uu.hi, pp.lo, uu.lo);
-      spv[r][cl] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+        int gy = y0 - R + r;
+        if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+        int gx = x0 - HX + 2 * g;
+        if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+        const dsf* a = cur + plane + (int64_t)gy * nx + gx;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) vs[f][it] = __ldg(reinterpret_cast<const float4*>(a + f * P));
+      }
+    }
+    fetch_row(0);
+#pragma unroll
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+        const float4 pp = vs[0][it], uu = vs[1][it], vv = vs[2][it];
+        spu[r][2 * g] = make_float4(pp.x, uu.x, pp.y, uu.y);
+        spu[r][2 * g + 1] = make_float4(pp.z, uu.z, pp.w, uu.w);
+        spv[r][2 * g] = make_float4(pp.x, vv.x, pp.y, vv.y);
+        spv[r][2 * g + 1] = make_float4(pp.z, vv.z, pp.w, vv.w);
+      }
+    }
+  } else {
+    using TS = TileStage<R>;
+    dsf stg[3][TS::NIT];
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        const dsf* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
+        stg[0][it] = ldg(a);
+        stg[1][it] = ldg(a + P);
+        stg[2][it] = ldg(a + 2 * P);
+      }
+    }
+    fetch_row(0);
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        const dsf pp = stg[0][it], uu = stg[1][it], vv = stg[2][it];
+        spu[r][cl + HX - R] = make_float4(pp.hi, uu.hi, pp.lo, uu.lo);
+        spv[r][cl + HX - R] = make_float4(pp.hi, vv.hi, pp.lo, vv.lo);
+      }
     }
   }
   __syncthreads();
@@ -579,7 +616,7 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
     const int ly = threadIdx.y + 8 * i;
     const int y = y0 + ly;
     if (y >= ny) break;
-    const int r = ly + R, cc = threadIdx.x + R;
+    const int r = ly + R, cc = threadIdx.x + HX;
     dsf pv[4];
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl) pv[fl] = nprev[fl];
@@ -1191,7 +1228,8 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
       const int u = timing_begin(p, st);
       if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
-        k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+        p.nx_vec ? k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n)
+                 : k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else if (SYS == SYS_ACOUSTIC && DIM >= 2 && p.nx_vec)
         k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
       else if (SYS == SYS_ACOUSTIC && DIM >= 2)
