@@ -808,11 +808,12 @@ __device__ __forceinline__ TileLoc tile_of(const StepPlan& p) {
 }
 
 // Forward level store, tiled: lev[n+1] = lev[n-1] + 2h f(lev[n]) (n >= 1), lev[1] = y_in + h f0.
-template <typename T, int DIM, int R>
+template <typename T, int DIM, int R, bool kVec>
 __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T* __restrict__ y_in, T* lev,
                                                        int64_t lev_stride, int k, int n) {
-  constexpr int W = kTileX + 2 * R, Hh = kTileY + 2 * R;
-  __shared__ T sh[3][Hh][W + 1];
+  // staged columns: HX = 4 on each side of the tile (>= R, whole 16-byte vectors)
+  constexpr int Hh = kTileY + 2 * R, HX = 4, WS = kTileX + 2 * HX;
+  __shared__ __align__(16) T sh[3][Hh][WS];
   const TileLoc tl = tile_of(p);
   const ProbDev& q = p.probs[tl.prob];
   const SlotDev& s = p.slots[q.slot];
@@ -846,25 +847,56 @@ __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T
   const T* cur = level(n);
   const T* prev = (n == 1) ? yi : level(n - 1);
   T* dst = level(n + 1);
-  using TS = TileStage<R>;
-  T stg[3][TS::NIT];
+  // stage the level (vectors when kVec: every nx a multiple of 4, as in k_lf_tiled)
+  if constexpr (kVec) {
+    constexpr int VW = 16 / sizeof(T), GR = WS / VW, NV = Hh * GR, NITV = (NV + 255) / 256;
+    using V = typename Vec16<T>::type;
+    const int ltid = threadIdx.y * kTileX + threadIdx.x;
+    V vs[3][NITV];
 #pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      const T* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
-      stg[0][it] = ldg(a);
-      stg[1][it] = ldg(a + P);
-      stg[2][it] = ldg(a + 2 * P);
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+        int gy = y0 - R + r;
+        if (gy < 0 || gy >= ny) gy = wrap_any(gy, ny);
+        int gx = x0 - HX + g * VW;
+        if (gx < 0 || gx >= nx) gx = wrap_any(gx, nx);
+        const T* a = cur + plane + (int64_t)gy * nx + gx;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) vs[f][it] = __ldg(reinterpret_cast<const V*>(a + f * P));
+      }
     }
-  }
 #pragma unroll
-  for (int it = 0; it < TS::NIT; ++it) {
-    int r, cl;
-    if (TS::rc(it, r, cl)) {
-      sh[0][r][cl] = stg[0][it];
-      sh[1][r][cl] = stg[1][it];
-      sh[2][r][cl] = stg[2][it];
+    for (int it = 0; it < NITV; ++it) {
+      const int e = ltid + 256 * it;
+      if (e < NV) {
+        const int r = e / GR, g = e - r * GR;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) *reinterpret_cast<V*>(&sh[f][r][g * VW]) = vs[f][it];
+      }
+    }
+  } else {
+    using TS = TileStage<R>;
+    T stg[3][TS::NIT];
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        const T* a = cur + TS::at(r, cl, x0, y0, nx, ny, plane);
+        stg[0][it] = ldg(a);
+        stg[1][it] = ldg(a + P);
+        stg[2][it] = ldg(a + 2 * P);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < TS::NIT; ++it) {
+      int r, cl;
+      if (TS::rc(it, r, cl)) {
+        sh[0][r][cl + HX - R] = stg[0][it];
+        sh[1][r][cl + HX - R] = stg[1][it];
+        sh[2][r][cl + HX - R] = stg[2][it];
+      }
     }
   }
   __syncthreads();
@@ -895,7 +927,7 @@ __global__ void __launch_bounds__(256) k_adj_fwd_tiled(const StepPlan p, const T
     for (int fl = 0; fl < F; ++fl) pv[fl] = nprev[fl];
     const T kv = nkv, bv = nbv;
     if (i + 1 < kTileRows) fetch_row(i + 1);
-    const int r = ly + R, cc = threadIdx.x + R;
+    const int r = ly + R, cc = threadIdx.x + HX;
     T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
@@ -1266,7 +1298,8 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
     const int Nk = p.max_steps_k[k];
     for (int n = 0; n <= Nk; ++n) {
       if (DIM >= 2)
-        k_adj_fwd_tiled<T, DIM, R><<<tgrid, tblock, 0, st>>>(p, y_in, lev, lev_stride, k, n);
+        p.nx_vec ? k_adj_fwd_tiled<T, DIM, R, true><<<tgrid, tblock, 0, st>>>(p, y_in, lev, lev_stride, k, n)
+                 : k_adj_fwd_tiled<T, DIM, R, false><<<tgrid, tblock, 0, st>>>(p, y_in, lev, lev_stride, k, n);
       else
         k_adj_fwd<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, lev, lev_stride, k, n);
       ++launches;
