@@ -374,7 +374,7 @@ def run_gpu(args):
     if not isinstance(H, list):
         hbuf = torch.empty(y.numel(), dtype=y.dtype, pin_memory=True)
         hbuf.copy_(y.cpu())
-        hout = torch.empty_like(hbuf)
+        hout = torch.empty(y.numel(), dtype=y.dtype, pin_memory=True)   # empty_like would not pin
         sol.step_host(hbuf, hout, H, 1)
         barrier()
         t0 = time.perf_counter()
