@@ -33,8 +33,9 @@ def _built():
 
 @pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("scheme", [S.GBS_8_6, S.SQ8_2468])
-def test_acoustic2d_parity(order, scheme):
-    case = AcousticCase((37, 53), order, X2, seed=3)
+@pytest.mark.parametrize("shape", [(37, 53), (40, 68)])   # point-by-point and vector staging
+def test_acoustic2d_parity(order, scheme, shape):
+    case = AcousticCase(shape, order, X2, seed=3)
     sol = case.solver()
     sol.set_scheme(scheme)
     assert not sol.uses_fused()
@@ -46,7 +47,8 @@ def test_acoustic2d_parity(order, scheme):
 
 
 def test_acoustic3d_and_1d_parity():
-    for shape, order, scheme, n in (((11, 14, 19), 4, S.GBS_8_6, 2), ((45,), 6, S.GBS_12_8, 4)):
+    for shape, order, scheme, n in (((11, 14, 19), 4, S.GBS_8_6, 2), ((11, 14, 20), 4, S.GBS_8_6, 2),
+                                    ((45,), 6, S.GBS_12_8, 4)):
         case = AcousticCase(shape, order, X2, seed=5)
         sol = case.solver()
         sol.set_scheme(scheme)

@@ -101,8 +101,9 @@ def test_wave1d_config1_fp64_parity_and_dalembert():
 @pytest.mark.parametrize("precision", [F64, F32])
 @pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("scheme", [S.GBS_8_6, S.SQ8_2468])
-def test_acoustic2d_parity(precision, order, scheme):
-    case = AcousticCase((37, 53), order, precision, seed=3)
+@pytest.mark.parametrize("shape", [(37, 53), (40, 68)])   # nx odd: point-by-point staging; nx % 4 == 0: vectors
+def test_acoustic2d_parity(precision, order, scheme, shape):
+    case = AcousticCase(shape, order, precision, seed=3)
     sol = case.solver()
     sol.set_scheme(scheme)
     H = 0.8 * sol.stability_limit()[0]
@@ -115,8 +116,9 @@ def test_acoustic2d_parity(precision, order, scheme):
 
 
 @pytest.mark.parametrize("precision", [F64, F32])
-def test_acoustic3d_parity(precision):
-    case = AcousticCase((11, 14, 19), 4, precision, seed=5)
+@pytest.mark.parametrize("shape", [(11, 14, 19), (11, 14, 20)])
+def test_acoustic3d_parity(precision, shape):
+    case = AcousticCase(shape, 4, precision, seed=5)
     sol = case.solver()
     sol.set_scheme(S.GBS_8_6)
     H = 0.8 * sol.stability_limit()[0]
@@ -239,9 +241,11 @@ def test_stability_limit_bounds_spectral_radius():
 
 
 @pytest.mark.parametrize("precision", [F64, F32])
-@pytest.mark.parametrize("shape,order", [((20, 23), 4), ((45, 70), 6), ((9, 10, 11), 4)])
+@pytest.mark.parametrize("shape,order", [((20, 23), 4), ((45, 70), 6), ((9, 10, 11), 4), ((20, 24), 4),
+                                         ((40, 68), 6), ((9, 10, 12), 4)])
 def test_adjoint_parity(precision, shape, order):
-    # one tile; several 32 x 32 tiles with ragged edges; 3D (z-stencils through the cache)
+    # one tile; several 32 x 32 tiles with ragged edges; 3D (z-stencils through the cache); each
+    # with an odd nx and with nx % 4 == 0 (vector staging of the forward recompute)
     case = AcousticCase(shape, order, precision, seed=6)
     sol = case.solver(enable_adjoint=True)
     sol.set_scheme(S.GBS_8_6)
