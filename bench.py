@@ -412,10 +412,11 @@ def run_gpu(args):
 def run_adjoint(args):
     """Misfit-gradient throughput: one step = J and dJ/dkappa over M macro-steps (forward sweep with
     a checkpoint every C, then the backward sweep recomputing each segment and running the
-    adjoint macro-steps), 2D acoustics n x n (default 1024^2), 4th-order FD, rho = 1, 16-Gaussian
-    kappa, Gaussian pressure source sigma = 8, 64 receivers on the row 3n/4, GBS_8,6 in FP32.
-    Counted work: M forward plus M adjoint macro-steps of P x 143 updates; the checkpoint
-    recomputation is overhead.  Observed data: a forward run of the same solver with a perturbed
+    adjoint macro-steps; with --adj-snapshots S a binomial schedule of S stored states instead),
+    2D acoustics n x n (default 1024^2), 4th-order FD, rho = 1, 16-Gaussian kappa, Gaussian
+    pressure source sigma = 8, 64 receivers on the row 3n/4, GBS_8,6 in FP32.  Counted work: M
+    forward plus M adjoint macro-steps of P x 143 updates; the checkpoint recomputation is
+    overhead.  Observed data: a forward run of the same solver with a perturbed
     kappa (kappa + 0.05 x one more seeded Gaussian)."""
     import numpy as np
     import torch
@@ -431,6 +432,8 @@ def run_adjoint(args):
     Bld.build()
     n = args.grid if args.grid != N_GRID else 1024
     M, C = args.adj_macro, args.adj_checkpoint
+    SN = args.adj_snapshots or None
+    ckpt_desc = f"binomial checkpointing with {SN} stored states" if SN else f"checkpoint every {C}"
     y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, 8.0, const_rho=True, dtype=np.float32)
     bump = inputs.smooth_media((n, n), 1, 7, 1.0) - 1.0        # one more seeded Gaussian
     tk = torch.tensor(kappa.ravel(), device="cuda")
@@ -454,7 +457,7 @@ def run_adjoint(args):
     upd = 2 * M * P * S.GBS_8_6.updates_per_point
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
-        gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+        gbs_misfit_and_grad(sol, y, H, M, rcv, data, C, SN)
     torch.cuda.synchronize()
     l0 = sol.kernel_launches
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -462,7 +465,7 @@ def run_adjoint(args):
         for i in range(args.steps):
             flush.fill_(float(i))
             evs[i][0].record()
-            J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+            J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C, SN)
             evs[i][1].record()
         torch.cuda.synchronize()
     launches = sol.kernel_launches - l0
@@ -495,7 +498,7 @@ def run_adjoint(args):
         y.copy_(hy, non_blocking=True)
         tk.copy_(hk, non_blocking=True)
         data.copy_(hd, non_blocking=True)
-        J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C)
+        J, g = gbs_misfit_and_grad(sol, y, H, M, rcv, data, C, SN)
         hg.copy_(g, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
@@ -506,10 +509,10 @@ def run_adjoint(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": (f"misfit gradient: 2D acoustics {n}x{n}, 4th-order FD, rho = 1, 64 receivers, "
-                                    f"GBS_8,6 FP32, {M} macro-steps, checkpoint every {C}; one step = forward + "
+                                    f"GBS_8,6 FP32, {M} macro-steps, {ckpt_desc}; one step = forward + "
                                     f"checkpointed backward; updates counted: {M} forward + {M} adjoint macro-steps"),
                        "shapes": [[n, n]], "scheme": "GBS_8,6", "updates_per_step_per_gpu": upd,
-                       "macro_steps": M, "checkpoint_every": C, "misfit_J": J,
+                       "macro_steps": M, "checkpoint_every": None if SN else C, "snapshots": SN, "misfit_J": J,
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas x1"},
             "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
     print(json.dumps(line), flush=True)
@@ -707,6 +710,8 @@ def main():
                          "adjoint (misfit gradient, 1024^2) or oneway (Sec. 4 spectral test problem)")
     ap.add_argument("--adj-macro", type=int, default=100, help="macro-steps of one misfit gradient (adjoint workload)")
     ap.add_argument("--adj-checkpoint", type=int, default=50, help="checkpoint interval (adjoint workload)")
+    ap.add_argument("--adj-snapshots", type=int, default=0,
+                    help="binomial checkpointing with this many stored states instead (adjoint workload)")
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")

@@ -10,6 +10,9 @@
   reverse, recomputes each segment's states from its checkpoint, and runs the
   adjoint macro-steps backwards through it (residuals injected at each
   macro-step end).  Memory: n_macro / C + C states instead of n_macro.
+  With ``snapshots=s`` it follows a binomial ("revolve") schedule instead
+  (``checkpoint.revolve_plan``): s + 1 states, and the least number of
+  recomputed macro-steps that s stored states allow.
 * ``GBSMisfitFn``: the same as an autograd Function of kappa.
 
 Every computation runs in libgbs.so; tensors only carry memory.
@@ -17,6 +20,7 @@ Every computation runs in libgbs.so; tensors only carry memory.
 import torch
 
 from . import binding as B
+from .checkpoint import WORK, revolve_plan
 
 
 def _stream():
@@ -55,11 +59,15 @@ class GBSStepFn(torch.autograd.Function):
         return lam, grad.to(y_in.dtype), None, None, None
 
 
-def gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every=50):
+def gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every=50, snapshots=None):
     """Return (J, dJ/dkappa as an FP64 tensor) for ``n_macro`` macro-steps from y0.
 
     rcv_idx: int64 device tensor of flat grid indices (field 0 of a single problem);
-    data: device tensor (n_macro, n_rcv) of observed pressures at macro-step ends."""
+    data: device tensor (n_macro, n_rcv) of observed pressures at macro-step ends.
+    snapshots: None for two-level checkpointing every ``checkpoint_every`` macro-steps,
+    else the number of stored states of a binomial schedule (y_0 included)."""
+    if snapshots is not None:
+        return _misfit_and_grad_revolve(solver, y0, H, n_macro, rcv_idx, data, int(snapshots))
     C = max(1, int(checkpoint_every))
     dev = y0.device
     n_rcv = rcv_idx.numel()
@@ -87,11 +95,46 @@ def gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every=
             solver.step(states[-1], nxt, H, 1)
             states.append(nxt)
         for m in range(s1 - 1, s0 - 1, -1):
-            if m >= 1:
-                solver.adjoint_step(states[m - s0], lam, lam, grad, H, rcv_idx, resid[m - 1])
-            else:
-                solver.adjoint_step(states[m - s0], lam, lam, grad, H)
+            _adjoint_macro_step(solver, states[m - s0], lam, grad, H, m, rcv_idx, resid)
         del states
+    solver.sync()
+    return float(J.item()), grad
+
+
+def _adjoint_macro_step(solver, y_m, lam, grad, H, m, rcv_idx, resid):
+    """lam <- dJ/dy_m from dJ/dy_(m+1): the adjoint of macro-step m, plus the residual at t_m."""
+    if m >= 1:
+        solver.adjoint_step(y_m, lam, lam, grad, H, rcv_idx, resid[m - 1])
+    else:
+        solver.adjoint_step(y_m, lam, lam, grad, H)
+
+
+def _misfit_and_grad_revolve(solver, y0, H, n_macro, rcv_idx, data, s):
+    """gbs_misfit_and_grad with s stored states placed by a binomial schedule."""
+    plan = revolve_plan(n_macro, s)
+    dev = y0.device
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    resid = torch.empty(n_macro, rcv_idx.numel(), dtype=y0.dtype, device=dev)
+    slots = [y0.detach().clone()] + [torch.empty_like(y0) for _ in range(plan.max_slots - 1)]
+    work = y0.detach().clone()
+    buf = lambda k: work if k == WORK else slots[k]
+    stores = dict(plan.forward_stores)
+    # forward sweep: misfit at every macro-step end, the first descent's states stored on the way
+    for m in range(n_macro):
+        solver.step(work, work, H, 1)
+        solver.misfit(work, rcv_idx, data[m], resid[m], J)
+        if (m + 1) in stores:
+            slots[stores[m + 1]].copy_(work)
+    grad = torch.zeros(solver.state_elems // solver.F, dtype=torch.float64, device=dev)
+    lam = torch.zeros_like(y0)
+    solver.inject(lam, rcv_idx, resid[n_macro - 1])
+    for act in plan.actions:
+        if act[0] == "advance":
+            _, src, dst, a, m = act
+            solver.step(buf(src), buf(dst), H, m - a)
+        else:
+            _, k, m = act
+            _adjoint_macro_step(solver, buf(k), lam, grad, H, m, rcv_idx, resid)
     solver.sync()
     return float(J.item()), grad
 
@@ -100,14 +143,14 @@ class GBSMisfitFn(torch.autograd.Function):
     """J(kappa) = receiver misfit after n_macro macro-steps; backward gives dJ/dkappa."""
 
     @staticmethod
-    def forward(ctx, kappa, solver, y0, H, n_macro, rcv_idx, data, checkpoint_every):
+    def forward(ctx, kappa, solver, y0, H, n_macro, rcv_idx, data, checkpoint_every, snapshots=None):
         if kappa.data_ptr() != solver._media[0].data_ptr():
             raise ValueError("kappa must be the tensor the solver was created with")
-        J, g = gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every)
+        J, g = gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every, snapshots)
         ctx.save_for_backward(g)
         return torch.tensor(J, dtype=torch.float64, device=kappa.device)
 
     @staticmethod
     def backward(ctx, gJ):
         (g,) = ctx.saved_tensors
-        return (gJ * g).to(torch.float64), None, None, None, None, None, None, None
+        return (gJ * g).to(torch.float64), None, None, None, None, None, None, None, None

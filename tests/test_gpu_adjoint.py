@@ -1,8 +1,9 @@
 """GPU parity of the discrete adjoint and of the autograd / checkpointing layer.
 
 * receiver misfit J and dJ/dkappa over several macro-steps with two-level
-  checkpointing (segments of C macro-steps, the last one partial) against the
-  oracle's FP64 misfit_and_gradient;
+  checkpointing (segments of C macro-steps, the last one partial) and with
+  binomial checkpointing (s stored states) against the oracle's FP64
+  misfit_and_gradient;
 * dJ/dkappa against central finite differences of the GPU forward on seeded
   directions (FP64 path);
 * GBSStepFn / GBSMisfitFn through torch.autograd.
@@ -45,11 +46,13 @@ def _setup(precision, shape=(24, 28), n_macro=7, seed=5):
     return case, sol, H, rcv, data, t
 
 
-@pytest.mark.parametrize("precision,ckpt", [(F64, 3), (F64, 100), (F32, 3)])
-def test_misfit_gradient_with_checkpointing_matches_oracle(precision, ckpt):
+@pytest.mark.parametrize("precision,ckpt,snaps", [(F64, 3, None), (F64, 100, None), (F32, 3, None),
+                                                 (F64, None, 2), (F64, None, 3), (F32, None, 2)])
+def test_misfit_gradient_with_checkpointing_matches_oracle(precision, ckpt, snaps):
     n_macro = 7
     case, sol, H, rcv, data, t = _setup(precision, n_macro=n_macro)
-    J, g = gbs_misfit_and_grad(sol, t["y0"], H, n_macro, t["rcv"], t["data"], checkpoint_every=ckpt)
+    J, g = gbs_misfit_and_grad(sol, t["y0"], H, n_macro, t["rcv"], t["data"], checkpoint_every=ckpt or 1,
+                               snapshots=snaps)
     steps, c = oracle_scheme(S.GBS_8_6)
     oJ, og = OG.misfit_and_gradient(case.f, case.fT, case.pair, case.y0, H, steps, c, n_macro, rcv, data)
     tol = 1e-10 if precision == F64 else 2e-5
