@@ -11,27 +11,48 @@ a bisection over h around the convex minimax subproblem (eq. "cvx_subproblem")
 
 The order constraints are kept exact by eliminating the dependent weights,
 c_dep = V_dep^-1 (b - V_free c_free) (Sec. 3.7 eq. "cdep_computation"), so R
-is affine in c_free.  The value of the subproblem
-is never below zero (|R(0)| = 1), so its optimal set is degenerate; what the
-bisection needs is feasibility -- some c_free with |R|^2 <= 1 + tol on every
-sample of the contour -- which is decided by minimising the convex penalty
-sum_j max(0, |R_j|^2 - 1)^2 (L-BFGS on scaled variables).  One more linear constraint keeps the
-stability region open along the axis near the origin: with R(xi) = e^xi +
-e_(p+1) xi^(p+1) + e_(p+2) xi^(p+2) + ..., |R(iy)|^2 - 1 starts with
-2 s (e_(p+1) - e_(p+2)) y^(p+2), s = +1 for p = 0 mod 4 and -1 for p = 2 mod 4,
-which must be negative (the sign of a_(p+2) in Sec. 3.5).
+is affine in c_free.  Since |R(0)| = 1 the subproblem's value is never below
+zero; the bisection needs its feasibility at a given h, decided here by linear
+programming on samples y_j of the contour:
+
+* |R_j| <= 1 - mu_j is the intersection of the half-planes
+  Re(e^(-i phi) R_j) <= 1 - mu_j over all phi.  The LP starts from eight
+  angles per sample and adds the tangent cut at phi = arg R_j wherever the
+  solution still leaves the circle (cutting planes), until every sample holds
+  to 1e-13.  mu_j = margin min(1, (h y_j / 4)^(p+2)) keeps the solution off the
+  circle away from the origin.
+* Near the origin the free weights move R only at O(y^(p+1)) (the order
+  constraints), below rounding: samples where they cannot move R by 1e-8 of
+  their largest effect are left to one linear constraint that keeps the
+  stability region open along the axis.  With R(xi) = e^xi + e_(p+1) xi^(p+1)
+  + e_(p+2) xi^(p+2) + ..., |R(iy)|^2 - 1 starts with
+  2 s (e_(p+1) - e_(p+2)) y^(p+2), s = +1 for p = 0 mod 4 and -1 for
+  p = 2 mod 4, which must be negative (the sign of a_(p+2) in Sec. 3.5); its
+  margin is relative, since these coefficients scale like 1/(p+1)!.
+* The LP's objective is a margin t weighted by each sample's sensitivity to
+  the free weights, which makes the LP always feasible and picks a central
+  point; h is feasible when the cut loop converges.
+* Exchange: the solution is checked on a grid `refine` times finer, points
+  that leave the circle (by more than half the margin) join the samples, and
+  the LP is solved again.
+* Every LP is centred on the weights of the largest feasible h so far, which
+  keeps its right-hand sides moderate.
 
 Stability polynomials are evaluated through the GBS recurrence on the test
 equation (well conditioned on the imaginary axis for |h lambda| <= N_k).
 This is a host-side design tool: it produces weights for gbs_set_weights and is
-checked by exact root isolation of the resulting R.
+checked by exact root isolation of the resulting R.  For order 8 on all even
+counts up to 22 and up to 30, and order 4 up to 28, it reproduces the optimal
+ISB_n the paper prints (Sec. 3.8, Table 2); at order 12 and 16 the LP's
+tolerances no longer resolve the constraints (rows whose sensitivities span
+many decades) and it stops short of the printed optima.
 """
 from dataclasses import dataclass
 from fractions import Fraction
 from math import factorial
 
 import numpy as np
-from scipy.optimize import minimize
+from scipy.optimize import linprog
 
 
 def _vandermonde(steps, order):
@@ -106,33 +127,18 @@ class OptResult:
     steps_dep: tuple
     steps_free: tuple
     c_free: np.ndarray
-    isb: float          # the bisection's h (ISB of the optimised scheme, up to the LP tolerance)
+    isb: float          # the bisection's h (ISB of the optimised scheme, up to the sampling)
     isb_n: float        # isb / (N_max + 1)
 
 
-def _solve_samples(h, steps, c0, G, lead, x0, ys, margin, order, penalty_scale=1e10):
-    """For fixed h, minimise sum_j max(0, |R(i h y_j)|^2 - 1 + m_j)^2 (+ the lead-term hinge)
-    over the free weights: convex and once differentiable (each |R_j|^2 is a convex
-    quadratic of the affine R_j).  Returns the weights."""
-    xi = 1j * h * ys
-    P = np.stack([gbs_poly_values(n, xi) for n in steps], axis=1)     # samples x m
-    Q0, QG = P @ c0, P @ G
-    m = _margin(h, ys, margin, order)
-    D = 1.0 / np.maximum(np.linalg.norm(QG, axis=0), 1e-300)         # variable scaling x = D z
-    QGs = QG * D[None, :]
-    la, lb = lead
-    la_s = la * D
-
-    def f(z):
-        R = Q0 + QGs @ z
-        v = np.maximum(R.real ** 2 + R.imag ** 2 - 1.0 + m, 0.0) * penalty_scale
-        lv = max(la_s @ z + lb, 0.0) * penalty_scale
-        dg = 2.0 * (R.real[:, None] * QGs.real + R.imag[:, None] * QGs.imag)
-        return float(np.sum(v * v) + lv * lv), 2.0 * penalty_scale * ((v[:, None] * dg).sum(0) + lv * la_s)
-
-    res = minimize(f, np.asarray(x0, float) / D, jac=True, method="L-BFGS-B",
-                   options={"maxiter": 20000, "ftol": 1e-32, "gtol": 1e-32, "maxcor": 30})
-    return res.x * D
+def _lead_constraint(order, steps, c0, G):
+    """(g, r): 2 s (e_(p+1) - e_(p+2)) = g . c_free + r, the leading term of |R(iy)|^2 - 1."""
+    coef = np.array([[float(v) for v in gbs_poly_coeffs(n, order + 2)] for n in steps])   # m x (p+3)
+    ek = lambda k: (coef[:, k] @ G, coef[:, k] @ c0 - 1.0 / factorial(k))
+    g1, r1 = ek(order + 1)
+    g2, r2 = ek(order + 2)
+    sg = 1.0 if order % 4 == 0 else -1.0
+    return 2 * sg * (g1 - g2), 2 * sg * (r1 - r2)
 
 
 def _margin(h, ys, margin, order):
@@ -141,70 +147,95 @@ def _margin(h, ys, margin, order):
     return margin * np.minimum(1.0, (h * ys / 4.0) ** (order + 2))
 
 
-def _violations(h, steps, c0, G, lead, x, ys, margin, order):
-    xi = 1j * h * ys
-    P = np.stack([gbs_poly_values(n, xi) for n in steps], axis=1)
-    R = P @ (c0 + G @ x)
-    return R.real ** 2 + R.imag ** 2 - 1.0 + _margin(h, ys, margin, order), float(lead[0] @ x + lead[1])
+def _lp_feasible(h, steps, c0, G, lead, order, ys, margin, x0, tol=1e-13, angles=8, rounds=40):
+    """Free weights with |R(i h y_j)| <= 1 - mu_j on the samples and the lead term negative,
+    by cutting planes around x0; None if the LP proves none exists or the cuts do not settle."""
+    P = np.stack([gbs_poly_values(n, 1j * h * ys) for n in steps], axis=1)
+    a, B = P @ (c0 + G @ x0), P @ G
+    D = 1.0 / np.maximum(np.abs(B).max(axis=0), 1e-300)     # column scaling: x = x0 + D z
+    Bs = B * D[None, :]
+    sens = np.abs(Bs).max(axis=1)
+    keep = sens > 1e-8
+    a, Bs, sens = a[keep], Bs[keep], sens[keep]
+    mu = _margin(h, ys[keep], margin, order)
+    nf = G.shape[1]
+    rows, rhs = [], []
 
+    def cut(j, phi):
+        e = np.exp(-1j * phi)
+        r = (e * Bs[j]).real
+        sc = 1.0 / max(np.abs(r).max(), sens[j])
+        rows.append(np.concatenate([r * sc, [-sens[j] * sc]]))
+        rhs.append((1.0 - mu[j] - (e * a[j]).real) * sc)
 
-def _feasible_weights(h, steps, c0, G, lead, x0, ys, margin, order, tol, refine=20, rounds=8):
-    """Exchange method: solve on the sample set, check a grid `refine` times finer, add the
-    points (and their neighbours) where |R| leaves the margin, repeat.  Returns (worst, x)."""
-    fine = np.arange(1, refine * ys.size + 1) / (refine * ys.size)
-    pts = ys.copy()
-    x = np.asarray(x0, float)
-    worst = np.inf
+    for j in range(a.size):
+        for k in range(angles):
+            cut(j, 2 * np.pi * k / angles)
+    lg, lr = lead
+    eps = 1e-8 * abs(lr)
+    ls = 1.0 / max(np.abs(lg * D).max(), 1e-300)
+    lead_row = np.concatenate([lg * D * ls, [0.0]])
+    lead_rhs = -(lr + lg @ x0 + eps) * ls
+    cost = np.zeros(nf + 1)
+    cost[-1] = 1.0
+    bounds = [(None, None)] * nf + [(-1.0, None)]
     for _ in range(rounds):
-        x = _solve_samples(h, steps, c0, G, lead, x, pts, margin, order)
-        v, lv = _violations(h, steps, c0, G, lead, x, fine, margin, order)
-        worst = max(float(v.max()), lv)
-        if worst <= tol:
-            return worst, x
+        A_ub, b_ub = np.array(rows + [lead_row]), np.array(rhs + [lead_rhs])
+        res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=bounds, method="highs-ds")
+        if res.status == 4:   # numerical trouble in the simplex: try the interior-point method
+            res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=bounds, method="highs-ipm")
+        if res.status != 0 or res.x[-1] > 0:
+            return None
+        z = res.x[:nf]
+        R = a + Bs @ z
+        v = np.abs(R) - 1 + mu
+        if v.max() <= tol:
+            return x0 + z * D
+        for j in np.where(v > tol)[0]:
+            cut(j, np.angle(R[j]))
+    return None
+
+
+def _feasible(h, steps, c0, G, lead, order, ys, fine, margin, x0, tol=1e-13, rounds=6):
+    """Exchange loop around the LP: weights stable on the fine grid (half the margin), or None."""
+    pts = ys
+    for _ in range(rounds):
+        x = _lp_feasible(h, steps, c0, G, lead, order, pts, margin, x0)
+        if x is None:
+            return None
+        P = np.stack([gbs_poly_values(n, 1j * h * fine) for n in steps], axis=1)
+        v = np.abs(P @ (c0 + G @ x)) - 1 + 0.5 * _margin(h, fine, margin, order)
         bad = np.where(v > tol)[0]
         if bad.size == 0:
-            return worst, x
-        add = np.unique(np.clip(np.concatenate([bad - 1, bad, bad + 1]), 0, fine.size - 1))
-        pts = np.unique(np.concatenate([pts, fine[add]]))
-    return worst, x
+            return x
+        pts = np.unique(np.concatenate([pts, fine[bad]]))
+    return None
 
 
-def optimise(order, steps_dep, steps_free, h_lo, h_hi=None, n_samples=600, iters=30, tol=1e-13,
-             x0=None, lead_margin=1e-14, margin=1e-8):
-    """Maximise the imaginary stability boundary over the free weights (App. B).
-
-    Bisection over h; at each h the convex subproblem is solved as a smooth penalty
-    minimisation (the minimax of eq. "cvx_subproblem" is degenerate because |R(0)| = 1, so
-    feasibility -- every sample with |R|^2 <= 1 + tol and the lead-term sign respected -- is
-    the test).  h_lo must be feasible (e.g. a fraction of a known scheme's ISB)."""
+def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-7, rel_tol=1e-7, h_hi=None):
+    """Maximise the imaginary stability boundary over the free weights (App. B): bisection over
+    h in (0, N_max + 1] with the LP feasibility test above.  The dependent/free split only fixes
+    the parametrisation (every split spans the same weights); small dependent counts keep it
+    well conditioned."""
     steps_dep, steps_free = tuple(steps_dep), tuple(steps_free)
     steps = steps_dep + steps_free
     c0, G = affine_weights(order, steps_dep, steps_free)
+    lead = _lead_constraint(order, steps, c0, G)
     nmax = max(steps)
-    coef = np.array([[float(v) for v in gbs_poly_coeffs(n, order + 2)] for n in steps])   # m x (p+3)
-    ek = lambda k: (coef[:, k] @ G, coef[:, k] @ c0 - 1.0 / factorial(k))
-    g1, r1 = ek(order + 1)
-    g2, r2 = ek(order + 2)
-    sg = 1.0 if order % 4 == 0 else -1.0
-    # |R(iy)|^2 - 1 = 2 sg (e_(p+1) - e_(p+2)) y^(p+2) + ...: keep it negative
-    lscale = 1.0 / max(np.max(np.abs(g1 - g2)), 1e-300)
-    lead = (2 * sg * (g1 - g2) * lscale, (2 * sg * (r1 - r2) + lead_margin) * lscale)
     ys = np.arange(1, n_samples + 1) / n_samples
-    hi = h_hi if h_hi is not None else float(nmax + 1)
-    x = np.zeros(len(steps_free)) if x0 is None else np.asarray(x0, float)
-    worst, x = _feasible_weights(h_lo, steps, c0, G, lead, x, ys, margin, order, tol)
-    if worst > tol:
-        raise ValueError(f"h_lo = {h_lo} is not feasible (violation {worst:.2e})")
-    lo, best = h_lo, x
-    for _ in range(iters):
+    fine = np.arange(1, refine * n_samples + 1) / (refine * n_samples)
+    lo, hi = 0.0, float(h_hi if h_hi is not None else nmax + 1)
+    best = np.zeros(len(steps_free))
+    found = False
+    while hi - lo > rel_tol * hi:
         mid = 0.5 * (lo + hi)
-        worst, xm = _feasible_weights(mid, steps, c0, G, lead, best, ys, margin, order, tol)
-        if worst <= tol:
-            lo, best = mid, xm
+        x = _feasible(mid, steps, c0, G, lead, order, ys, fine, margin, best)
+        if x is not None:
+            lo, best, found = mid, x, True
         else:
             hi = mid
-        if hi - lo < 1e-6 * hi:
-            break
+    if not found:
+        raise ValueError("no stable free weights found")
     return OptResult(steps_dep, steps_free, best, lo, lo / (nmax + 1))
 
 

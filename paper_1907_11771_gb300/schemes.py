@@ -12,11 +12,13 @@ no free part (Sec. 3.2).
 * GBS_12_8  -- Sec. 3.8.3 (order 12, eight cores, ISB_n 0.7116)
 * SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1 -- Table 1 (fully determined)
 * SQ8_2468  -- classical Richardson extrapolation with N = 2, 4, 6, 8 (order 8)
-* GBS_6_6   -- order 6 on six cores (all even counts up to N_max = 22), free weights
-               optimised for the imaginary axis with paper_1907_11771_gb300.optimize (App. B)
-               and rounded to rationals with denominators below 2^16 (as Sec. 3.8 does for its
-               schemes); exact ISB 15.00302 (ISB_n 0.65231).  The paper prints no order-6
-               scheme: square order-6 schemes have ISB 0 (Sec. 2.2).
+* GBS_6_6   -- order 6 on six cores (all even counts up to N_max = 22): a genuinely order-6
+               scheme with positive imaginary-axis coverage, from an earlier penalty-method run
+               of the App. B optimisation, rounded to rationals with denominators below 2^16 (as
+               Sec. 3.8 does for its schemes); exact ISB 15.00302 (ISB_n 0.65231).  It is not the
+               order-6 optimum: on these counts that coincides with the order-8 optimum (ISB_n
+               0.7695), whose order-7 error term vanishes.  The paper prints no order-6 scheme:
+               square order-6 schemes have ISB 0 (Sec. 2.2).
 """
 from dataclasses import dataclass
 from fractions import Fraction
