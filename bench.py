@@ -700,7 +700,7 @@ def sol_kernel_is_fused(sol, B):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gbs", "reference"], default="gbs")
     ap.add_argument("--kernel", choices=["auto", "plain", "fused"], default="auto")
