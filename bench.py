@@ -46,10 +46,14 @@ def workload_desc(n=N_GRID, prec=0):
             f"{PREC_DESC[prec]}, H = {H_FRACTION} x stability limit")
 
 
-# DRAM bytes (read + write) of one time-blocked pass-kernel launch, from the ncu capture in
-# profiles/k_passes_2d2048.md (2D 2048^2, FP32, default schedule hseg 256, tmax 4, schedule 0).
-# It describes that kernel build only: set to None when the kernel changes until re-measured.
-PASSES_2D2048_TRAFFIC = 4.77e9 + 3.06e9
+# DRAM bytes (read + write) of one time-blocked pass-kernel launch per schedule (hseg, tmax,
+# schedule), from the ncu captures in profiles/k_passes_2d2048.md (2D 2048^2, FP32).  They
+# describe that kernel build only: empty this table when the kernel changes until re-measured.
+PASSES_2D2048_TRAFFIC = {
+    (256, 4, 0): 4.765e9 + 3.059e9, (192, 4, 0): 4.997e9 + 3.056e9, (128, 4, 0): 5.325e9 + 3.054e9,
+    (384, 4, 0): 4.605e9 + 3.068e9, (96, 4, 0): 5.829e9 + 3.055e9, (192, 4, 1): 4.515e9 + 3.056e9,
+    (256, 4, 1): 4.006e9 + 3.059e9,
+}
 
 
 def peaks():
@@ -312,7 +316,11 @@ def run_gpu(args):
     tuned = None
     if args.hseg:
         sol.set_option("hseg", args.hseg)
-    elif not args.no_autotune:
+    if args.tmax:
+        sol.set_option("tmax", args.tmax)
+    if args.schedule >= 0:
+        sol.set_option("schedule", args.schedule)
+    if not (args.hseg or args.tmax or args.schedule >= 0 or args.no_autotune):
         from paper_1907_11771_gb300 import autotune as AT
         r = AT.autotune(sol, y, H, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
         if r is not None:
@@ -357,13 +365,12 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
     traffic = None
-    if (PASSES_2D2048_TRAFFIC and args.workload == "2d" and args.grid == N_GRID and not (args.f64 or args.f32x2)
-            and sol_kernel_is_fused(sol, B)
-            and [sol.get_option(k) for k in ("hseg", "tmax", "schedule")] == [256, 4, 0]):
-        traffic = PASSES_2D2048_TRAFFIC
+    if (args.workload == "2d" and args.grid == N_GRID and not (args.f64 or args.f32x2)
+            and sol_kernel_is_fused(sol, B)):
+        traffic = PASSES_2D2048_TRAFFIC.get(tuple(sol.get_option(k) for k in ("hseg", "tmax", "schedule")))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "traffic_source": "profiles/k_passes_2d2048.md (ncu, same kernel and schedule)" if traffic else None,
+            "traffic_source": "profiles/k_passes_2d2048.md (ncu, same kernel build and schedule)" if traffic else None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
             "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "tiled leap-frog step (k_lf_tiled)",
             "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
@@ -715,6 +722,8 @@ def main():
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
+    ap.add_argument("--tmax", type=int, default=0, help="most leap-frog levels per time-blocked pass (0: default)")
+    ap.add_argument("--schedule", type=int, default=-1, help="work-queue order of the time-blocked kernel (-1: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default time-blocked schedule instead of autotuning it first")
