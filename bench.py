@@ -320,6 +320,8 @@ def run_gpu(args):
         sol.set_option("tmax", args.tmax)
     if args.schedule >= 0:
         sol.set_option("schedule", args.schedule)
+    if args.tma != -1:
+        sol.set_option("tma", args.tma)
     if not (args.hseg or args.tmax or args.schedule >= 0 or args.no_autotune):
         from paper_1907_11771_gb300 import autotune as AT
         r = AT.autotune(sol, y, H, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
@@ -725,6 +727,8 @@ def main():
     ap.add_argument("--tmax", type=int, default=0, help="most leap-frog levels per time-blocked pass (0: default)")
     ap.add_argument("--schedule", type=int, default=-1, help="work-queue order of the time-blocked kernel (-1: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tma", type=int, default=-1, choices=[-1, 0, 1],
+                    help="tensor-copy staging of the plain step kernel: -1 default (3D), 1 always, 0 never")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default time-blocked schedule instead of autotuning it first")
     ap.add_argument("--time-to-solution", action="store_true",

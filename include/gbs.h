@@ -217,7 +217,13 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * GBS_ERR_TIMEOUT (default 2^20, about half a second), and
  * "inject_unsatisfiable_wait" = 0/1, a failure-detection test hook that makes
  * the kernel's first work item wait on a flag nothing sets (the wait runs out,
- * gbs_sync reports GBS_ERR_TIMEOUT, the handle stays usable).  gbs_get_option also
+ * gbs_sync reports GBS_ERR_TIMEOUT, the handle stays usable), and "tma" = -1/0/1
+ * (default -1): the FP32 one-step-per-launch kernel can stage the tiles of a single
+ * 2D/3D acoustic problem whose nx is a multiple of 4 with tensor-memory-access
+ * copies where a tile's box lies inside the grid (identical results to the load
+ * staging; a copy that does not complete latches GBS_ERR_TIMEOUT); 1 uses them
+ * wherever they apply, -1 only in 3D (where they measured faster), 0 never;
+ * gbs_get_option answers 1 only where those copies are in use.  gbs_get_option also
  * answers "kernel_in_use" (the GBS_KERNEL_* value gbs_step would run now).
  * Unknown names: GBS_ERR_INVALID. */
 gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value);

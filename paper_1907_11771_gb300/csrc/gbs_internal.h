@@ -85,7 +85,19 @@ struct StepPlan {
   const int64_t* active_pts;   // [k * (GBS_MAX_STEPS + 1) + n]: points updated by step (k, n)
   double unit_bytes;           // algorithmic bytes per grid-point update of the dominant kernel
   double adj_unit_bytes;       // the same for the adjoint's reverse step (k_adj_rev)
+  // tensor-map (TMA) staging of the FP32 tiled leap-frog step: host pointers to the 128-byte
+  // maps of the level buffers L0 and L1 (NULL: stage with loads), and the device error flag a
+  // bounded wait on the copy latches GBS_ERR_TIMEOUT in
+  const void* lf_tmap[2];
+  int* err;
 };
+
+// Tensor map of one FP32 level buffer [F][nz][ny][nx] for the tiled leap-frog step's staging
+// box (the tile's 40 staged columns x 32 + 2R rows x one z-plane x the fields p, u, v); writes
+// the 128-byte map to `map`.  Requires nx % 4 == 0 and a 16-byte aligned base.  Returns 0, or
+// -1 when the driver entry point or the encoding is unavailable (the kernel then stages with
+// loads).
+int lf_tma_encode(void* map, void* base, int nx, int ny, int nz, int F, int R);
 
 // Record the start of a timed launch; returns the slot index or -1.
 inline int timing_begin(const StepPlan& p, cudaStream_t s) {

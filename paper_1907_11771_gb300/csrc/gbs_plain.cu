@@ -12,7 +12,9 @@
 //                    acc (+)= c_k y*_k, the last sequence writing y_out
 // With a batch, every launch covers all problems; a problem whose scheme has
 // no step (k, n) leaves the launch at once.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <type_traits>
 
@@ -267,13 +269,22 @@ constexpr int lf_min_blocks() {
   return sizeof(T) == 4 ? (DIM == 2 ? 6 : 5) : (DIM == 2 ? 3 : 2);
 }
 
-template <typename T, int DIM, int R, bool kVec>
+// TMA staging helpers (inline PTX): shared-window address, mbarrier, 4D tensor copy
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
+}
+constexpr long long kTmaSpin = 1ll << 22;   // try_wait polls before a copy counts as lost
+
+template <typename T, int DIM, int R, bool kVec, bool kTma>
 __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
-    k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n) {
+    k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n,
+               const __grid_constant__ CUtensorMap tmap) {
   constexpr int Hh = kTileY + 2 * R;
   // staged columns: HX on each side of the tile (>= R and a whole number of 16-byte vectors)
   constexpr int HX = 4, WS = kTileX + 2 * HX;
-  __shared__ __align__(16) T sh[3][Hh][WS];
+  // 128-byte aligned: the tensor copy's destination (its box is [3][Hh][WS], x fastest)
+  __shared__ __align__(128) T sh[3][Hh][WS];
+  __shared__ __align__(8) unsigned long long tma_bar;
   // problem of this block (binary search over the tiled-grid offsets)
   int lo = 0, hi = p.batch - 1;
   const int64_t blk = blockIdx.x;
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   // the tile's W = kTileX + 2 R columns move point by point.
   constexpr int VW = 16 / sizeof(T);
   using V = typename Vec16<T>::type;
-  if constexpr (kVec) {
+  auto stage_vectors = [&]() {
     constexpr int GR = WS / VW, NV = Hh * GR, NITV = (NV + 255) / 256;
     const int ltid = threadIdx.y * kTileX + threadIdx.x;
     V vs[3][NITV];
@@ -378,6 +389,53 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
         for (int f = 0; f < 3; ++f) *reinterpret_cast<V*>(&sh[f][r][g * VW]) = vs[f][it];
       }
     }
+  };
+  if constexpr (kTma) {
+    // Tensor-memory-access staging (every nx a multiple of 4, a single FP32 problem): when the
+    // tile's box of WS columns x Hh rows lies inside the grid, thread (0, 0) starts one 4D copy
+    // of p, u, v (coordinates x0 - HX, a multiple of 4 floats, y0 - R, z, field 0) that
+    // completes on an mbarrier, while every thread fetches its first row's point-wise operands;
+    // boxes that cross the periodic edge use the vector loads.  A copy that does not complete
+    // within kTmaSpin polls latches GBS_ERR_TIMEOUT and the block returns.
+    const bool inside = x0 >= HX && x0 + kTileX + HX <= nx && y0 >= R && y0 + kTileY + R <= ny;
+    if (inside) {
+      const unsigned bar = smem_u32(&tma_bar);
+      const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+      if (lead) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncthreads();
+      if (lead) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((unsigned)sizeof(sh))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(&sh[0][0][0])),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 - HX), "r"(y0 - R), "r"(z), "r"(0), "r"(bar)
+            : "memory");
+      }
+      fetch_row(0);
+      unsigned ready = 0;
+      for (long long it = 0; it < kTmaSpin && !ready; ++it)
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(ready)
+            : "r"(bar)
+            : "memory");
+      if (__syncthreads_or(!ready)) {
+        if (lead) atomicCAS(p.err, 0, (int)GBS_ERR_TIMEOUT);
+        return;
+      }
+    } else {
+      stage_vectors();
+    }
+  } else if constexpr (kVec) {
+    stage_vectors();
   } else {
     using TS = TileStage<R>;
     T stg[3][TS::NIT];
@@ -1246,6 +1304,9 @@ __global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid, int6
 // Host-side dispatch
 // ---------------------------------------------------------------------------
 
+// the tensor-map argument of launches that stage with loads (never read)
+const CUtensorMap kNoTensorMap{};
+
 template <typename T, int SYS, int DIM, int R>
 int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStream_t st) {
   const T* y_in = static_cast<const T*>(y_in_v);
@@ -1262,10 +1323,23 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
       if constexpr (SYS == SYS_ACOUSTIC && DIM >= 2 && std::is_same<T, dsf>::value)
         p.nx_vec ? k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n)
                  : k_lf_tiled_x2<(DIM >= 2 ? DIM : 2), R, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
-      else if (SYS == SYS_ACOUSTIC && DIM >= 2 && p.nx_vec)
-        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
-      else if (SYS == SYS_ACOUSTIC && DIM >= 2)
-        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(p, y_in, y_out, k, n);
+      else if (SYS == SYS_ACOUSTIC && DIM >= 2 && p.nx_vec) {
+        // the level staged by step n is L1 for odd n, else L0 (see k_lf_tiled)
+        const void* map = p.lf_tmap[n & 1];
+        bool tma = false;
+        if constexpr (std::is_same<T, float>::value) {
+          if (map) {
+            k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, true, true><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(
+                p, y_in, y_out, k, n, *static_cast<const CUtensorMap*>(map));
+            tma = true;
+          }
+        }
+        if (!tma)
+          k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, true, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(
+              p, y_in, y_out, k, n, kNoTensorMap);
+      } else if (SYS == SYS_ACOUSTIC && DIM >= 2)
+        k_lf_tiled<T, (DIM >= 2 ? DIM : 2), R, false, false><<<(unsigned)p.total_tiles, dim3(kTileX, 8), 0, st>>>(
+            p, y_in, y_out, k, n, kNoTensorMap);
       else
         k_lf<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in, y_out, k, n);
       timing_end(p, u, st, p.tev ? p.unit_bytes * (double)p.active_pts[k * (GBS_MAX_STEPS + 1) + n] : 0.0);
@@ -1434,6 +1508,34 @@ int plain_adjoint_step(const AdjPlan& a, const void* y_in, const void* lam_out, 
   if (a.fw.system != GBS_ACOUSTIC) return -1;
   return a.fw.f64 ? adjoint_sys<double>(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, s)
                   : adjoint_sys<float>(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, s);
+}
+
+
+int lf_tma_encode(void* map, void* base, int nx, int ny, int nz, int F, int R) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
+  }
+  if (!encode || nx % 4 || F < 3 || (reinterpret_cast<uintptr_t>(base) & 15)) return -1;
+  // dimensions x, y, z, field; strides of y, z and field in bytes (multiples of 16: nx % 4 == 0)
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)F};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+  // the staging box of k_lf_tiled: HX = 4 columns on either side of the 32-column tile, R rows
+  // above and below its 32 rows, one z-plane, the fields p, u, v
+  const cuuint32_t box[4] = {(cuuint32_t)(kTileX + 8), (cuuint32_t)(kTileY + 2 * R), 1, 3};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
+                            box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
 }
 
 }  // namespace gbs
