@@ -167,6 +167,24 @@ gbs_status gbs_step_batch(gbs_handle h, const void* y_in, void* y_out, const dou
 gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, double H,
                          int n_macro);
 
+/* End-to-end over a stream of independent inputs (Sec. 2.1 / 3.2 per input):
+ * y_out_host[i] = (macro-step)^n_macro (y_in_host[i]) for i = 0..count-1,
+ * every y_in_host[i] / y_out_host[i] a HOST state buffer in the layout of
+ * gbs_step (pinned memory lets the copies run asynchronously; pageable memory
+ * works but serialises them).  The arrays themselves are host arrays of count
+ * pointers; an output may alias another output (the device-to-host copies run
+ * in order); an output must not alias a later input.  Two library-owned device staging states
+ * alternate: the host-to-device copy of input i+1 and the device-to-host copy
+ * of result i-1 run on two copy streams while the handle's stream steps input
+ * i, so the copies hide behind the macro-steps where they are shorter.  Results
+ * written to aliasing outputs land in input order.  Allocates nothing (the
+ * staging states, the copy streams and their events are created by
+ * gbs_create).  Returns when every result is in host memory; count == 0 is a
+ * no-op.  Errors: GBS_ERR_INVALID for NULL arrays or entries, otherwise as
+ * gbs_step. */
+gbs_status gbs_step_host_stream(gbs_handle h, const void* const* y_in_host, void* const* y_out_host,
+                                int count, double H, int n_macro);
+
 /* Discrete adjoint of ONE macro-step (the exact transpose of the forward
  * steps above; not in the paper).  With y_out = M(kappa) y_in:
  *   lam_in = M^T lam_out + S^T r

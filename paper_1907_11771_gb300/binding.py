@@ -54,6 +54,7 @@ _SIGS = {
     "gbs_step": (_I, [_P, _P, _P, _D, _I]),
     "gbs_step_batch": (_I, [_P, _P, _P, ctypes.POINTER(_D), _I]),
     "gbs_step_host": (_I, [_P, _P, _P, _D, _I]),
+    "gbs_step_host_stream": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _D, _I]),
     "gbs_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _P, _I, _P]),
     "gbs_misfit": (_I, [_P, _P, _P, _I, _P, _P, _P]),
     "gbs_norms": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
@@ -185,6 +186,15 @@ def gbs_step_batch(h, y_in, y_out, H, n_macro):
 
 def gbs_step_host(h, y_in_host, y_out_host, H, n_macro):
     _check(h, lib().gbs_step_host(h, _ptr(y_in_host), _ptr(y_out_host), float(H), int(n_macro)))
+
+
+def gbs_step_host_stream(h, y_in_hosts, y_out_hosts, H, n_macro):
+    n = len(y_in_hosts)
+    if len(y_out_hosts) != n:
+        raise ValueError("as many output buffers as inputs are needed")
+    ins = (_P * max(n, 1))(*[_ptr(t) for t in y_in_hosts])
+    outs = (_P * max(n, 1))(*[_ptr(t) for t in y_out_hosts])
+    _check(h, lib().gbs_step_host_stream(h, ins, outs, n, float(H), int(n_macro)))
 
 
 def gbs_adjoint_step(h, y_in, lam_out, lam_in, grad_kappa, H, rcv_idx=None, rcv_resid=None):

@@ -73,6 +73,10 @@ struct gbs_ctx {
   void* L1 = nullptr;
   double* acc = nullptr;
   void* stage = nullptr;
+  void* stage2 = nullptr;                 // second staging state: gbs_step_host_stream alternates
+  cudaStream_t copy_stream = nullptr;     // gbs_step_host_stream: host-to-device copies
+  cudaStream_t d2h_stream = nullptr;      // and device-to-host copies (separate copy engines)
+  cudaEvent_t ev_in[2] = {}, ev_out[2] = {}, ev_d2h[2] = {};
   void* levels = nullptr;
   void* ds_y0 = nullptr;                  // GBS_F32X2: y_in, kappa, b as FP32 pairs
   void* ds_kappa = nullptr;
@@ -227,11 +231,18 @@ void free_graphs(gbs_ctx* h) {
 void free_all(gbs_ctx* h) {
   free_graphs(h);
   void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
-                  h->acc, h->stage, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa, h->ds_b,
-                  h->gpair};
+                  h->acc, h->stage, h->stage2, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa,
+                  h->ds_b, h->gpair};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+    if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+    if (h->ev_d2h[i]) cudaEventDestroy(h->ev_d2h[i]);
+  }
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
   h->tev.clear();
   fused_destroy(h->fw);
@@ -532,7 +543,7 @@ size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps) {
   const Sizes s = sizes_of(pb);
   const size_t esz = pb->precision == GBS_F32_STATE_F64_COMBINE ? 4 : 8;
   size_t bytes = 0;
-  bytes += 4 * s.state_elems * esz;       // f0, L0, L1, stage
+  bytes += 5 * s.state_elems * esz;       // f0, L0, L1, two staging states
   bytes += 8 * s.state_elems;             // acc
   bytes += s.media_elems * esz;           // b
   if (pb->precision == GBS_F32X2) bytes += 8 * (s.state_elems + 2 * s.media_elems);   // pair copies
@@ -614,6 +625,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   if ((st = dalloc(h, &h->L1, E * h->esz)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->acc, E * sizeof(double))) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->stage, E * h->esz)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->stage2, E * h->esz)) != GBS_OK) return bail(st);
   if (h->system == GBS_ACOUSTIC && (st = dalloc(h, &h->b, P * h->esz)) != GBS_OK) return bail(st);
   if (h->ds) {   // FP32 pairs take 8 bytes, like the FP64 values they are made from
     if ((st = dalloc(h, &h->ds_y0, E * 8)) != GBS_OK) return bail(st);
@@ -627,10 +639,19 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
     if ((st = dalloc(h, &h->mu_shared, E * h->esz)) != GBS_OK) return bail(st);
     if (!h->f64 && (st = dalloc(h, &h->gpair, P * sizeof(float2))) != GBS_OK) return bail(st);
   }
-  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking) != cudaSuccess) {
     fail(h, GBS_ERR_CUDA, "cudaStreamCreate failed");
     return bail(GBS_ERR_CUDA);
   }
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_d2h[i], cudaEventDisableTiming) != cudaSuccess) {
+      fail(h, GBS_ERR_CUDA, "cudaEventCreate failed");
+      return bail(GBS_ERR_CUDA);
+    }
   if (cudaMemset(h->d_err, 0, 64) != cudaSuccess || cudaMemset(h->d_slots, 0, sizeof(SlotDev) * GBS_MAX_SLOTS) != cudaSuccess ||
       cudaMemcpy(h->d_probs, h->probs.data(), sizeof(ProbDev) * h->batch, cudaMemcpyHostToDevice) != cudaSuccess) {
     fail(h, GBS_ERR_CUDA, "workspace initialisation failed");
@@ -853,6 +874,53 @@ gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, 
   gbs_status st = gbs_step(h, h->stage, h->stage, H, n_macro);
   if (st != GBS_OK) return st;
   CK(h, cudaMemcpyAsync(y_out_host, h->stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return GBS_OK;
+}
+
+gbs_status gbs_step_host_stream(gbs_handle h, const void* const* y_in_host, void* const* y_out_host, int count,
+                                double H, int n_macro) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (count < 0 || (count > 0 && (!y_in_host || !y_out_host)))
+    return fail(h, GBS_ERR_INVALID, "bad host buffer arrays");
+  for (int i = 0; i < count; ++i)
+    if (!y_in_host[i] || !y_out_host[i]) return fail(h, GBS_ERR_INVALID, "host buffer %d is NULL", i);
+  const size_t bytes = (size_t)h->state_elems * h->esz;
+  void* buf[2] = {h->stage, h->stage2};
+  cudaStream_t hs = h->copy_stream, ds = h->d2h_stream;
+  // input i goes to buf[i % 2].  Host-to-device copies run on hs, device-to-host copies on ds
+  // (separate copy engines), the macro-steps on the handle's stream: step i waits for H2D(i),
+  // D2H(i) waits for step i, and H2D(i + 1) into the other buffer waits for D2H(i - 1), the
+  // buffer's previous reader (which itself waited for step i - 1).  So H2D(i + 1) and D2H(i - 1)
+  // overlap step i.  Both copy streams first wait for the handle's stream's earlier work.
+  CK(h, cudaEventRecord(h->ev_out[0], h->stream));
+  CK(h, cudaStreamWaitEvent(hs, h->ev_out[0], 0));
+  CK(h, cudaStreamWaitEvent(ds, h->ev_out[0], 0));
+  if (count > 0) {
+    CK(h, cudaMemcpyAsync(buf[0], y_in_host[0], bytes, cudaMemcpyHostToDevice, hs));
+    CK(h, cudaEventRecord(h->ev_in[0], hs));
+  }
+  for (int i = 0; i < count; ++i) {
+    const int b = i & 1;
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_in[b], 0));
+    gbs_status st = gbs_step(h, buf[b], buf[b], H, n_macro);
+    if (st != GBS_OK) {
+      cudaStreamSynchronize(hs);
+      cudaStreamSynchronize(ds);
+      return st;
+    }
+    CK(h, cudaEventRecord(h->ev_out[b], h->stream));
+    if (i + 1 < count) {
+      if (i >= 1) CK(h, cudaStreamWaitEvent(hs, h->ev_d2h[b ^ 1], 0));
+      CK(h, cudaMemcpyAsync(buf[b ^ 1], y_in_host[i + 1], bytes, cudaMemcpyHostToDevice, hs));
+      CK(h, cudaEventRecord(h->ev_in[b ^ 1], hs));
+    }
+    CK(h, cudaStreamWaitEvent(ds, h->ev_out[b], 0));
+    CK(h, cudaMemcpyAsync(y_out_host[i], buf[b], bytes, cudaMemcpyDeviceToHost, ds));
+    CK(h, cudaEventRecord(h->ev_d2h[b], ds));
+  }
+  CK(h, cudaStreamSynchronize(hs));
+  CK(h, cudaStreamSynchronize(ds));
   CK(h, cudaStreamSynchronize(h->stream));
   return GBS_OK;
 }

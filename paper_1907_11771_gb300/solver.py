@@ -80,6 +80,10 @@ class GBSSolver:
     def step_host(self, y_in_host, y_out_host, H, n_macro=1):
         B.gbs_step_host(self.h, y_in_host, y_out_host, H, n_macro)
 
+    def step_host_stream(self, y_in_hosts, y_out_hosts, H, n_macro=1):
+        """Independent host inputs through the device with copies overlapping the steps."""
+        B.gbs_step_host_stream(self.h, y_in_hosts, y_out_hosts, H, n_macro)
+
     def adjoint_step(self, y_in, lam_out, lam_in, grad_kappa, H, rcv_idx=None, rcv_resid=None):
         B.gbs_adjoint_step(self.h, y_in, lam_out, lam_in, grad_kappa, H, rcv_idx, rcv_resid)
 
