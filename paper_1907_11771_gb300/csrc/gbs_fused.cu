@@ -36,6 +36,7 @@
 #include <cstring>
 #include <vector>
 
+#include "gbs_ds.cuh"
 #include "gbs_internal.h"
 #include "gbs_stencil.cuh"
 
@@ -92,6 +93,10 @@ struct Params {
   const PassDesc* pdesc; // [slot][seq][pass]
   const TileGeo* tgeo;   // per problem
   long long spin_limit;  // polls of a dependency flag before GBS_ERR_TIMEOUT
+  // GBS_F32X2: init, lev and ystar hold (hi, lo) float pairs (8 bytes per element); the media
+  // as pairs
+  const dsf* kap2;
+  const dsf* b2;
 };
 
 __device__ __forceinline__ int wrapi(int a, int n) {
@@ -344,7 +349,207 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same sweep in FP32-pair arithmetic (GBS_F32X2: FP64 states carried as hi + lo float pairs),
+// passes of two levels.  Every value is a pair: (p, v) windows as ds2 (two pairs per packed
+// lane), (p, u) plane entries as float4 (p.hi, u.hi, p.lo, u.lo), the scaled media as float4
+// (kappa'.hi, kappa'.lo, b'.hi, b'.lo); every sum, product and update is a pair operation
+// (gbs_ds.cuh).  With T = 2 the register windows and shared planes take the room the FP32
+// sweep takes at T = 4.
+// ---------------------------------------------------------------------------
+constexpr int kTX2 = 2;
+
+__host__ __device__ constexpr float fd_hi(int R, int j) { return float(R == 2 ? fd_coef<2>(j) : fd_coef<3>(j)); }
+__host__ __device__ constexpr float fd_lo(int R, int j) {
+  return float((R == 2 ? fd_coef<2>(j) : fd_coef<3>(j)) - double(fd_hi(R, j)));
+}
+
+__device__ __forceinline__ ds2 ds2_of(float4 a) { return ds2{make_float2(a.x, a.y), make_float2(a.z, a.w)}; }
+
+// x-sums of (p, u) over a plane row: sum_j c_j (row[+j] - row[-j]) in pairs
 template <int R>
+__device__ __forceinline__ ds2 xsum_x2(const float4* row) {
+  ds2 acc = ds2_mul(ds2_of(row[1]) - ds2_of(row[-1]), fd_hi(R, 1), fd_lo(R, 1));
+#pragma unroll
+  for (int j = 2; j <= R; ++j) acc = acc + ds2_mul(ds2_of(row[j]) - ds2_of(row[-j]), fd_hi(R, j), fd_lo(R, j));
+  return acc;
+}
+
+// y-sums of (p, v) over a register window indexed by row mod U
+template <int R>
+__device__ __forceinline__ ds2 ysum_x2(const ds2 (&w)[2 * R + 1], int r) {
+  constexpr int U = 2 * R + 1;
+  ds2 acc = ds2_mul(w[(r + 1) % U] - w[(r + U - 1) % U], fd_hi(R, 1), fd_lo(R, 1));
+#pragma unroll
+  for (int j = 2; j <= R; ++j) acc = acc + ds2_mul(w[(r + j) % U] - w[(r + U - j) % U], fd_hi(R, j), fd_lo(R, j));
+  return acc;
+}
+
+__device__ __forceinline__ dsf ds_of(float2 a) { return dsf(a.x, a.y); }
+__device__ __forceinline__ float2 f2_of(dsf a) { return make_float2(a.hi, a.lo); }
+
+template <int R>
+__device__ __forceinline__ void run_item_x2(const Params& P, const Item& it, const PassDesc& pd, float4* smem) {
+  constexpr int T = kTX2;
+  constexpr int U = 2 * R + 1;
+  constexpr int OFF = 64 * U;
+  const int tid = threadIdx.x;
+  const ProbDev q = P.probs[it.prob];
+  const TileGeo tg = P.tgeo[it.prob];
+  const int nx = q.n[0], ny = q.n[1];
+  const int PPn = nx * ny;
+  const int sx = it.tile % tg.nst, sy = it.tile / tg.nst;
+  const int x0 = (sx * nx) / tg.nst;
+  const int wout = ((sx + 1) * nx) / tg.nst - x0;
+  const int Y0 = (sy * ny) / tg.nseg;
+  const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
+  const int x = wrapi(x0 - R * T + tid, nx);
+  const double hd = P.hk[it.prob * GBS_MAX_SEQ + it.seq];
+  const dsf h1 = dsf(hd);
+  const dsf mh = dsf(-2.0 * hd * q.inv_dx[0]);                      // -2h / dx
+  const double rxyd = q.inv_dx[1] / q.inv_dx[0];
+  const bool unit = rxyd == 1.0;
+  const dsf rxy = dsf(rxyd);
+  const dsf* kap = P.kap2 + q.media_off;
+  const dsf* bmd = P.b2 + q.media_off;
+  const float2* init = reinterpret_cast<const float2*>(P.init);
+  float2* lev = reinterpret_cast<float2*>(P.lev);
+  float2* ystar = reinterpret_cast<float2*>(P.ystar);
+  const int64_t E = P.E;
+  const float2* inA = pd.first ? init + q.state_off : lev + ((int64_t)(it.seq * 2 + ((it.pass - 1) & 1)) * 2) * E + q.state_off;
+  float2* outA = pd.last ? ystar + (int64_t)it.seq * E + q.state_off
+                         : lev + ((int64_t)(it.seq * 2 + (it.pass & 1)) * 2) * E + q.state_off;
+  const bool out_col = tid >= R * T && tid < R * T + wout;
+  float4* const lvl = smem + kPad + tid;                // plane t, slot r: lvl[(t U + r) kRow]
+  float4* const med = smem + T * U * kRow + tid;        // slot r: med[r kThreads]
+
+  ds2 w[T][U];
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[t][u] = ds2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+
+  const int S = hs + 2 * R * T;
+  int e0 = wrapf(Y0 - R * T, ny) * nx + x;
+  int e1 = wrapf(Y0 - R * T - R, ny) * nx + x;
+  int eo = (Y0 - 2 * R * T) * nx + x;
+  float2 n0[3], y0v[3], n1[3];
+  dsf nk, nb;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) y0v[f] = make_float2(0.f, 0.f);
+  auto fetch = [&]() {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      n0[f] = __ldcg(inA + E + e0 + f * PPn);
+      if (pd.first) y0v[f] = __ldcg(inA + e0 + f * PPn);
+      n1[f] = __ldcg(inA + e1 + f * PPn);
+    }
+    nk = ldg(kap + e0);
+    nb = ldg(bmd + e0);
+  };
+  // L2 prefetch of the next block of U rows (as in run_item; a pair row segment is 16 lines)
+  const int xf = wrapi(x0 - R * T, nx);
+  auto prefetch_block = [&](int sn) {
+    const int wq = tid >> 5;
+    if (wq > 5) return;
+    const int row0 = wrapi(Y0 - R * T + sn - (wq >= 3 ? R : 0), ny);
+    const float2* base = wq < 3 ? inA + E + wq * PPn : inA + (wq - 3) * PPn;
+    constexpr int kSamp = 17;   // columns 16 pairs (one line) apart, plus the last one
+    for (int i = tid & 31; i < U * kSamp; i += 32) {
+      const int j = i / kSamp, c = i - j * kSamp;
+      int row = row0 + j;
+      if (row >= ny) row -= ny;
+      const int col = (xf + (c + 1 < kSamp ? c * 16 : kThreads - 1)) % nx;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (size_t)row * nx + col));
+    }
+  };
+  fetch();
+  for (int sb = 0; sb < S; sb += U) {
+    prefetch_block(sb + U);
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) {
+      const int s = sb + uu;
+      if (s >= S) break;
+      // ---- level 0, level -1, media ----
+      const int r0 = (uu + OFF - R * T) % U;
+      dsf p0 = ds_of(n0[0]), u0 = ds_of(n0[1]), v0 = ds_of(n0[2]);
+      if (pd.first) {
+        p0 = ds_of(y0v[0]) + h1 * p0;
+        u0 = ds_of(y0v[1]) + h1 * u0;
+        v0 = ds_of(y0v[2]) + h1 * v0;
+      }
+      w[0][r0] = make_ds2(p0, v0);
+      lvl[r0 * kRow] = make_float4(p0.hi, u0.hi, p0.lo, u0.lo);
+      {
+        const dsf km = nk * mh, bk = nb * mh;
+        med[r0 * kThreads] = make_float4(km.hi, km.lo, bk.hi, bk.lo);
+      }
+      const ds2 am_pv = make_ds2(ds_of(n1[0]), ds_of(n1[2]));
+      const dsf am_u = ds_of(n1[1]);
+      e0 += nx;
+      if (e0 >= PPn) e0 -= PPn;
+      e1 += nx;
+      if (e1 >= PPn) e1 -= PPn;
+      fetch();
+      const bool stT = out_col && (unsigned)(s - 2 * R * T) < (unsigned)hs;
+      const bool stT1 = out_col && (unsigned)(s - 2 * R * T + R) < (unsigned)hs;
+      // ---- levels 1..T ----
+#pragma unroll
+      for (int t = 1; t <= T; ++t) {
+        const int r = (uu + OFF - R * T - R * t) % U;
+        const float4 mf = med[r * kThreads];
+        const dsf km(mf.x, mf.y), bk(mf.z, mf.w);
+        const ds2 sxv = xsum_x2<R>(lvl + ((t - 1) * U + r) * kRow);   // (sum_x p, sum_x u)
+        const ds2 syv = ysum_x2<R>(w[t - 1], r);                       // (sum_y p, sum_y v)
+        ds2 ppv;
+        dsf pu;
+        if (t == 1) {
+          ppv = am_pv;
+          pu = am_u;
+        } else {
+          ppv = w[t - 2][r];
+          const float4 o = lvl[((t - 2) * U + r) * kRow];
+          pu = dsf(o.y, o.w);
+        }
+        // (p, v) += (kappa', b') * (sum_x u + rxy sum_y v, rxy sum_y p);  u += b' sum_x p
+        const dsf syv_v = unit ? lane_y(syv) : rxy * lane_y(syv);
+        const dsf syv_p = unit ? lane_x(syv) : rxy * lane_x(syv);
+        const ds2 npv = ppv + ds2_mul(make_ds2(lane_y(sxv) + syv_v, syv_p), make_ds2(km, bk));
+        const dsf nu = pu + bk * lane_x(sxv);
+        const dsf np = lane_x(npv), nv = lane_y(npv);
+        if (t < T) {
+          w[t][r] = npv;
+          lvl[(t * U + r) * kRow] = make_float4(np.hi, nu.hi, np.lo, nu.lo);
+        }
+        if (!pd.last) {
+          if (t == T - 1 && stT1) {
+            float2* o = outA + (eo + R * nx);
+            __stcs(o, f2_of(np));
+            __stcs(o + PPn, f2_of(nu));
+            __stcs(o + 2 * PPn, f2_of(nv));
+          }
+          if (t == T && stT) {
+            float2* o = outA + E + eo;
+            __stcs(o, f2_of(np));
+            __stcs(o + PPn, f2_of(nu));
+            __stcs(o + 2 * PPn, f2_of(nv));
+          }
+        } else if (t == T && stT) {
+          const ds2 cpv = w[T - 1][r];
+          const float4 co = lvl[((T - 1) * U + r) * kRow];
+          float2* o = outA + eo;
+          __stcs(o, f2_of(gragg_avg(lane_x(ppv), lane_x(cpv), np)));
+          __stcs(o + PPn, f2_of(gragg_avg(pu, dsf(co.y, co.w), nu)));
+          __stcs(o + 2 * PPn, f2_of(gragg_avg(lane_y(ppv), lane_y(cpv), nv)));
+        }
+      }
+      eo += nx;
+      if (uu % R == R - 1 || uu == U - 1) __syncthreads();
+    }
+  }
+}
+
+template <int R, bool X2>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
@@ -371,7 +576,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P)
     const Item it = P.items[i];
     const ProbDev& q = P.probs[it.prob];
     const PassDesc pd = P.pdesc[(q.slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
-    if (pd.T == 2) run_item<R, 2>(P, it, pd, smem);
+    if constexpr (X2) run_item_x2<R>(P, it, pd, reinterpret_cast<float4*>(smem));
+    else if (pd.T == 2) run_item<R, 2>(P, it, pd, smem);
 #if GBS_FUSED_TMAX >= 6
     else if (pd.T == 6) run_item<R, 6>(P, it, pd, smem);
 #endif
@@ -441,9 +647,26 @@ __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch
   }
 }
 
-size_t ring_bytes(int R) {
+size_t ring_bytes(int R, bool x2) {
   const int u = 2 * R + 1;
+  if (x2) return (size_t)(kTX2 * u * kRow + u * kThreads) * sizeof(float4);
   return (size_t)(kTMax * u * kRow + media_planes() * u * kThreads) * sizeof(float2);
+}
+
+// GBS_F32X2: y_out (FP64) = sum_k c_k y*_k, the averages held as FP32 pairs, summed in FP64 in
+// ascending k (the FP64 combine of the pair path)
+__global__ void __launch_bounds__(256) k_combine_x2(const ProbDev* probs, int batch, const SlotDev* slots,
+                                                    const float2* __restrict__ ystar, int64_t E,
+                                                    double* __restrict__ y_out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
+    double acc = 0.0;
+    for (int k = 0; k < s.m; ++k) {
+      const float2 v = __ldcs(ystar + (int64_t)k * E + e);
+      acc = fma(s.c[k], (double)v.x + (double)v.y, acc);
+    }
+    y_out[e] = acc;
+  }
 }
 
 }  // namespace fused
@@ -469,6 +692,7 @@ struct FusedWork {
   fused::PassDesc* pdesc = nullptr;
   fused::TileGeo* tgeo = nullptr;
   size_t lev_cap = 0, ystar_cap = 0, items_cap = 0, init_cap = 0, kb_cap = 0;
+  bool x2 = false;        // GBS_F32X2: levels, averages and inputs as FP32 pairs
   double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
   long long spin_limit = fused::kSpinLimit;
   int inject_wait = 0;    // test hook: item 0 also waits on a flag that nothing sets
@@ -511,8 +735,8 @@ fused::TileGeo tiles_of(int nx, int ny, int hseg, int halo) {
 }  // namespace
 
 bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
-  if (p.system != GBS_ACOUSTIC || p.ndim != 2 || p.f64 || (p.R != 2 && p.R != 3)) return false;
-  const int halo = p.R * fused::kTMax;
+  if (p.system != GBS_ACOUSTIC || p.ndim != 2 || (p.f64 && !p.ds) || (p.R != 2 && p.R != 3)) return false;
+  const int halo = p.R * (p.ds ? fused::kTX2 : fused::kTMax);
   for (int q = 0; q < p.batch; ++q) {
     // rows wrap at most twice around the period; several strips must each be wider than
     // the halo
@@ -556,7 +780,9 @@ static int grow(T** p, size_t* cap, size_t bytes) {
 int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h,
                   const FusedTune& tune, char* msg, size_t msglen) {
   using namespace fused;
-  const int hseg = tune.hseg, tmax = tune.tmax;
+  const int hseg = tune.hseg, tmax = p.ds ? kTX2 : tune.tmax;   // pair passes: two levels
+  w->x2 = p.ds != 0;
+  const size_t esz = w->x2 ? 8 : 4;
   if (tmax < 2 || tmax > kTMax || tmax % 2) {
     std::snprintf(msg, msglen, "tmax must be even and in [2, %d]", kTMax);
     return -1;
@@ -649,9 +875,9 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
       }
   }
   // device buffers
-  const size_t lev_bytes = (size_t)4 * p.max_m * p.state_elems * sizeof(float);
-  const size_t ys_bytes = (size_t)p.max_m * p.state_elems * sizeof(float);
-  const size_t init_bytes = (size_t)2 * p.state_elems * sizeof(float);
+  const size_t lev_bytes = (size_t)4 * p.max_m * p.state_elems * esz;
+  const size_t ys_bytes = (size_t)p.max_m * p.state_elems * esz;
+  const size_t init_bytes = (size_t)2 * p.state_elems * esz;
   const size_t kb_bytes =
       (size_t)(probs_h[p.batch - 1].media_off + probs_h[p.batch - 1].pts) * sizeof(float2);
   if (grow(&w->lev, &w->lev_cap, lev_bytes) || grow(&w->ystar, &w->ystar_cap, ys_bytes) ||
@@ -700,7 +926,7 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
       const double pts = (double)(((sx + 1) * nx) / g.nst - (sx * nx) / g.nst) *
                          (((sy + 1) * ny) / g.nseg - (sy * ny) / g.nseg);
       const PassDesc& d = pdesc[((size_t)probs_h[it.prob].slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
-      by += pts * 4.0 * (2.0 * p.F + 2.0 + (d.last ? 1.0 : 2.0) * p.F);
+      by += pts * (double)esz * (2.0 * p.F + 2.0 + (d.last ? 1.0 : 2.0) * p.F);
     }
     w->alg_bytes = by;
   }
@@ -708,13 +934,17 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = ring_bytes(p.R);
-  if (p.R == 2) {
-    cudaFuncSetAttribute(k_passes<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_passes<2>, kThreads, smem);
+  const size_t smem = ring_bytes(p.R, w->x2);
+  auto occupancy = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  };
+  if (w->x2) {
+    if (p.R == 2) occupancy(k_passes<2, true>);
+    else occupancy(k_passes<3, true>);
   } else {
-    cudaFuncSetAttribute(k_passes<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_passes<3>, kThreads, smem);
+    if (p.R == 2) occupancy(k_passes<2, false>);
+    else occupancy(k_passes<3, false>);
   }
   if (cudaGetLastError() != cudaSuccess || per_sm < 1) {
     std::snprintf(msg, msglen, "the fused kernel cannot be resident (smem %zu bytes)", smem);
@@ -727,13 +957,20 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
 int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err) {
   using namespace fused;
   int launches = 0;
-  // f0 goes next to a copy of y_0, and the media are interleaved for the passes
-  StepPlan pf = p;
-  pf.f0 = w->init + w->E;
-  pf.f0_ycopy = w->init;
-  pf.f0_kb = w->kb;
-  if (launch_f0(pf, y_in, s) < 0) return -1;
-  ++launches;
+  if (w->x2) {
+    // y_in, kappa and b as FP32 pairs, f0 in pair arithmetic, y_0 and f0 E pairs apart
+    const int l = ds_prologue(p, y_in, w->init, reinterpret_cast<float2*>(w->init) + w->E, s);
+    if (l < 0) return -1;
+    launches += l;
+  } else {
+    // f0 goes next to a copy of y_0, and the media are interleaved for the passes
+    StepPlan pf = p;
+    pf.f0 = w->init + w->E;
+    pf.f0_ycopy = w->init;
+    pf.f0_kb = w->kb;
+    if (launch_f0(pf, y_in, s) < 0) return -1;
+    ++launches;
+  }
   if (cudaMemsetAsync(w->done, 0, sizeof(int) * (w->n_items + 2), s) != cudaSuccess) return -1;
   Params P;
   P.items = w->items;
@@ -754,13 +991,24 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.pdesc = w->pdesc;
   P.tgeo = w->tgeo;
   P.spin_limit = w->spin_limit;
-  const size_t smem = ring_bytes(w->R);
+  P.kap2 = static_cast<const dsf*>(p.ds_kappa);
+  P.b2 = static_cast<const dsf*>(p.ds_b);
+  const size_t smem = ring_bytes(w->R, w->x2);
   const int u = timing_begin(p, s);
-  if (w->R == 2) k_passes<2><<<w->grid, kThreads, smem, s>>>(P);
-  else k_passes<3><<<w->grid, kThreads, smem, s>>>(P);
+  if (w->x2) {
+    if (w->R == 2) k_passes<2, true><<<w->grid, kThreads, smem, s>>>(P);
+    else k_passes<3, true><<<w->grid, kThreads, smem, s>>>(P);
+  } else {
+    if (w->R == 2) k_passes<2, false><<<w->grid, kThreads, smem, s>>>(P);
+    else k_passes<3, false><<<w->grid, kThreads, smem, s>>>(P);
+  }
   timing_end(p, u, s, w->alg_bytes);
   ++launches;
-  k_combine<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<float*>(y_out));
+  if (w->x2)
+    k_combine_x2<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, reinterpret_cast<const float2*>(w->ystar), w->E,
+                                      static_cast<double*>(y_out));
+  else
+    k_combine<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<float*>(y_out));
   ++launches;
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return launches;

@@ -143,7 +143,13 @@ int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStrea
 // f0 = f(y_in) for every problem (point-parallel); returns 1 or -1.
 int launch_f0(const StepPlan& p, const void* y_in, cudaStream_t s);
 
-// Time-blocked FP32 path for 2D acoustics (gbs_fused.cu).  FusedWork holds its
+// GBS_F32X2 inputs of the time-blocked path: y_in (FP64) as FP32 pairs at y_pairs, kappa and b as
+// pairs at p.ds_kappa / p.ds_b, and f0 = f(y_in) in pair arithmetic at f0_pairs (acoustics).
+// Returns the number of kernels launched, or -1.
+int ds_prologue(const StepPlan& p, const void* y_in, void* y_pairs, void* f0_pairs, cudaStream_t s);
+
+// Time-blocked path for 2D acoustics (gbs_fused.cu): FP32 states, or FP64 states in FP32 pairs
+// (GBS_F32X2).  FusedWork holds its
 // schedule and level store; fused_prepare (set-up time) allocates them.
 struct FusedWork;
 FusedWork* fused_create();

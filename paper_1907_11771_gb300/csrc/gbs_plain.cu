@@ -1469,6 +1469,20 @@ __global__ void k_to_ds(const double* __restrict__ a, dsf* __restrict__ o, int64
     o[i] = dsf(a[i]);
 }
 
+int ds_prologue(const StepPlan& p, const void* y_in, void* y_pairs, void* f0_pairs, cudaStream_t s) {
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(y_in), static_cast<dsf*>(y_pairs), p.state_elems);
+  const int64_t m = p.probs_media_elems;
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.kappa), static_cast<dsf*>(p.ds_kappa), m);
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.b), static_cast<dsf*>(p.ds_b), m);
+  StepPlan q = p;
+  q.kappa = p.ds_kappa;
+  q.b = p.ds_b;
+  q.f0 = f0_pairs;
+  q.f0_ycopy = nullptr;
+  q.f0_kb = nullptr;
+  return f0_sys<dsf>(q, y_pairs, s) < 0 ? -1 : 4;
+}
+
 int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s) {
   if (p.system == GBS_ONEWAY_SPECTRAL) return spectral_macro_step(p, y_in, y_out, s);
   if (p.ds) {

@@ -136,10 +136,34 @@ def test_adjoint_of_a_pair_handle_is_the_fp64_adjoint():
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
-def test_time_blocked_kernel_is_refused():
-    case = AcousticCase((64, 64), 6, X2)
+def test_time_blocked_kernel_refused_for_fp64_states_and_3d():
+    for shape, prec in (((64, 64), F64), ((8, 40, 40), X2)):
+        case = AcousticCase(shape, 6, prec)
+        sol = case.solver()
+        sol.set_scheme(S.GBS_8_6)
+        with pytest.raises(B.GbsError):
+            sol.set_option("kernel", B.GBS_KERNEL_FUSED)
+        sol.close()
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("scheme", [S.GBS_8_6, S.SQ8_2468])
+@pytest.mark.parametrize("shape,hseg", [((60, 520), 32), ((45, 251), 256)])
+def test_time_blocked_pairs_parity(order, scheme, shape, hseg):
+    """The time-blocked kernel in FP32-pair arithmetic (passes of two levels) against the FP64
+    oracle at the pair tolerance: several strips and row segments, ragged edges, odd nx."""
+    case = AcousticCase(shape, order, X2, seed=7)
     sol = case.solver()
-    sol.set_scheme(S.GBS_8_6)
-    with pytest.raises(B.GbsError):
-        sol.set_option("kernel", B.GBS_KERNEL_FUSED)
+    sol.set_scheme(scheme)
+    sol.set_option("kernel", B.GBS_KERNEL_FUSED)
+    sol.set_option("hseg", hseg)
+    assert sol.uses_fused()
+    H = 0.8 * sol.stability_limit()[0]
+    steps, c = oracle_scheme(scheme)
+    fused = case.gpu_run(sol, H, 3)
+    err = rel_l2(fused, case.oracle_run(steps, c, H, 3))
+    assert err <= TOL, err
+    sol.set_option("kernel", B.GBS_KERNEL_PLAIN)
+    plain = case.gpu_run(sol, H, 3)
+    assert rel_l2(fused, plain) <= TOL
     sol.close()
