@@ -624,8 +624,8 @@ def run_oneway(args):
 
 def run_time_to_solution(args):
     """Time to a relative L2 error of 1e-6 at t = M0 H0 (2D acoustics, same recipe on an
-    n x n grid): the fused FP32-state path, the plain FP64 path and the plain FP32-pair path,
-    each swept over
+    n x n grid): the fused FP32-state path, the plain FP64 path, and FP64 states in FP32-pair
+    arithmetic on the plain and the fused (time-blocked) kernels, each swept over
     H = H0 / 2^j (H0 = 0.8 x the GBS_8,6 stability limit), against an FP64 GBS_12,8
     reference run at a quarter of its own 0.8 x limit and checked against one at an eighth."""
     import numpy as np
@@ -676,7 +676,8 @@ def run_time_to_solution(args):
     rows = {}
     paths = [("fused FP32 state + FP64-class combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
              ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64),
-             ("plain FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_PLAIN, torch.float64)]
+             ("plain FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_PLAIN, torch.float64),
+             ("fused FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_FUSED, torch.float64)]
     tuned = {}
     for name, prec, kernel, dt in paths:
         sol = solver(prec, S.GBS_8_6, kernel)

@@ -435,7 +435,6 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
 gbs_status prepare_fused(gbs_ctx* h) {
   h->fw_ready = false;
   if (h->opt_kernel == GBS_KERNEL_PLAIN) return GBS_OK;
-  if (h->ds && h->opt_kernel != GBS_KERNEL_FUSED) return GBS_OK;   // pairs: time-blocked on request
   StepPlan p;
   if (build_plan(h, &p) != GBS_OK) {  // some slot without weights yet: nothing to prepare
     h->err.clear();

@@ -142,7 +142,7 @@ def gpu_run(shape_zyx, order, prec, kernel, scheme, n_macro, seed):
 
 
 @pytest.mark.parametrize("order", [4, 6])
-@pytest.mark.parametrize("prec,kernel", [(F64, B.GBS_KERNEL_PLAIN), (X2, B.GBS_KERNEL_PLAIN),
+@pytest.mark.parametrize("prec,kernel", [(F64, B.GBS_KERNEL_PLAIN), (X2, B.GBS_KERNEL_PLAIN), (X2, B.GBS_KERNEL_FUSED),
                                          (F32, B.GBS_KERNEL_PLAIN), (F32, B.GBS_KERNEL_FUSED)])
 def test_acoustic2d_modes_follow_matrix_R(order, prec, kernel):
     shape = (40, 72)                      # ragged against the 32 x 32 tiles in both directions

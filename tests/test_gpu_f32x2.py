@@ -38,6 +38,8 @@ def test_acoustic2d_parity(order, scheme, shape):
     case = AcousticCase(shape, order, X2, seed=3)
     sol = case.solver()
     sol.set_scheme(scheme)
+    assert sol.uses_fused()                      # the default for 2D pairs: the time-blocked kernel
+    sol.set_option("kernel", B.GBS_KERNEL_PLAIN)
     assert not sol.uses_fused()
     H = 0.8 * sol.stability_limit()[0]
     steps, c = oracle_scheme(scheme)
