@@ -132,4 +132,53 @@ __device__ __forceinline__ dsf lane_x(const ds2& a) { return dsf(a.hi.x, a.lo.x)
 __device__ __forceinline__ dsf lane_y(const ds2& a) { return dsf(a.hi.y, a.lo.y); }
 __device__ __forceinline__ ds2 make_ds2(dsf x, dsf y) { return ds2{make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
 
+// Centred finite-difference sums of two pair lanes with the weights as integers over a common
+// divisor: sum_j m_j (a[+j] - a[-j]) = div x the stencil sum (4th order: m = 8, -1, div 12; 6th
+// order: 45, -9, 1, div 60); the caller folds 1/div into a scaling it applies anyway.  hi(j) and
+// lo(j) give the two lanes' hi and lo parts at offset j.  The hi parts' differences are taken
+// exactly (TwoDiff), the integer products exactly (FMA error term; 8 and 1 need none), the main
+// terms are summed exactly (TwoSum), and every small term -- the differences' errors, the lo
+// parts' differences, the products' errors, the sums' errors -- goes into one FP32 accumulator,
+// whose own rounding is 2^-24 of terms already 2^-24 below the result: the pair carries about 48
+// bits as the general pair operations do, for about two thirds of their instructions.
+template <int R>
+__host__ __device__ constexpr float fd_int(int j) {
+  return R == 2 ? (j == 1 ? 8.f : -1.f) : (j == 1 ? 45.f : j == 2 ? -9.f : 1.f);
+}
+template <int R>
+__host__ __device__ constexpr double fd_div() { return R == 2 ? 12.0 : 60.0; }
+
+template <int R, class Hi, class Lo>
+__device__ __forceinline__ ds2 isum_x2(Hi hi, Lo lo) {
+  float2 S = make_float2(0.f, 0.f), small = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const float2 a = hi(j), b = hi(-j);
+    const float2 d = f2_sub(a, b);                                   // TwoDiff: d + e = a - b
+    const float2 bb = f2_sub(d, a);
+    const float2 e = f2_sub(f2_sub(a, f2_sub(d, bb)), f2_add(b, bb));
+    const float2 l = f2_sub(lo(j), lo(-j));
+    const float m = fd_int<R>(j);   // folds: the loop is unrolled
+    const float2 mm = make_float2(m, m);
+    float2 pm;
+    if (m == 1.f || m == -1.f || m == 8.f) {                         // exact products
+      pm = m == 1.f ? d : __fmul2_rn(mm, d);
+    } else {
+      pm = __fmul2_rn(mm, d);
+      small = f2_add(small, __ffma2_rn(mm, d, make_float2(-pm.x, -pm.y)));   // product error
+    }
+    small = __ffma2_rn(mm, f2_add(e, l), small);
+    if (j == 1) {
+      S = pm;
+    } else {                                                          // TwoSum S + pm
+      const float2 t = f2_add(S, pm);
+      const float2 tb = f2_sub(t, S);
+      small = f2_add(small, f2_add(f2_sub(S, f2_sub(t, tb)), f2_sub(pm, tb)));
+      S = t;
+    }
+  }
+  const float2 h = f2_add(S, small);                                 // Fast2Sum
+  return ds2{h, f2_sub(small, f2_sub(h, S))};
+}
+
 }  // namespace gbs

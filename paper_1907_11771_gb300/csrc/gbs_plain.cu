@@ -536,26 +536,9 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
 
 // Tiled leap-frog step for 2D/3D acoustics in FP32 pairs (GBS_F32X2), two pair values per
 // packed instruction: the x-stencils of (p, u) and the y-stencils of (p, v) run lane by lane
-// on f32x2 (ds2).  The tile holds (p.hi, u.hi, p.lo, u.lo) and (p.hi, v.hi, p.lo, v.lo) per
-// point so that each stencil operand is one 16-byte shared load.  Same steps, averaging and
-// FP64 combine as k_lf_tiled.
-template <int R>
-__device__ __forceinline__ ds2 xstencil2(const float4 (*row)[kTileX + 8], int r, int cc, bool along_x) {
-  ds2 s{};
-#pragma unroll
-  for (int j = 1; j <= R; ++j) {
-    const float4 a = along_x ? row[r][cc + j] : row[r + j][cc];
-    const float4 b = along_x ? row[r][cc - j] : row[r - j][cc];
-    const double c = fd_coef<R>(j);
-    const float chi = float(c), clo = float(c - double(float(c)));
-    const ds2 d = ds2_mul(ds2{make_float2(a.x, a.y), make_float2(a.z, a.w)} -
-                              ds2{make_float2(b.x, b.y), make_float2(b.z, b.w)},
-                          chi, clo);
-    s = j == 1 ? d : s + d;
-  }
-  return s;
-}
-
+// on f32x2 (ds2), as integer-weight sums (isum_x2) whose divisor is folded into 2h.  The tile
+// holds (p.hi, u.hi, p.lo, u.lo) and (p.hi, v.hi, p.lo, v.lo) per point so that each stencil
+// operand is one 16-byte shared load.  Same steps, averaging and FP64 combine as k_lf_tiled.
 template <int DIM, int R, bool kVec>
 __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const StepPlan p, const dsf* y_in, double* y_out, int k, int n) {
   // staged columns: HX = 4 on each side of the tile (>= R, whole 16-byte vectors of two pairs)
@@ -585,6 +568,7 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
   const int64_t plane = (int64_t)z * nx * ny;
   dsf h, h2;
   step_sizes(p, lo, k, h, h2);
+  h2 = h2 * dsf(1.0 / fd_div<R>());   // the stencil sums below carry the integer weights' divisor
   dsf* const L0 = static_cast<dsf*>(p.L0) + q.state_off;
   dsf* const L1 = static_cast<dsf*>(p.L1) + q.state_off;
   const dsf* cur = (n & 1) ? L1 : L0;
@@ -680,22 +664,24 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
     for (int fl = 0; fl < 4; ++fl) pv[fl] = nprev[fl];
     const dsf kv = nkv, bv = nbv;
     if (i + 1 < kTileRows) fetch_row(i + 1);
-    ds2 sx = xstencil2<R>(spu, r, cc, true);    // (D_x p, D_x u), unscaled
-    ds2 sy = xstencil2<R>(spv, r, cc, false);   // (D_y p, D_y v), unscaled
+    // (D_x p, D_x u) and (D_y p, D_y v) times the integer weights' divisor, unscaled by dx
+    ds2 sx = isum_x2<R>([&](int j) { const float4 v = spu[r][cc + j]; return make_float2(v.x, v.y); },
+                        [&](int j) { const float4 v = spu[r][cc + j]; return make_float2(v.z, v.w); });
+    ds2 sy = isum_x2<R>([&](int j) { const float4 v = spv[r + j][cc]; return make_float2(v.x, v.y); },
+                        [&](int j) { const float4 v = spv[r + j][cc]; return make_float2(v.z, v.w); });
     const int64_t pt = plane + (int64_t)y * nx + x;
-    ds2 sz{};                                    // (D_z p, D_z w), 3D only
+    ds2 sz{};                                    // (D_z p, D_z w) times the divisor, 3D only
     if (DIM == 3) {
+      ds2 zv[2 * R + 1];                         // (p, w) at z - R .. z + R (the centre unused)
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
         const int zp = z + j >= nz ? z + j - nz : z + j;
         const int zm = z - j < 0 ? z - j + nz : z - j;
         const int64_t op = (int64_t)(zp - z) * nx * ny, om = (int64_t)(zm - z) * nx * ny;
-        const double cj = fd_coef<R>(j);
-        const ds2 d = make_ds2(ldg(cur + pt + op), ldg(cur + 3 * P + pt + op)) -
-                      make_ds2(ldg(cur + pt + om), ldg(cur + 3 * P + pt + om));
-        const ds2 t = ds2_mul(d, float(cj), float(cj - double(float(cj))));
-        sz = j == 1 ? t : sz + t;
+        zv[R + j] = make_ds2(ldg(cur + pt + op), ldg(cur + 3 * P + pt + op));
+        zv[R - j] = make_ds2(ldg(cur + pt + om), ldg(cur + 3 * P + pt + om));
       }
+      sz = isum_x2<R>([&](int j) { return zv[R + j].hi; }, [&](int j) { return zv[R + j].lo; });
     }
     if (!unit) {
       sx = ds2_mul(sx, idx.hi, idx.lo);
