@@ -114,3 +114,14 @@ def test_product_scheme_table_matches_printed_values():
     assert S.GBS_8_6.updates_per_point == 143
     assert S.GBS_8_8.updates_per_point == 255
     assert S.SQ8_2468.updates_per_point == 24
+
+
+def test_entry_points_refuse_a_null_handle_without_gpu(libpath):
+    # every stepping call checks its handle before any device work, the host-stream call
+    # included (its arrays of host buffers are checked next)
+    L = B.lib()
+    ptrs = (ctypes.c_void_p * 1)(None)
+    assert L.gbs_step_host_stream(None, ptrs, ptrs, 1, ctypes.c_double(0.1), 1) == 1
+    assert L.gbs_step_host(None, None, None, ctypes.c_double(0.1), 1) == 1
+    assert L.gbs_step(None, None, None, ctypes.c_double(0.1), 1) == 1
+    assert L.gbs_set_option(None, b"tma", 1) == 1
