@@ -666,7 +666,14 @@ def run_time_to_solution(args):
 
     f64 = solver(B.GBS_F64, S.GBS_8_6, B.GBS_KERNEL_PLAIN)
     H0 = H_FRACTION * f64.stability_limit()[0]
-    T = M0 * H0
+    T = M0 * H0                          # the final time: M0 macro-steps of GBS_8,6 at H0
+    # the scheme raced (default GBS_8,6): M0 becomes the fewest of its macro-steps at 0.8 x its
+    # own stability limit that reach T
+    scheme = S.ALL[args.tts_scheme]
+    if scheme is not S.GBS_8_6:
+        sch = solver(B.GBS_F64, scheme, B.GBS_KERNEL_PLAIN)
+        M0 = int(np.ceil(T / (H_FRACTION * sch.stability_limit()[0])))
+        sch.close()
     ref_sol = solver(B.GBS_F64, S.GBS_12_8, B.GBS_KERNEL_PLAIN)
     Mref = int(np.ceil(T / (H_FRACTION * ref_sol.stability_limit()[0]))) * 4
     ref, _ = run(ref_sol, T / Mref, Mref, torch.float64)
@@ -680,7 +687,7 @@ def run_time_to_solution(args):
              ("fused FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_FUSED, torch.float64)]
     tuned = {}
     for name, prec, kernel, dt in paths:
-        sol = solver(prec, S.GBS_8_6, kernel)
+        sol = solver(prec, scheme, kernel)
         if kernel == B.GBS_KERNEL_FUSED and not args.no_autotune:
             from paper_1907_11771_gb300 import autotune as AT
             yt = torch.tensor(y0.ravel(), dtype=dt, device="cuda")
@@ -692,10 +699,11 @@ def run_time_to_solution(args):
             M = M0 * 2 ** j
             out, secs = run(sol, T / M, M, dt)
             rows[name].append({"H_over_H0": 2.0 ** -j, "macro_steps": M, "seconds": secs, "rel_l2": rel(out),
-                               "gpt_updates_per_s": S.GBS_8_6.updates_per_point * n * n * M / secs / 1e9})
+                               "gpt_updates_per_s": scheme.updates_per_point * n * n * M / secs / 1e9})
         sol.close()
     best = {k: min((r["seconds"] for r in v if r["rel_l2"] <= 1e-6), default=None) for k, v in rows.items()}
-    print(json.dumps({"study": "time to relative L2 error 1e-6", "grid": [n, n], "t_final": T, "H0": H0,
+    print(json.dumps({"study": "time to relative L2 error 1e-6", "grid": [n, n], "scheme": scheme.name,
+                      "t_final": T, "H0": T / M0,
                       "macro_steps_at_H0": M0, "reference": f"GBS_12,8 FP64, {Mref} macro-steps",
                       "reference_self_check_rel_l2": ref_err, "paths": rows, "time_to_1e-6_s": best,
                       "autotuned_schedule": tuned}), flush=True)
@@ -739,6 +747,7 @@ def main():
     ap.add_argument("--tts-grid", type=int, default=1024)
     ap.add_argument("--tts-macro", type=int, default=100)
     ap.add_argument("--tts-levels", type=int, default=3)
+    ap.add_argument("--tts-scheme", default="GBS_8,6", help="scheme raced in the time-to-solution study (schemes.ALL)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gbs":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
