@@ -3,7 +3,10 @@
 The time-blocked kernel's work decomposition has three knobs that change its speed but not its
 results beyond rounding order: the row-segment height of a tile ("hseg"), the most leap-frog
 levels per pass ("tmax"; deeper passes move fewer bytes but widen the halo) and the order of
-the work queue ("schedule").  ``autotune`` times every candidate on the caller's own problem
+the work queue ("schedule").  The plain one-step-per-launch kernels are one more candidate: with
+few sequences on a small grid the time-blocked kernel has too few independent items and waits on
+its dependencies, and the plain kernels are faster.  ``autotune`` times every candidate on the
+caller's own problem
 (whole macro-steps, CUDA events on the current stream, a buffer larger than L2 written before
 each timed step), applies the fastest and caches the choice in a JSON file keyed by the
 workload and the GPU, so a later run with the same key applies it without timing.
@@ -86,15 +89,24 @@ def event_timer(solver, y, H, reps=3, warmup=1, flush_bytes=256 << 20):
     return timer
 
 
-def autotune(solver, y=None, H=None, space=None, cache=None, timer=None, key=None, retune=False):
-    """Pick the fastest time-blocked schedule for `solver`'s problem and apply it.
+def _apply(solver, options):
+    from . import binding as B
+    for k in KNOBS:
+        solver.set_option(k, options[k])
+    solver.set_option("kernel", options.get("kernel", B.GBS_KERNEL_FUSED))
+
+
+def autotune(solver, y=None, H=None, space=None, cache=None, timer=None, key=None, retune=False, plain=True):
+    """Pick the fastest time-blocked schedule for `solver`'s problem -- or the plain kernels, if
+    `plain` and they are faster -- and apply it.
 
     y, H: a representative state and step size (used by the default event timer).  space: dict
     knob -> candidate values (default DEFAULT_SPACE).  cache: JSON path (default
     default_cache_path(); False disables caching).  timer: callable() -> seconds for the options
     currently set (default: CUDA-event timing of one macro-step).  Returns a dict with the chosen
-    options, their time and the whole table; None when the problem does not use the
-    time-blocked kernel (nothing to tune)."""
+    options ("kernel" plus the schedule knobs), their time and the whole table; None when the
+    problem does not use the time-blocked kernel (nothing to tune)."""
+    from . import binding as B
     if not solver.uses_fused():
         return None
     space = dict(DEFAULT_SPACE if space is None else space)
@@ -104,20 +116,23 @@ def autotune(solver, y=None, H=None, space=None, cache=None, timer=None, key=Non
     table = _load(cache) if cache else {}
     if cache and not retune and key in table:
         best = table[key]
-        for k in KNOBS:
-            solver.set_option(k, best["options"][k])
+        _apply(solver, best["options"])
         return dict(best, cached=True)
     if timer is None:
         timer = event_timer(solver, y, H)
     rows = []
+    solver.set_option("kernel", B.GBS_KERNEL_FUSED)
     for values in itertools.product(*(space[k] for k in KNOBS)):
         opts = dict(zip(KNOBS, values))
         for k, v in opts.items():
             solver.set_option(k, v)
-        rows.append({"options": opts, "seconds": float(timer())})
+        rows.append({"options": dict(opts, kernel=B.GBS_KERNEL_FUSED), "seconds": float(timer())})
+    if plain:   # the plain kernels, keeping the best schedule for a later switch back
+        fused_best = min(rows, key=lambda r: r["seconds"])["options"]
+        solver.set_option("kernel", B.GBS_KERNEL_PLAIN)
+        rows.append({"options": dict(fused_best, kernel=B.GBS_KERNEL_PLAIN), "seconds": float(timer())})
     best = min(rows, key=lambda r: r["seconds"])
-    for k in KNOBS:
-        solver.set_option(k, best["options"][k])
+    _apply(solver, best["options"])
     result = {"options": best["options"], "seconds": best["seconds"], "table": rows}
     if cache:
         table = _load(cache)

@@ -29,9 +29,9 @@ def test_autotune_applies_caches_and_keeps_parity(tmp_path):
     cache = str(tmp_path / "tune.json")
     space = {"hseg": [48, 96, 512], "tmax": [4, 2], "schedule": [0, 1]}
     r = A.autotune(sol, y, H, space=space, cache=cache)
-    assert not r["cached"] and len(r["table"]) == 12
+    assert not r["cached"] and len(r["table"]) == 12 + 1          # the schedules and the plain kernels
     assert all(row["seconds"] > 0 for row in r["table"])
-    for k in A.KNOBS:
+    for k in A.KNOBS + ("kernel",):
         assert sol.get_option(k) == r["options"][k]
     steps, c = oracle_scheme(S.GBS_8_6)
     o = case.oracle_run(steps, c, H, 2)
