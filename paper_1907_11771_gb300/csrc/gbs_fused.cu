@@ -353,37 +353,12 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
 // The same sweep in FP32-pair arithmetic (GBS_F32X2: FP64 states carried as hi + lo float pairs),
 // passes of two levels.  Every value is a pair: (p, v) windows as ds2 (two pairs per packed
 // lane), (p, u) plane entries as float4 (p.hi, u.hi, p.lo, u.lo), the scaled media as float4
-// (kappa'.hi, kappa'.lo, b'.hi, b'.lo); every sum, product and update is a pair operation
-// (gbs_ds.cuh).  With T = 2 the register windows and shared planes take the room the FP32
-// sweep takes at T = 4.
+// (kappa'.hi, kappa'.lo, b'.hi, b'.lo); the stencil sums are exact integer-weight pair sums
+// (isum_x2, their divisor folded into the media scaling) and every other sum, product and update
+// is a pair operation (gbs_ds.cuh).  With T = 2 the register windows and shared planes take the
+// room the FP32 sweep takes at T = 4.
 // ---------------------------------------------------------------------------
 constexpr int kTX2 = 2;
-
-__host__ __device__ constexpr float fd_hi(int R, int j) { return float(R == 2 ? fd_coef<2>(j) : fd_coef<3>(j)); }
-__host__ __device__ constexpr float fd_lo(int R, int j) {
-  return float((R == 2 ? fd_coef<2>(j) : fd_coef<3>(j)) - double(fd_hi(R, j)));
-}
-
-__device__ __forceinline__ ds2 ds2_of(float4 a) { return ds2{make_float2(a.x, a.y), make_float2(a.z, a.w)}; }
-
-// x-sums of (p, u) over a plane row: sum_j c_j (row[+j] - row[-j]) in pairs
-template <int R>
-__device__ __forceinline__ ds2 xsum_x2(const float4* row) {
-  ds2 acc = ds2_mul(ds2_of(row[1]) - ds2_of(row[-1]), fd_hi(R, 1), fd_lo(R, 1));
-#pragma unroll
-  for (int j = 2; j <= R; ++j) acc = acc + ds2_mul(ds2_of(row[j]) - ds2_of(row[-j]), fd_hi(R, j), fd_lo(R, j));
-  return acc;
-}
-
-// y-sums of (p, v) over a register window indexed by row mod U
-template <int R>
-__device__ __forceinline__ ds2 ysum_x2(const ds2 (&w)[2 * R + 1], int r) {
-  constexpr int U = 2 * R + 1;
-  ds2 acc = ds2_mul(w[(r + 1) % U] - w[(r + U - 1) % U], fd_hi(R, 1), fd_lo(R, 1));
-#pragma unroll
-  for (int j = 2; j <= R; ++j) acc = acc + ds2_mul(w[(r + j) % U] - w[(r + U - j) % U], fd_hi(R, j), fd_lo(R, j));
-  return acc;
-}
 
 // x-sums of (p, u) and y-sums of (p, v) in the integer form (times fd_div)
 template <int R>
