@@ -640,19 +640,22 @@ size_t ring_bytes(int R, bool x2) {
   return (size_t)(kTMax * u * kRow + media_planes() * u * kThreads) * sizeof(float2);
 }
 
-// GBS_F32X2: y_out (FP64) = sum_k c_k y*_k, the averages held as FP32 pairs, summed in FP64 in
-// ascending k (the FP64 combine of the pair path)
+// GBS_F32X2: y_out (FP64) = sum_k c_k y*_k from the averages held as FP32 pairs, summed in
+// ascending k in compensated FP32 pairs as the FP32 path does (pair_combine_add on the hi parts,
+// c_hi times the lo parts into the low word; error about 2^-48 of sum_k |c_k y*_k|) and rounded
+// to FP64 once.  An FP64 sum spent 1.08 ms of a 9.3 ms 2048^2 macro-step on GB300's FP64 pipe.
 __global__ void __launch_bounds__(256) k_combine_x2(const ProbDev* probs, int batch, const SlotDev* slots,
                                                     const float2* __restrict__ ystar, int64_t E,
                                                     double* __restrict__ y_out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
     const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
-    double acc = 0.0;
+    float sh = 0.f, sl = 0.f;
     for (int k = 0; k < s.m; ++k) {
       const float2 v = __ldcs(ystar + (int64_t)k * E + e);
-      acc = fma(s.c[k], (double)v.x + (double)v.y, acc);
+      pair_combine_add(s.chi[k], s.clo[k], v.x, sh, sl);
+      sl = fmaf(s.chi[k], v.y, sl);
     }
-    y_out[e] = acc;
+    y_out[e] = (double)sh + (double)sl;
   }
 }
 
