@@ -125,3 +125,30 @@ def test_entry_points_refuse_a_null_handle_without_gpu(libpath):
     assert L.gbs_step_host(None, None, None, ctypes.c_double(0.1), 1) == 1
     assert L.gbs_step(None, None, None, ctypes.c_double(0.1), 1) == 1
     assert L.gbs_set_option(None, b"tma", 1) == 1
+
+
+def test_noalloc_refuses_invalid_descriptions_without_gpu(libpath):
+    # the allocation-free entry point checks the description, the media and the state pointers
+    # before its first device call, and leaves a message naming the problem
+    B.lib()
+    sq = S.SQ8_2468
+    args = (sq.order, sq.steps_dep, sq.steps_free, [])
+    cases = [
+        (B.make_problem(3, 1, 4, B.GBS_F64, [(16,)], [(1.0,)]), None, None, 1, 1, "system"),
+        (B.make_problem(B.GBS_WAVE1D, 2, 4, B.GBS_F64, [(16, 16)], [(1.0, 1.0)]), None, None, 1, 1, "ndim"),
+        (B.make_problem(B.GBS_ACOUSTIC, 2, 5, B.GBS_F64, [(16, 16)], [(1.0, 1.0)]), 1, 1, 1, 1, "fd_order"),
+        (B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F32X2, [(16, 16)], [(1.0, 1.0)]), 1, 1, 1, 1, "precision"),
+        (B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F64, [(16, 16)], [(1.0, 1.0)], enable_adjoint=True),
+         1, 1, 1, 1, "adjoint"),
+        (B.make_problem(B.GBS_ACOUSTIC, 2, 4, B.GBS_F64, [(16, 16)], [(1.0, 1.0)]), None, None, 1, 1, "kappa"),
+        (B.make_problem(B.GBS_WAVE1D, 1, 4, B.GBS_F64, [(16,)], [(1.0,)]), 1, 1, 1, 1, "kappa"),
+        (B.make_problem(B.GBS_WAVE1D, 1, 4, B.GBS_F64, [(16,)], [(1.0,)]), None, None, None, 1, "NULL"),
+    ]
+    for pb, kappa, rho, y_in, y_out, word in cases:
+        with pytest.raises(B.GbsError) as e:
+            B.gbs_step_noalloc(pb, kappa, rho, *args, y_in, y_out, 0.1, 1)
+        assert e.value.status == 1
+        assert word in B.gbs_noalloc_last_error(), (word, B.gbs_noalloc_last_error())
+    assert B.lib().gbs_step_noalloc(None, None, None, 8, 4, None, 0, None, None, None, None,
+                                    ctypes.c_double(0.1), 1, None) == 1
+    assert "NULL" in B.gbs_noalloc_last_error()
