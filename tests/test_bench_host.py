@@ -1,0 +1,45 @@
+"""bench.py's host-side bookkeeping (no GPU): the clock record that decides whether
+a timed run is kept, and the HBM peak the roofline divides by."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def _summary_of(tmp_path, lines):
+    path = tmp_path / "clocks.csv"
+    path.write_text("".join(l + "\n" for l in lines))
+    s = bench.ClockSampler(0)
+    s.proc, s.path = object(), str(path)
+    return s.summary()
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path):
+    ok = "0, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {cap}"
+    lines = [ok.format(mhz=m, cap="Not Active") for m in (2070, 2055, 2070, 1980)]
+    lines.append(ok.format(mhz=1900, cap="Active"))
+    lines.append("garbage line")
+    s = _summary_of(tmp_path, lines)
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 5
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_reports_thermal_and_hw_slowdown(tmp_path):
+    line = "0, 1500, 2070, 1300.0, 0x48, Active, Not Active, Active, Not Active"
+    s = _summary_of(tmp_path, [line])
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_nvidia_smi():
+    s = bench.ClockSampler(0).summary()
+    assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(monkeypatch, tmp_path):
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6753.8}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6753.8, "measured")
+    os.unlink(tmp_path / "MEASURED_PEAKS.json")
+    assert bench.peaks() == (pytest.approx(6800.0), "fallback")
