@@ -98,10 +98,14 @@ typedef struct {
 } gbs_problem;
 
 /* Bytes of device workspace gbs_create would allocate for `pb` when schemes
- * with up to `max_steps` steps per sequence are used (0 on invalid input). */
+ * with up to `max_steps` steps per sequence are used (0 on invalid input).
+ * No counterpart in the paper: sizing of the storage for the levels of
+ * Sec. 2.1 eq. "GBS".  Host only; never touches the GPU. */
 size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps);
 
-/* Number of scalars in one state buffer of `pb` (sum over problems of F * points). */
+/* Number of scalars in one state buffer of `pb` (sum over problems of F * points):
+ * the length of the method-of-lines state y of y' = f(y) (Sec. 2.1).  Host only;
+ * 0 on invalid input. */
 size_t gbs_state_elems(const gbs_problem* pb);
 
 /* Create a handle.  kappa and rho are device arrays (media layout, state
@@ -111,11 +115,19 @@ size_t gbs_state_elems(const gbs_problem* pb);
  * legacy default stream).  All workspace is allocated here, none later, except
  * the adjoint level store sized in gbs_set_weights.
  * Errors: GBS_ERR_INVALID (bad description or pointers), GBS_ERR_NOMEM,
- * GBS_ERR_CUDA; *out is NULL on error. */
+ * GBS_ERR_CUDA; *out is NULL on error.
+ * Defines the ODE y' = f(y) that the macro-steps advance (Sec. 2.1); the
+ * paper leaves the spatial operator open, so f is one of the periodic systems
+ * of gbs_problem.system (Sec. 4's spectral one-way wave among them). */
 gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
                       void* cuda_stream, gbs_handle* out);
 
-/* Replace the media (same layout rules as gbs_create); recomputes b = 1/rho. */
+/* Replace the media (same layout rules as gbs_create); recomputes b = 1/rho.
+ * The coefficients of f in y' = f(y) (Sec. 2.1); the paper's own test problem
+ * has none.  Waits for the handle's stream (the wave-speed maximum used by
+ * gbs_stability_limit is read back); the caller keeps kappa alive.  Errors:
+ * GBS_ERR_INVALID (NULL handle, a non-acoustic handle, non-device pointers),
+ * GBS_ERR_NONFINITE (a non-positive or non-finite wave speed), GBS_ERR_CUDA. */
 gbs_status gbs_set_media(gbs_handle h, const void* kappa, const void* rho);
 
 /* Define the scheme of weight slot `slot` (0 <= slot < GBS_MAX_SLOTS).
@@ -138,17 +150,29 @@ gbs_status gbs_set_weights(gbs_handle h, int slot, int order_p, int n_dep, const
 /* Read back a slot: *m sequences, steps[m] and FP64 weights c[m] (host arrays
  * of at least GBS_MAX_SEQ entries, each may be NULL), and *isb = the
  * imaginary stability boundary of R(xi) = sum_k c_k P_k(xi), found by a dense
- * scan of |R(iy)| - 1 > 1e-12 refined by bisection (may be NULL). */
+ * scan of |R(iy)| - 1 > 1e-12 refined by bisection (may be NULL).
+ * R(xi) is the scheme's stability polynomial on Dahlquist's test equation
+ * (App. A.1) and the ISB its imaginary-axis coverage (Sec. 2.2).  Host only.
+ * Errors: GBS_ERR_INVALID (bad handle or slot), GBS_ERR_STATE (slot unset). */
 gbs_status gbs_get_weights(gbs_handle h, int slot, int* m, int* steps, double* c, double* isb);
 
 /* Batched problems: host array slot_per_problem[batch] selects each
- * problem's weight slot (default: all use slot 0). */
+ * problem's weight slot (default: all use slot 0).  No counterpart in the
+ * paper (batches of independent problems are a library addition; each
+ * problem still takes the macro-step of Sec. 2.1).  Errors: GBS_ERR_INVALID
+ * (NULL handle or array, slot out of range), GBS_ERR_STATE (a slot without
+ * weights), GBS_ERR_CUDA (table upload). */
 gbs_status gbs_assign_slots(gbs_handle h, const int* slot_per_problem);
 
 /* Largest stable H per problem as ISB(slot) / rho_hat, where rho_hat =
  * max(sqrt(kappa b)) * sqrt(sum_d (s_max / dx_d)^2) bounds the spectral
  * radius of the acoustic operator (s_max = max |stencil symbol|; for the 1D
- * wave system kappa b = 1).  H_max: host array of `batch` doubles. */
+ * wave system kappa b = 1).  H_max: host array of `batch` doubles.
+ * Follows App. A.1 (the eigenvalues of the method-of-lines operator, scaled by
+ * the step, must lie in the stability domain; for these wave operators they
+ * lie on the imaginary axis) with the ISB of Sec. 2.2.  Host only (the wave
+ * speeds are read back when the media are set).  Errors: GBS_ERR_INVALID
+ * (NULL handle or H_max), GBS_ERR_STATE (a used slot has no weights). */
 gbs_status gbs_stability_limit(gbs_handle h, double* H_max);
 
 /* Advance every problem by n_macro macro-steps of size H (Sec. 2.1 / 3.2):
@@ -158,12 +182,17 @@ gbs_status gbs_stability_limit(gbs_handle h, double* H_max);
  * (a used slot has no weights), GBS_ERR_CUDA (launch failure). */
 gbs_status gbs_step(gbs_handle h, const void* y_in, void* y_out, double H, int n_macro);
 
-/* As gbs_step with one H per problem (host array of `batch` doubles). */
+/* As gbs_step with one H per problem (host array of `batch` doubles): the
+ * macro-step of Sec. 2.1 / 3.2 for each problem with its own section length.
+ * Errors as gbs_step, and GBS_ERR_INVALID for a NULL array or an H that is
+ * not finite and positive. */
 gbs_status gbs_step_batch(gbs_handle h, const void* y_in, void* y_out, const double* H,
                           int n_macro);
 
 /* End-to-end variant: y_in and y_out are HOST buffers (pinned or pageable).
- * Copies in, steps on the device, copies out and waits for completion. */
+ * Copies in, steps on the device, copies out and waits for completion.
+ * Computes what gbs_step computes (Sec. 2.1 / 3.2) through library-owned
+ * device staging; allocates nothing.  Errors as gbs_step. */
 gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, double H,
                          int n_macro);
 
@@ -204,20 +233,25 @@ gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out,
  * arrays, state element type) and, if J is non-NULL (device double), adds
  * 0.5 * sum_i resid[i]^2 to *J with a warp-shuffle reduction.  Indices are
  * flat points of field 0 of problem 0; one outside [0, points) gets a zero
- * residual and latches GBS_ERR_INVALID (reported by gbs_sync()). */
+ * residual and latches GBS_ERR_INVALID (reported by gbs_sync()).
+ * Not in the paper: the receiver misfit whose gradient gbs_adjoint_step
+ * serves. */
 gbs_status gbs_misfit(gbs_handle h, const void* y, const int64_t* rcv_idx, int n_rcv,
                       const void* data, void* resid, double* J);
 
 /* Adjoint of receiver sampling: lam[field 0][rcv_idx[i]] += values[i] (device
  * arrays; indices of problem 0, range-checked like gbs_misfit).  Used to seed
- * the adjoint with the misfit residual of the final state. */
+ * the adjoint with the misfit residual of the final state.  Not in the paper
+ * (the transpose of gbs_misfit's sampling). */
 gbs_status gbs_inject(gbs_handle h, void* lam, const int64_t* rcv_idx, int n_rcv, const void* values);
 
 /* Norms over a whole state buffer, accumulated in FP64 with warp-shuffle and
  * block reductions in a fixed order: out[0] = sum (a - b)^2,
  * out[1] = sum b^2, out[2] = max |a - b|, out[3] = number of non-finite
  * entries of a.  `b` may be NULL (treated as zero).  out: host array of 4
- * doubles; the call waits for the result. */
+ * doubles; the call waits for the result.  No counterpart in the paper: the
+ * error measure of the parity checks and of the time-to-accuracy study.
+ * Errors: GBS_ERR_INVALID (NULL handle, a or out), GBS_ERR_CUDA. */
 gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
 
 /* Tuning options: "kernel" = GBS_KERNEL_*, "graph" = 0/1 (CUDA-graph replay
@@ -243,7 +277,8 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * wherever they apply, -1 only in 3D (where they measured faster), 0 never;
  * gbs_get_option answers 1 only where those copies are in use.  gbs_get_option also
  * answers "kernel_in_use" (the GBS_KERNEL_* value gbs_step would run now).
- * Unknown names: GBS_ERR_INVALID. */
+ * Unknown names: GBS_ERR_INVALID.  No counterpart in the paper: these choose
+ * how the macro-step is scheduled on the GPU, not what it computes. */
 gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value);
 gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value);
 
@@ -253,20 +288,28 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value);
  * kernel in gbs_adjoint_step); also
  * reports the algorithmic bytes those launches move (*bytes, may be NULL), the
  * per-launch figure being the unit cost of the kernel times the grid-point
- * updates it performs.  Waits for the stream; resets the counters. */
+ * updates it performs.  Waits for the stream; resets the counters.  No
+ * counterpart in the paper (measurement).  launches and total_ms are host
+ * pointers.  Errors: GBS_ERR_INVALID, GBS_ERR_CUDA. */
 gbs_status gbs_kernel_time(gbs_handle h, int64_t* launches, double* total_ms, double* bytes);
 
-/* Wait for the handle's stream and report a latched device-side error. */
+/* Wait for the handle's stream and report a latched device-side error
+ * (GBS_ERR_TIMEOUT from a bounded wait that ran out, GBS_ERR_INVALID from an
+ * out-of-range receiver index), clearing it, or GBS_ERR_CUDA.  No counterpart
+ * in the paper (library service). */
 gbs_status gbs_sync(gbs_handle h);
 
-/* Free the workspace and the handle (NULL is accepted). */
+/* Free the workspace and the handle (NULL is accepted).  Waits for work in
+ * flight on the handle's stream first.  No counterpart in the paper. */
 gbs_status gbs_destroy(gbs_handle h);
 
 /* Last error message of `h` ("" if none); for h == NULL, the last error of a
- * failed gbs_create on this thread.  Valid until the next call on h. */
+ * failed gbs_create on this thread.  Valid until the next call on h.  No
+ * counterpart in the paper. */
 const char* gbs_last_error(gbs_handle h);
 
-/* Number of GPU kernels this handle has launched (for launch accounting). */
+/* Number of GPU kernels this handle has launched (for launch accounting;
+ * 0 for NULL).  No counterpart in the paper. */
 int64_t gbs_kernel_launches(gbs_handle h);
 
 /* ---------------------------------------------------------------------------
@@ -303,7 +346,8 @@ gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa, const void
                             const double* c_free, const void* y_in, void* y_out, double H,
                             int n_macro, void* cuda_stream);
 
-/* Message of the last failed gbs_step_noalloc call on this thread ("" if none). */
+/* Message of the last failed gbs_step_noalloc call on this thread ("" if none).
+ * No counterpart in the paper. */
 const char* gbs_noalloc_last_error(void);
 
 #ifdef __cplusplus

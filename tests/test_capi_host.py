@@ -152,3 +152,18 @@ def test_noalloc_refuses_invalid_descriptions_without_gpu(libpath):
     assert B.lib().gbs_step_noalloc(None, None, None, 8, 4, None, 0, None, None, None, None,
                                     ctypes.c_double(0.1), 1, None) == 1
     assert "NULL" in B.gbs_noalloc_last_error()
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    # each entry point's comment names the section, equation or appendix that defines the
+    # operation, or states that the paper has no counterpart
+    src = open(os.path.join(ROOT, "include", "gbs.h")).read()
+    cite = re.compile(r"Sec\. \d|App\. [AB]|eq\. \"|no counterpart|not in the paper", re.I)
+    names = []
+    for m in re.finditer(r"^[a-z][a-z_0-9 *]*\b(gbs_[a-z_0-9]+)\s*\(", src, flags=re.M):
+        before = src[:m.start()]
+        comment = before[before.rfind("/*"):before.rfind("*/")]
+        comment = re.sub(r"\s*\n\s*\*\s*", " ", comment)
+        assert cite.search(comment), m.group(1)
+        names.append(m.group(1))
+    assert set(names) == set(declared_symbols())
