@@ -36,7 +36,8 @@ def gbs_sequence(f, y0, H, N, f0=None):
 
 
 def gbs_macro_step(f, y, H, steps, c, state_dtype=None):
-    """sum_k c_k y*_k for the sequences ``steps`` with weights ``c``; FP64 sum."""
+    """sum_k c_k y*_k for the sequences ``steps`` with weights ``c``; FP64 sum.
+    Sec. 2.1 eq. "GBS" per sequence, combined as in Sec. 3.2."""
     sdt = np.dtype(state_dtype) if state_dtype is not None else y.dtype
     ys = y.astype(sdt)
     f0 = f(ys)                                     # shared first evaluation
@@ -59,7 +60,8 @@ def gbs_run(f, y, H, steps, c, n_macro, state_dtype=None):
 # --------------------------------------------------------------------------
 
 def gbs_macro_step_adjoint(f, fT, pair, y0, lam_out, H, steps, c):
-    """Return (lam_in, g) with lam_in = M^T lam_out for the linear macro-step
+    """Not in the paper: the exact transpose of the Sec. 2.1 macro-step.
+    Return (lam_in, g) with lam_in = M^T lam_out for the linear macro-step
     y_out = M y0 = sum_k c_k S_k y0, and g = d<lam_out, M(kappa) y0>/dkappa
     pointwise (``pair(mu, y)`` returns <mu, dA/dkappa_i y> for every i).
 
@@ -101,12 +103,13 @@ def gbs_macro_step_adjoint(f, fT, pair, y0, lam_out, H, steps, c):
 # --------------------------------------------------------------------------
 
 def sample_receivers(y, rcv_flat):
-    """Pressure (field 0) at flat grid indices ``rcv_flat``."""
+    """Pressure (field 0) at flat grid indices ``rcv_flat`` (receiver sampling; not in the paper)."""
     return y[0].reshape(-1)[rcv_flat]
 
 
 def inject_receivers(shape, rcv_flat, values, dtype=np.float64):
-    """A state-shaped array that is zero except field 0 at the receivers (adds duplicates)."""
+    """Not in the paper: the transpose of ``sample_receivers``.
+    A state-shaped array that is zero except field 0 at the receivers (adds duplicates)."""
     out = np.zeros(shape, dtype=dtype)
     flat = out[0].reshape(-1)
     np.add.at(flat, rcv_flat, values)
@@ -115,7 +118,8 @@ def inject_receivers(shape, rcv_flat, values, dtype=np.float64):
 
 
 def misfit_and_gradient(f, fT, pair, y0, H, steps, c, n_macro, rcv_flat, data):
-    """J = 1/2 sum_m sum_r (p(x_r, t_m) - d_r(t_m))^2 over macro-step ends m = 1..n_macro
+    """Not in the paper (receiver misfit and its gradient by the adjoint).
+    J = 1/2 sum_m sum_r (p(x_r, t_m) - d_r(t_m))^2 over macro-step ends m = 1..n_macro
     and dJ/dkappa by the discrete adjoint.  ``data`` has shape (n_macro, n_rcv)."""
     states = [y0]
     for _ in range(n_macro):

@@ -42,7 +42,8 @@ def _axis(f, d):
 
 
 def deriv(f, d, dx, order):
-    """Centred periodic first derivative of the field ``f`` along direction d."""
+    """Centred periodic first derivative of the field ``f`` along direction d.
+    Textbook 4th/6th-order weights; the paper fixes no spatial operator (Sec. 4 uses spectral ones)."""
     dt = f.dtype.type
     out = np.zeros_like(f)
     for j, w in FD_WEIGHTS[order].items():
@@ -51,7 +52,7 @@ def deriv(f, d, dx, order):
 
 
 def deriv_T(f, d, dx, order):
-    """Transpose of ``deriv`` (each shift replaced by the opposite shift)."""
+    """Transpose of ``deriv`` (each shift replaced by the opposite shift); for the adjoint, not in the paper."""
     dt = f.dtype.type
     out = np.zeros_like(f)
     for j, w in FD_WEIGHTS[order].items():
@@ -78,7 +79,8 @@ def rhs_wave1d_T(lam, dx, order):
 # --------------------------------------------------------------------------
 
 def rhs_acoustic(y, kappa, b, dx, order):
-    """f(y) for y = (p, u_x, u_y[, u_z]); kappa, b arrays of the grid shape."""
+    """f(y) for y = (p, u_x, u_y[, u_z]); kappa, b arrays of the grid shape.
+    The right-hand side of y' = f(y) (Sec. 2.1) for linear acoustics; the paper fixes no system."""
     ndim = y.ndim - 1
     p = y[0]
     div = np.zeros_like(p)
@@ -91,7 +93,7 @@ def rhs_acoustic(y, kappa, b, dx, order):
 
 
 def rhs_acoustic_T(lam, kappa, b, dx, order):
-    """A^T lam for the acoustic operator A(kappa, b) of ``rhs_acoustic``."""
+    """A^T lam for the acoustic operator A(kappa, b) of ``rhs_acoustic`` (adjoint; not in the paper)."""
     ndim = lam.ndim - 1
     lp = lam[0]
     out_p = np.zeros_like(lp)
@@ -104,7 +106,8 @@ def rhs_acoustic_T(lam, kappa, b, dx, order):
 
 
 def dA_dkappa_pairing(mu, y, dx, order):
-    """Pointwise <mu, (dA/dkappa_i) y>: the p row of A y is -kappa div u, so the
+    """Not in the paper (gradient with respect to kappa).
+    Pointwise <mu, (dA/dkappa_i) y>: the p row of A y is -kappa div u, so the
     derivative with respect to kappa at point i is mu_p[i] * (-div u)[i]."""
     ndim = y.ndim - 1
     div = np.zeros_like(y[0])
@@ -149,7 +152,8 @@ def symbol_max(order):
 
 
 def power_iteration_rho(apply_A, y_shape, iters=300, seed=0):
-    """Estimate the spectral radius of A by power iteration on A^2.
+    """Estimate the spectral radius of A by power iteration on A^2: the bound on |lambda| that
+    App. A.1 scales by the step to place the spectrum in the stability domain.
 
     For the operators here A is skew-adjoint in an energy inner product, so its
     eigenvalues are +-i omega and A^2 has the real, non-positive eigenvalues

@@ -44,7 +44,8 @@ def rhs_b(order):
 
 
 def solve_exact(A, b):
-    """Solve the square rational system A x = b by plain Gauss-Jordan elimination."""
+    """Solve the square rational system A x = b by plain Gauss-Jordan elimination
+    (Sec. 3.2 eq. "vander", Sec. 3.7 eq. "cdep_computation")."""
     n = len(A)
     M = [list(map(Fraction, A[i])) + [Fraction(b[i])] for i in range(n)]
     for col in range(n):
@@ -77,13 +78,13 @@ def dependent_weights(order, steps_dep, steps_free, c_free):
 
 
 def scheme_weights(order, steps_dep, steps_free=(), c_free=()):
-    """Full step-count list and exact weight list (dependent first, then free)."""
+    """Full step-count list and exact weight list (dependent first, then free); Sec. 3.7."""
     c_dep = dependent_weights(order, list(steps_dep), list(steps_free), list(c_free))
     return list(steps_dep) + list(steps_free), c_dep + [Fraction(c) for c in c_free]
 
 
 def order_residuals(steps, c, order):
-    """sum_i c_i h_i^(2j) - b_j for j = 0..p/2-1, exactly."""
+    """sum_i c_i h_i^(2j) - b_j for j = 0..p/2-1, exactly: the order constraints of Sec. 3.7."""
     V = vandermonde(steps, order)
     b = rhs_b(order)
     return [sum((V[j][i] * Fraction(c[i]) for i in range(len(steps))), Fraction(0)) - b[j]
@@ -91,7 +92,8 @@ def order_residuals(steps, c, order):
 
 
 def to_fp64(c):
-    """Round exact weights to nearest FP64 (Python's Fraction -> float rounds correctly)."""
+    """Sec. 3.8 gives rational weights; the library runs on their FP64 values.
+    Round exact weights to nearest FP64 (Python's Fraction -> float rounds correctly)."""
     return [float(Fraction(v)) for v in c]
 
 
@@ -114,7 +116,8 @@ def _pshift(a):  # multiply by xi
 
 
 def gbs_stability_poly(n):
-    """P_n(xi): one GBS sequence with n steps of h = H/n on y' = lambda y, xi = H lambda.
+    """Stability polynomial (App. A.1) of one sequence of Sec. 2.1 eq. "GBS".
+    P_n(xi): one GBS sequence with n steps of h = H/n on y' = lambda y, xi = H lambda.
 
     With z = h lambda = xi/n: y_0 = 1, y_1 = y_0 + z y_0 (FE), y_(j+1) = y_(j-1) + 2 z y_j
     for j = 1..n (LF), P = (y_(n-1) + 2 y_n + y_(n+1)) / 4 (averaging).
@@ -138,7 +141,7 @@ def stability_poly(steps, c):
 
 
 def poly_eval(coeffs, x):
-    """Evaluate a coefficient list at x (Horner); x may be complex or Fraction."""
+    """Evaluate a coefficient list at x (Horner); x may be complex or Fraction (helper)."""
     acc = 0
     for a in reversed(coeffs):
         acc = acc * x + a
@@ -150,7 +153,8 @@ def poly_eval(coeffs, x):
 # ---------------------------------------------------------------------------
 
 def _abs2_minus_one(R):
-    """Coefficients in s = y^2 of |R(iy)|^2 - 1 (an even polynomial in y)."""
+    """Coefficients in s = y^2 of |R(iy)|^2 - 1 (an even polynomial in y); the ISB of
+    Sec. 2.2 is where it first turns positive for y > 0."""
     # R(iy) = sum a_k i^k y^k ; Re = sum_{k even} a_k (-1)^(k/2) y^k ; Im = sum_{k odd} a_k (-1)^((k-1)/2) y^k
     re = [Fraction(0)] * len(R)
     im = [Fraction(0)] * len(R)
