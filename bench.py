@@ -322,6 +322,8 @@ def run_gpu(args):
         sol.set_option("schedule", args.schedule)
     if args.tma != -1:
         sol.set_option("tma", args.tma)
+    if args.combine == "pairs":
+        sol.set_option("combine", 1)
     if not (args.hseg or args.tmax or args.schedule >= 0 or args.no_autotune):
         from paper_1907_11771_gb300 import autotune as AT
         r = AT.autotune(sol, y, H, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
@@ -402,7 +404,8 @@ def run_gpu(args):
         fused = sol_kernel_is_fused(sol, B)
         if tuned is not None:
             cfg["autotuned_schedule"] = tuned
-        cfg.update({"combine_dtype": ("f32 pairs (double-single, ~48-bit)" if fused else "f64"),
+        cfg.update({"combine_dtype": ("f32 pairs (double-single, ~48-bit)" if fused and args.combine == "pairs"
+                                      else "f64"),
                     "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
                     "parallelism": f"replicas x{ws}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -738,6 +741,8 @@ def main():
     ap.add_argument("--tmax", type=int, default=0, help="most leap-frog levels per time-blocked pass (0: default)")
     ap.add_argument("--schedule", type=int, default=-1, help="work-queue order of the time-blocked kernel (-1: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--combine", choices=["f64", "pairs"], default="f64",
+                    help="combine of the time-blocked FP32 path: FP64 (default) or compensated FP32 pairs")
     ap.add_argument("--tma", type=int, default=-1, choices=[-1, 0, 1],
                     help="tensor-copy staging of the plain step kernel: -1 default (3D), 1 always, 0 never")
     ap.add_argument("--no-autotune", action="store_true",

@@ -275,7 +275,12 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * copies where a tile's box lies inside the grid (identical results to the load
  * staging; a copy that does not complete latches GBS_ERR_TIMEOUT); 1 uses them
  * wherever they apply, -1 only in 3D (where they measured faster), 0 never;
- * gbs_get_option answers 1 only where those copies are in use.  gbs_get_option also
+ * gbs_get_option answers 1 only where those copies are in use.  "combine" = 0/1
+ * (default 0): how the time-blocked kernel's FP32-state path sums y_0 + sum_k c_k d*_k,
+ * 0 in FP64 (the averages promoted exactly, FP64 FMAs, one rounding to FP32), 1 in
+ * compensated FP32 pairs (error about 2^-48 of sum_k |c_k d*_k|, on the FP32 units;
+ * faster on GB300, whose FP64 rate is a small fraction of its FP32 rate); the plain
+ * kernels always sum in FP64.  gbs_get_option also
  * answers "kernel_in_use" (the GBS_KERNEL_* value gbs_step would run now).
  * Unknown names: GBS_ERR_INVALID.  No counterpart in the paper: these choose
  * how the macro-step is scheduled on the GPU, not what it computes. */
@@ -324,21 +329,30 @@ int64_t gbs_kernel_launches(gbs_handle h);
  * right-hand side, FP64 accumulator, 1/rho, problem tables) in one array of
  * GBS_NOALLOC_SCRATCH_BYTES compiled into the library as a __device__
  * variable, which every GPU that loads the library reserves until the process
- * exits.  It calls no cudaMalloc/cudaFree and uses no heap memory.
+ * exits.  It allocates no GPU memory: it calls no cudaMalloc/cudaFree and no
+ * allocating library routine (its host-side tables live on the stack; only the
+ * per-thread error message is thread-local storage).
  *  - Arguments as in gbs_create (pb, kappa, rho; pb->enable_adjoint must be 0,
  *    batch <= 256), gbs_set_weights (order_p .. c_free; all problems use this
  *    scheme) and gbs_step (y_in, y_out, H, n_macro); cuda_stream is a
- *    cudaStream_t.  The caller owns every pointer it passes.
+ *    cudaStream_t.  The caller owns every pointer it passes.  The weights are
+ *    solved and checked as gbs_set_weights does (GBS_ERR_ORDER when the rounded
+ *    weights break an order constraint, GBS_ERR_INVALID for a non-finite free
+ *    weight); kappa and rho are not checked for non-positive or non-finite
+ *    values (gbs_create does check them).
  *  - A problem whose scratch would exceed GBS_NOALLOC_SCRATCH_BYTES is
  *    rejected with GBS_ERR_INVALID; the message is returned by
  *    gbs_noalloc_last_error().
  *  - The first call on a device (with that device current) looks up the
- *    array's device address with cudaGetSymbolAddress; make that first call
- *    outside any stream capture.
+ *    array's device address with cudaGetSymbolAddress.
+ *  - The problem tables are copied into the array from pageable host memory:
+ *    each call returns only after the work queued earlier on cuda_stream has
+ *    finished, and no call may be made while cuda_stream is being captured
+ *    (GBS_ERR_STATE, returned before anything is enqueued).  The macro-steps
+ *    themselves run asynchronously on cuda_stream.
  *  - All calls on a device share the one array, which keeps the previous
  *    call's contents: calls whose GPU work overlaps (other streams or threads)
  *    race and must be serialised by the caller.
- *  - Asynchronous on cuda_stream, like gbs_step.
  * ------------------------------------------------------------------------- */
 #define GBS_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa, const void* rho, int order_p,

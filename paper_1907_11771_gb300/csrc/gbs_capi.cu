@@ -14,6 +14,7 @@
 
 #include "gbs_dd.h"
 #include "gbs_internal.h"
+#include "gbs_weights.h"
 
 using namespace gbs;
 
@@ -104,6 +105,8 @@ struct gbs_ctx {
   alignas(64) unsigned char lf_tmap[2][128] = {};
   int64_t opt_spin_limit = 1 << 20;
   int opt_inject_wait = 0;
+  int opt_combine = 0;                    // time-blocked FP32 path: 0 = FP64 combine, 1 = compensated
+                                          // FP32 pairs
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
   std::vector<double> tev_bytes;
   int tev_used = 0;
@@ -269,18 +272,6 @@ Sizes sizes_of(const gbs_problem* pb) {
 // ---------------------------------------------------------------------------
 
 // Dual Vandermonde system sum_i z_i x_i^j = r_j (j = 0..n) by Bjorck-Pereyra, in dd.
-void bjorck_pereyra_dual(const std::vector<dd>& x, std::vector<dd>& b) {
-  const int n = (int)x.size() - 1;
-  for (int k = 0; k < n; ++k)
-    for (int i = n; i > k; --i) b[i] = b[i] - x[k] * b[i - 1];
-  for (int k = n - 1; k >= 0; --k) {
-    for (int i = k + 1; i <= n; ++i) b[i] = b[i] / (x[i] - x[i - k - 1]);
-    for (int i = k; i < n; ++i) b[i] = b[i] - b[i + 1];
-  }
-}
-
-dd inv_sq(int n) { return dd_from(1.0) / dd_from(double(n) * double(n)); }
-
 // |R(iy)|^2 - 1 for the scheme; R = sum_k c_k P_k(iy), P_k from the GBS recurrence on y' = lambda y.
 double abs2_minus_one(const Slot& s, double y) {
   std::complex<double> R = 0;
@@ -725,46 +716,19 @@ gbs_status gbs_set_weights(gbs_handle h, int slot, int order_p, int n_dep, const
   s.order = order_p;
   s.m = m;
   for (int k = 0; k < m; ++k) s.steps[k] = steps[k];
+  char msg[200];
+  gbs_status wst;
   if (c_full) {
     for (int k = 0; k < m; ++k) {
       if (!std::isfinite(c_full[k])) return fail(h, GBS_ERR_INVALID, "weight %d is not finite", k);
       s.c[k] = c_full[k];
     }
+    wst = check_order_constraints(order_p, m, s.steps, s.c, msg, sizeof msg);
   } else {
-    // r_j = b_j - sum_free c_i h_i^(2j), then V_dep c_dep = r (Sec. 3.7), all in dd
-    const int q = n_dep;
-    std::vector<dd> x(q), r(q);
-    for (int i = 0; i < q; ++i) x[i] = inv_sq(steps[i]);
-    for (int j = 0; j < q; ++j) {
-      dd rj = dd_from(j == 0 ? 1.0 : 0.0);
-      for (int i = 0; i < n_free; ++i) {
-        if (!std::isfinite(c_free[i])) return fail(h, GBS_ERR_INVALID, "free weight %d is not finite", i);
-        dd pw = dd_from(1.0);
-        const dd hx = inv_sq(steps[n_dep + i]);
-        for (int e = 0; e < j; ++e) pw = pw * hx;
-        rj = rj - dd_from(c_free[i]) * pw;
-      }
-      r[j] = rj;
-    }
-    bjorck_pereyra_dual(x, r);
-    for (int i = 0; i < q; ++i) s.c[i] = r[i].hi + r[i].lo;
-    for (int i = 0; i < n_free; ++i) s.c[n_dep + i] = c_free[i];
+    // c_dep from c_free (Sec. 3.7) in dd, then the order constraints with the rounded weights
+    wst = scheme_weights(order_p, n_dep, n_free, s.steps, c_free, s.c, msg, sizeof msg);
   }
-  // order constraints with the rounded weights, in dd
-  for (int j = 0; j < order_p / 2; ++j) {
-    dd sum = dd_from(j == 0 ? -1.0 : 0.0);
-    double scale = 0.0;
-    for (int k = 0; k < m; ++k) {
-      dd pw = dd_from(1.0);
-      const dd hx = inv_sq(steps[k]);
-      for (int e = 0; e < j; ++e) pw = pw * hx;
-      sum = sum + dd_from(s.c[k]) * pw;
-      scale += std::fabs(s.c[k]) * (pw.hi + pw.lo);
-    }
-    const double res = std::fabs(sum.hi + sum.lo);
-    if (!(res <= 64.0 * 2.220446049250313e-16 * scale))
-      return fail(h, GBS_ERR_ORDER, "order constraint j=%d violated: residual %.3e > 64 ulp of %.3e", j, res, scale);
-  }
+  if (wst != GBS_OK) return fail(h, wst, "%s", msg);
   s.isb = scan_isb(s);
   s.set = true;
   h->slots[slot] = s;
@@ -1032,6 +996,10 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
   } else if (!std::strcmp(name, "tma")) {
     if (value < -1 || value > 1) return fail(h, GBS_ERR_INVALID, "tma must be -1, 0 or 1");
     h->opt_tma = (int)value;
+  } else if (!std::strcmp(name, "combine")) {
+    if (value != 0 && value != 1) return fail(h, GBS_ERR_INVALID, "combine must be 0 (FP64) or 1 (FP32 pairs)");
+    h->opt_combine = (int)value;
+    fused_set_combine(h->fw, value == 0);
   } else if (!std::strcmp(name, "time_kernels")) {
     if (value && h->tev.empty()) {
       const int pairs = 8192;
@@ -1061,6 +1029,7 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "tma")) *value = tma_in_use(h) ? 1 : 0;
   else if (!std::strcmp(name, "spin_limit")) *value = h->opt_spin_limit;
   else if (!std::strcmp(name, "inject_unsatisfiable_wait")) *value = h->opt_inject_wait;
+  else if (!std::strcmp(name, "combine")) *value = h->opt_combine;
   else if (!std::strcmp(name, "kernel_in_use")) {
     StepPlan p;
     gbs_status st = build_plan(h, &p);

@@ -2,9 +2,11 @@
 //
 // One macro-step (Sec. 2.1 eq. "GBS", Sec. 3.6, Sec. 3.2) runs as
 //   1. f0 = f(y_in)              point-parallel, shared by every sequence (Sec. 3.6); the same
-//                                kernel copies y_in next to f0 and interleaves the media
+//                                kernel interleaves the media (FP32 pairs: a prologue converts
+//                                y_in and the media and evaluates f0 in pairs)
 //   2. k_passes                  all Forward-Euler / leap-frog levels of all sequences
-//   3. k_combine                 y_out = sum_k c_k y*_k in compensated FP32 pairs
+//   3. k_combine                 y_out = sum_k c_k y*_k: in FP64 (FP32 states: y_0 + sum_k c_k d*_k,
+//                                the increment form), or in compensated FP32 pairs
 //
 // Work items.  Sequence k has the Forward-Euler level y_1 and N_k leap-frog
 // levels y_2 .. y_(N+1).  The leap-frog levels are cut into passes of T <= kTMax
@@ -85,7 +87,7 @@ struct Params {
   const SlotDev* slots;
   const double* hk;
   const float2* hkf;
-  const float2* kb;      // media as (kappa, b) pairs
+  const float4* aux;     // FP32: per point (kappa, b, f0_p, f0_u), written by the f0 kernel
   const float* init;     // [2][E]: y_0, f0
   float* lev;            // [seq][set][2][E]
   float* ystar;          // [seq][E]
@@ -121,6 +123,32 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+
+// Tensor memory (TMEM) as per-thread scratch for the FP32 sweep's forcing ring (below).  A CTA
+// allocates kTmemCols columns of the SM's 512 x 128-lane TMEM; warp w reaches only lanes
+// 32 (w mod 4) .. 32 (w mod 4) + 31, so warps w and w + 4 take different halves of the columns.
+// Thread t of a warp reads and writes its own lane with the 32x32b shape.  Two CTAs per SM use
+// 2 kTmemCols <= 512 columns, so an allocation never waits.
+constexpr int kTmemCols = 128;
+constexpr int kGSlots = 16;   // ring of forcing rows (power of two > R T)
+// No "memory" clobbers: these touch only tensor memory, and volatile asm statements keep their
+// order among themselves; a clobber would also pin every global and shared access around them.
+__device__ __forceinline__ void tmem_st4(uint32_t ta, float a, float b, float c, float d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta), "r"(__float_as_uint(a)),
+               "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)));
+}
+// Load four words of this thread's lane; the registers are valid only after tmem_wait_ld, which
+// takes them as read-write operands so that no use is scheduled before it.
+__device__ __forceinline__ void tmem_ld4(uint32_t ta, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(ta));
+}
+__device__ __forceinline__ float4 tmem_wait_ld(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b), "+r"(c), "+r"(d));
+  return make_float4(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c), __uint_as_float(d));
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 
 // Shared memory of one CTA (float2 words):
 //   level planes  [kTMax][U][kRow]        (p, u) of the newest U = 2R + 1 rows of levels 0..T-1,
@@ -180,8 +208,16 @@ __device__ __forceinline__ float2 ysum2(const float2 (&w)[2 * R + 1], int r) {
   return acc;
 }
 
+// The FP32 sweep runs in increment form (gbs_stencil.cuh): the levels hold d_n = y_n - y_0, the
+// first pass starts from (d_0, d_1) = (0, h f0), and every leap-frog update adds the forcing
+// g = 2h f0 of its row.  g is computed when level 0 reaches a row and kept for the T levels that
+// pass over it later, in a ring of kGSlots rows per thread in tensor memory (tbase: this
+// thread's lane and column base): row r's slot is r mod kGSlots, and a row is needed for R T <
+// kGSlots steps.  A slot written at step s is read from step s + R on; every R steps the sweep
+// waits for its tensor-memory stores to complete before its barrier, so each read sees them.
 template <int R, int T>
-__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float2* smem) {
+__device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float2* smem,
+                                         uint32_t tbase) {
   constexpr int U = 2 * R + 1;       // window rows = plane slots
   constexpr int OFF = 64 * U;        // keeps compile-time slot arithmetic non-negative
   const int tid = threadIdx.x;
@@ -196,12 +232,15 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
   const int x = wrapi(x0 - R * T + tid, nx);
   const float2 hf = P.hkf[it.prob * GBS_MAX_SEQ + it.seq];
-  const float h1 = hf.x;
+  const double hd = P.hk[it.prob * GBS_MAX_SEQ + it.seq];
+  float gh, gl;                                            // 2h as a float pair
+  split_h(2.0 * hd, gh, gl);
   const float mh = -hf.y * float(q.inv_dx[0]);            // -2h / dx
   const float rxy = float(q.inv_dx[1] / q.inv_dx[0]);      // y-stencil weight relative to x
-  const float2* kbm = P.kb + q.media_off;
-  // the two input levels (y_(n-1), y_n) -- (y_0, f0) for a first pass -- and the two output
-  // levels (or the average) are E apart
+  const float4* auxm = P.aux + q.media_off;               // (kappa, b, f0_p, f0_u) per point
+  const float* f0v = P.init + P.E + q.state_off + 2 * (int64_t)PPn;   // f0_v
+  // the two input levels (d_(n-1), d_n) are E apart (a first pass reads only f0: d_0 = 0,
+  // d_1 = h f0), and so are the two output levels (or the average)
   const float* inA = pd.first ? P.init + q.state_off
                               : P.lev + ((int64_t)(it.seq * 2 + ((it.pass - 1) & 1)) * 2) * P.E + q.state_off;
   float* outA = pd.last ? P.ystar + (int64_t)it.seq * P.E + q.state_off
@@ -225,27 +264,24 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   int e0 = wrapf(Y0 - R * T, ny) * nx + x;       // level 0's row at step 0
   int e1 = wrapf(Y0 - R * T - R, ny) * nx + x;   // level -1 at level 1's row at step 0
   int eo = (Y0 - 2 * R * T) * nx + x;            // level T's output row at step 0 (unwrapped)
-  // raw loads of the next step: level 0 (f0 in a first pass, whose level 0 is y_0 + h f0,
-  // combined at the commit so that no load is consumed in the step that issues it), y_0 at
-  // level 0's row (first pass only), level -1 at level 1's row, media
-  float n0p, n0u, n0v, y0p = 0.f, y0u = 0.f, y0v = 0.f, n1p, n1u, n1v;
-  float2 nm;
+  // raw loads of the next step (consumed at the next step's commit): the media and f0 at level
+  // 0's row (f0 gives the forcing, and in a first pass level 0 = h f0), and in later passes
+  // level 0 and level -1 (at level 1's row; in a first pass d_0 = 0)
+  float n0p = 0.f, n0u = 0.f, n0v = 0.f, nfv, n1p = 0.f, n1u = 0.f, n1v = 0.f;
+  float4 na;
   auto fetch = [&]() {
-    const float* a = inA + e1;
-    const float* b = inA + E + e0;
-    n0p = __ldcg(b);
-    n0u = __ldcg(b + PPn);
-    n0v = __ldcg(b + 2 * PPn);
-    if (pd.first) {
-      const float* y = inA + e0;
-      y0p = __ldcg(y);
-      y0u = __ldcg(y + PPn);
-      y0v = __ldcg(y + 2 * PPn);
+    na = __ldg(auxm + e0);
+    nfv = __ldg(f0v + e0);
+    if (!pd.first) {
+      const float* a = inA + e1;
+      const float* b = inA + E + e0;
+      n0p = __ldcg(b);
+      n0u = __ldcg(b + PPn);
+      n0v = __ldcg(b + 2 * PPn);
+      n1p = __ldcg(a);
+      n1u = __ldcg(a + PPn);
+      n1v = __ldcg(a + 2 * PPn);
     }
-    n1p = __ldcg(a);
-    n1u = __ldcg(a + PPn);
-    n1v = __ldcg(a + 2 * PPn);
-    nm = __ldg(kbm + e0);
   };
   // L2 prefetch of the rows the next block of U steps loads, so that the one-step-ahead
   // register loads find them in L2: warps 0-2 take level 0's fields, warps 3-5 level -1's (in a
@@ -256,7 +292,7 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int xf = wrapi(x0 - R * T, nx);   // column of thread 0
   auto prefetch_block = [&](int sn) {
     const int wq = tid >> 5;
-    if (wq > 5) return;   // warps 6 and 7 issue none
+    if (wq > 5 || pd.first) return;   // warps 6 and 7 issue none, nor any warp in a first pass
     const int row0 = wrapi(Y0 - R * T + sn - (wq >= 3 ? R : 0), ny);
     const float* base = wq < 3 ? inA + E + wq * PPn : inA + (wq - 3) * PPn;
     constexpr int kSamp = 9;   // columns 32 floats (one line) apart, plus the last one
@@ -275,14 +311,20 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
     for (int uu = 0; uu < U; ++uu) {
       const int s = sb + uu;
       if (s >= S) break;
-      // ---- level 0 (local row s - R T), level -1, media ----
+      // ---- level 0 (local row s - R T), its forcing, level -1, media ----
       const int r0 = (uu + OFF - R * T) % U;
       float p0 = n0p, u0 = n0u, v0 = n0v;
+      // the forcing g = 2h f0; in a first pass level 0 is d_1 = h f0 = g / 2
+      const float gp = mul_split(gh, gl, na.z);
+      const float gu = mul_split(gh, gl, na.w);
+      const float gv = mul_split(gh, gl, nfv);
+      const float2 nm = make_float2(na.x, na.y);
       if (pd.first) {
-        p0 = fmaf(h1, p0, y0p);
-        u0 = fmaf(h1, u0, y0u);
-        v0 = fmaf(h1, v0, y0v);
+        p0 = 0.5f * gp;
+        u0 = 0.5f * gu;
+        v0 = 0.5f * gv;
       }
+      tmem_st4(tbase + 4u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T) & (kGSlots - 1)), gp, gu, gv, 0.f);
       w[0][r0] = make_float2(p0, v0);
       lvl[r0 * kRow] = make_float2(p0, u0);
       med[r0 * kThreads] = __fmul2_rn(make_float2(mh, mh), nm);
@@ -302,6 +344,8 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
         const int r = (uu + OFF - R * T - R * t) % U;   // slot of this level's row
         const float2 km = med[(((t - 1) / 2) * U + r) * kThreads];
         if (t % 2 == 0 && t < T) med[((t / 2) * U + r) * kThreads] = km;
+        uint32_t g0, g1, g2, g3;   // this row's forcing, loaded while the stencil sums run
+        tmem_ld4(tbase + 4u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T - R * t) & (kGSlots - 1)), g0, g1, g2, g3);
         const float2 sxv = xsum2<R>(lvl + ((t - 1) * U + r) * kRow);   // (sum_x p, sum_x u)
         const float2 syv = ysum2<R>(w[t - 1], r);                       // (sum_y p, sum_y v)
         float2 ppv;
@@ -313,9 +357,10 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
           ppv = w[t - 2][r];
           pu = lvl[((t - 2) * U + r) * kRow].y;
         }
-        const float np = fmaf(km.x, fmaf(rxy, syv.y, sxv.y), ppv.x);
-        const float nu = fmaf(km.y, sxv.x, pu);
-        const float nv = fmaf(km.y * rxy, syv.x, ppv.y);
+        const float4 g = tmem_wait_ld(g0, g1, g2, g3);
+        const float np = fmaf(km.x, fmaf(rxy, syv.y, sxv.y), ppv.x + g.x);
+        const float nu = fmaf(km.y, sxv.x, pu + g.y);
+        const float nv = fmaf(km.y * rxy, syv.x, ppv.y + g.z);
         if (t < T) {
           w[t][r] = make_float2(np, nv);
           lvl[(t * U + r) * kRow] = make_float2(np, nu);
@@ -344,7 +389,10 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
         }
       }
       eo += nx;
-      if (uu % R == R - 1 || uu == U - 1) __syncthreads();
+      if (uu % R == R - 1 || uu == U - 1) {
+        tmem_wait_st();
+        __syncthreads();
+      }
     }
   }
 }
@@ -540,12 +588,28 @@ template <int R, bool X2>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P) {
   extern __shared__ float2 smem[];
   __shared__ int s_item;
+  __shared__ uint32_t s_tmem;
+  const int warp = threadIdx.x >> 5;
+  if constexpr (!X2) {
+    // the FP32 sweep's forcing ring lives in tensor memory (run_item)
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  const uint32_t tbase = X2 ? 0u : s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemCols / 2) * (warp >> 2);
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
     __syncthreads();
     const int i = s_item;
     __syncthreads();
-    if (i >= P.n_items) return;
+    if (i >= P.n_items) break;
     if (threadIdx.x < kMaxDeps) {
       const int d = P.deps[i * kMaxDeps + threadIdx.x];
       if (d >= 0) {
@@ -564,19 +628,26 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_passes(const Params P)
     const ProbDev& q = P.probs[it.prob];
     const PassDesc pd = P.pdesc[(q.slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
     if constexpr (X2) run_item_x2<R>(P, it, pd, reinterpret_cast<float4*>(smem));
-    else if (pd.T == 2) run_item<R, 2>(P, it, pd, smem);
+    else if (pd.T == 2) run_item<R, 2>(P, it, pd, smem, tbase);
 #if GBS_FUSED_TMAX >= 6
-    else if (pd.T == 6) run_item<R, 6>(P, it, pd, smem);
+    else if (pd.T == 6) run_item<R, 6>(P, it, pd, smem, tbase);
 #endif
 #if GBS_FUSED_TMAX >= 8
-    else if (pd.T == 8) run_item<R, 8>(P, it, pd, smem);
+    else if (pd.T == 8) run_item<R, 8>(P, it, pd, smem, tbase);
 #endif
-    else run_item<R, 4>(P, it, pd, smem);
+    else run_item<R, 4>(P, it, pd, smem, tbase);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       st_release(P.done + i, 1);
     }
+  }
+  if constexpr (!X2) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -590,45 +661,91 @@ __device__ __forceinline__ int problem_of(const ProbDev* probs, int batch, int64
   return lo;
 }
 
-// y_out = sum_k c_k y*_k (per problem, its slot's weights), accumulated in FP32 pairs
-// (pair_combine_add: error about 2^-48 of sum_k |c_k y*_k|, FP64-class, on FP32 units only;
-// GB300 runs FP64 at a small fraction of the FP32 rate and a plain FP64 sum of 11 terms per
-// element would saturate that pipe).  Four consecutive elements per thread: the loads of all
-// sequences are issued before the sums (float4 when the group is 16-byte aligned and inside
-// one problem, else element by element).
+// Exact FP32 -> FP64 promotion on the integer pipe, bit for bit the hardware conversion (all 2^32
+// inputs checked on the host): a normal float's sign, exponent (re-biased by 1023 - 127 = 896)
+// and 23 mantissa bits placed into the double's fields; infinities and NaNs keep exponent 2047
+// and their payload; a subnormal m 2^-149 is normalised (its leading bit found by clz); zero
+// keeps its sign.  GB300's conversion instruction shares the slow FP64 pipe with the combine's
+// FMAs, so a converted operand per FMA would double that pipe's work.
+__device__ __forceinline__ double promote(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu, ex = mag >> 23;
+  unsigned hi = sign | ((mag >> 3) + (ex == 0xffu ? (1792u << 20) : (896u << 20)));
+  unsigned lo = b << 29;
+  if (ex == 0u) {
+    const int sh = __clz(mag) - 8;                     // mag << sh has bit 23 set (mag != 0)
+    const unsigned fr = (mag << sh) & 0x7fffffu;
+    hi = mag ? (sign | ((897u - (unsigned)sh) << 20) | (fr >> 3)) : sign;
+    lo = mag ? (fr << 29) : 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// y_out = y_0 + sum_k c_k d*_k (per problem, its slot's weights): the increment form's combine
+// (y*_k = y_0 + d*_k, sum_k c_k = 1; Sec. 2.1, Sec. 3.2), in ascending k.  kF64: the averages and
+// y_0 are promoted to FP64 exactly and summed with FP64 FMAs, rounded to FP32 once (GB300's FP64
+// pipe makes this the costlier variant); otherwise the sum runs in compensated FP32 pairs
+// (pair_combine_add, error about 2^-48 of sum_k |c_k d*_k|, FP32 units only).  Four consecutive
+// elements per thread: the loads of all sequences are issued before the sums (float4 when the
+// group is 16-byte aligned and inside one problem, else element by element).  y_0 may be y_out
+// (in place): each element is read before it is written by the same thread.
+template <bool kF64>
 __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch, const SlotDev* slots,
-                                                 const float* __restrict__ ystar, int64_t E,
-                                                 float* __restrict__ y_out) {
+                                                 const float* __restrict__ dstar, int64_t E, const float* y0,
+                                                 float* y_out) {
   const int64_t groups = (E + 3) / 4;
-  // float4 access needs E % 4 == 0 (sequence blocks and y_out groups 16-byte aligned; ystar is
-  // a library allocation) and a 16-byte aligned caller buffer
-  const bool vec = (E % 4) == 0 && (reinterpret_cast<uintptr_t>(y_out) & 15) == 0;
+  // float4 access needs E % 4 == 0 (sequence blocks and y groups 16-byte aligned; dstar is a
+  // library allocation) and 16-byte aligned caller buffers
+  const bool vec = (E % 4) == 0 && ((reinterpret_cast<uintptr_t>(y_out) | reinterpret_cast<uintptr_t>(y0)) & 15) == 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e0 = 4 * g;
     const int q0 = problem_of(probs, batch, e0);
     const int64_t e3 = e0 + 3 < E ? e0 + 3 : E - 1;
     if (vec && (q0 + 1 >= batch || probs[q0 + 1].state_off > e3)) {
       const SlotDev& s = slots[probs[q0].slot];
-      float4 y[GBS_MAX_SEQ];
+      float4 d[GBS_MAX_SEQ];
 #pragma unroll
       for (int k = 0; k < GBS_MAX_SEQ; ++k)
-        if (k < s.m) y[k] = __ldcs(reinterpret_cast<const float4*>(ystar + (int64_t)k * E + e0));
-      float4 sh = make_float4(0.f, 0.f, 0.f, 0.f), sl = sh;
+        if (k < s.m) d[k] = __ldcs(reinterpret_cast<const float4*>(dstar + (int64_t)k * E + e0));
+      const float4 yv = *reinterpret_cast<const float4*>(y0 + e0);
+      float4 out;
+      if constexpr (kF64) {
+        double a0 = promote(yv.x), a1 = promote(yv.y), a2 = promote(yv.z), a3 = promote(yv.w);
 #pragma unroll
-      for (int k = 0; k < GBS_MAX_SEQ; ++k)
-        if (k < s.m) {
-          pair_combine_add(s.chi[k], s.clo[k], y[k].x, sh.x, sl.x);
-          pair_combine_add(s.chi[k], s.clo[k], y[k].y, sh.y, sl.y);
-          pair_combine_add(s.chi[k], s.clo[k], y[k].z, sh.z, sl.z);
-          pair_combine_add(s.chi[k], s.clo[k], y[k].w, sh.w, sl.w);
-        }
-      *reinterpret_cast<float4*>(y_out + e0) = make_float4(sh.x + sl.x, sh.y + sl.y, sh.z + sl.z, sh.w + sl.w);
+        for (int k = 0; k < GBS_MAX_SEQ; ++k)
+          if (k < s.m) {
+            const double c = s.c[k];
+            a0 = fma(c, promote(d[k].x), a0);
+            a1 = fma(c, promote(d[k].y), a1);
+            a2 = fma(c, promote(d[k].z), a2);
+            a3 = fma(c, promote(d[k].w), a3);
+          }
+        out = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+      } else {
+        float4 sh = yv, sl = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < GBS_MAX_SEQ; ++k)
+          if (k < s.m) {
+            pair_combine_add(s.chi[k], s.clo[k], d[k].x, sh.x, sl.x);
+            pair_combine_add(s.chi[k], s.clo[k], d[k].y, sh.y, sl.y);
+            pair_combine_add(s.chi[k], s.clo[k], d[k].z, sh.z, sl.z);
+            pair_combine_add(s.chi[k], s.clo[k], d[k].w, sh.w, sl.w);
+          }
+        out = make_float4(sh.x + sl.x, sh.y + sl.y, sh.z + sl.z, sh.w + sl.w);
+      }
+      *reinterpret_cast<float4*>(y_out + e0) = out;
     } else {
       for (int64_t e = e0; e <= e3; ++e) {
         const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
-        float sh = 0.f, sl = 0.f;
-        for (int k = 0; k < s.m; ++k) pair_combine_add(s.chi[k], s.clo[k], __ldcs(ystar + (int64_t)k * E + e), sh, sl);
-        y_out[e] = sh + sl;
+        if constexpr (kF64) {
+          double a = promote(y0[e]);
+          for (int k = 0; k < s.m; ++k) a = fma(s.c[k], promote(__ldcs(dstar + (int64_t)k * E + e)), a);
+          y_out[e] = (float)a;
+        } else {
+          float sh = y0[e], sl = 0.f;
+          for (int k = 0; k < s.m; ++k) pair_combine_add(s.chi[k], s.clo[k], __ldcs(dstar + (int64_t)k * E + e), sh, sl);
+          y_out[e] = sh + sl;
+        }
       }
     }
   }
@@ -675,15 +792,16 @@ struct FusedWork {
   float* lev = nullptr;
   float* ystar = nullptr;
   float* init = nullptr;   // [2][E]: copy of y_0, f0 (written by the f0 kernel)
-  float2* kb = nullptr;    // media as (kappa, b) pairs (written by the f0 kernel)
+  float4* aux = nullptr;   // FP32: (kappa, b, f0_p, f0_u) per point (written by the f0 kernel)
   fused::Item* items = nullptr;
   int* deps = nullptr;
   int* done = nullptr;   // n_items flags followed by the queue counter
   fused::PassDesc* pdesc = nullptr;
   fused::TileGeo* tgeo = nullptr;
-  size_t lev_cap = 0, ystar_cap = 0, items_cap = 0, init_cap = 0, kb_cap = 0;
+  size_t lev_cap = 0, ystar_cap = 0, items_cap = 0, init_cap = 0, aux_cap = 0;
   bool x2 = false;        // GBS_F32X2: levels, averages and inputs as FP32 pairs
   double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
+  int combine_f64 = 1;    // FP32 states: combine in FP64 (1) or in compensated FP32 pairs (0)
   long long spin_limit = fused::kSpinLimit;
   int inject_wait = 0;    // test hook: item 0 also waits on a flag that nothing sets
 };
@@ -691,12 +809,12 @@ struct FusedWork {
 namespace {
 
 void free_work(FusedWork* w) {
-  void* ptrs[] = {w->lev, w->ystar, w->init, w->kb, w->items, w->deps, w->done, w->pdesc, w->tgeo};
+  void* ptrs[] = {w->lev, w->ystar, w->init, w->aux, w->items, w->deps, w->done, w->pdesc, w->tgeo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w->lev = w->ystar = w->init = nullptr;
-  w->kb = nullptr;
-  w->init_cap = w->kb_cap = 0;
+  w->aux = nullptr;
+  w->init_cap = w->aux_cap = 0;
   w->items = nullptr;
   w->deps = w->done = nullptr;
   w->pdesc = nullptr;
@@ -740,6 +858,8 @@ bool fused_supported(const StepPlan& p, const ProbDev* probs_h) {
 FusedWork* fused_create() { return new FusedWork(); }
 
 int fused_max_levels() { return fused::kTMax; }
+
+void fused_set_combine(FusedWork* w, int f64) { w->combine_f64 = f64 != 0; }
 
 void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait) {
   w->spin_limit = spin_limit;
@@ -868,12 +988,12 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   const size_t lev_bytes = (size_t)4 * p.max_m * p.state_elems * esz;
   const size_t ys_bytes = (size_t)p.max_m * p.state_elems * esz;
   const size_t init_bytes = (size_t)2 * p.state_elems * esz;
-  const size_t kb_bytes =
-      (size_t)(probs_h[p.batch - 1].media_off + probs_h[p.batch - 1].pts) * sizeof(float2);
+  const size_t aux_bytes =
+      (size_t)(probs_h[p.batch - 1].media_off + probs_h[p.batch - 1].pts) * sizeof(float4);
   if (grow(&w->lev, &w->lev_cap, lev_bytes) || grow(&w->ystar, &w->ystar_cap, ys_bytes) ||
-      grow(&w->init, &w->init_cap, init_bytes) || grow(&w->kb, &w->kb_cap, kb_bytes)) {
+      grow(&w->init, &w->init_cap, init_bytes) || (!w->x2 && grow(&w->aux, &w->aux_cap, aux_bytes))) {
     std::snprintf(msg, msglen, "cudaMalloc of the fused level store (%zu bytes) failed",
-                  lev_bytes + ys_bytes + init_bytes + kb_bytes);
+                  lev_bytes + ys_bytes + init_bytes + aux_bytes);
     return -2;
   }
   if (w->items) cudaFree(w->items);
@@ -904,8 +1024,10 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
     return -3;
   }
   w->n_items = n;
-  // algorithmic bytes per launch: every item reads its two input levels (y_0 and f0 for a
-  // first pass) and the two media over its tile once and writes two levels (one average)
+  // algorithmic bytes per launch: every item reads the two media over its tile once and its two
+  // input levels, and writes two levels (one average); FP32 states in increment form also read
+  // f0 (a first pass reads only the media and f0: its input levels are 0 and h f0), FP32 pairs
+  // read (y_0, f0) in a first pass
   {
     double by = 0;
     for (int i = 0; i < n; ++i) {
@@ -916,7 +1038,8 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
       const double pts = (double)(((sx + 1) * nx) / g.nst - (sx * nx) / g.nst) *
                          (((sy + 1) * ny) / g.nseg - (sy * ny) / g.nseg);
       const PassDesc& d = pdesc[((size_t)probs_h[it.prob].slot * GBS_MAX_SEQ + it.seq) * kMaxPasses + it.pass];
-      by += pts * (double)esz * (2.0 * p.F + 2.0 + (d.last ? 1.0 : 2.0) * p.F);
+      const double rd = w->x2 ? 2.0 * p.F + 2.0 : (d.first ? 0.0 : 2.0 * p.F) + p.F + 2.0;
+      by += pts * (double)esz * (rd + (d.last ? 1.0 : 2.0) * p.F);
     }
     w->alg_bytes = by;
   }
@@ -929,12 +1052,29 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   };
+  // The occupancy calculator answers 1 CTA per SM for any kernel that allocates tensor memory
+  // (it cannot know how many columns), so for the FP32 sweep the residency is derived from its
+  // registers and shared memory instead: kMinBlocks CTAs of kTmemCols columns each fit the
+  // SM's 512 columns, and a tensor-memory CTA is co-resident with another once it has
+  // relinquished its allocation right (k_passes does so right after allocating).
+  auto residency = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes fa;
+    int regs_sm = 0, smem_sm = 0, smem_res = 0;
+    cudaFuncGetAttributes(&fa, kern);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int by_regs = regs_sm / std::max(1, ((fa.numRegs + 7) / 8) * 8 * kThreads);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + smem_res);
+    per_sm = std::min({kMinBlocks, by_regs, by_smem, 512 / kTmemCols});
+  };
   if (w->x2) {
     if (p.R == 2) occupancy(k_passes<2, true>);
     else occupancy(k_passes<3, true>);
   } else {
-    if (p.R == 2) occupancy(k_passes<2, false>);
-    else occupancy(k_passes<3, false>);
+    if (p.R == 2) residency(k_passes<2, false>);
+    else residency(k_passes<3, false>);
   }
   if (cudaGetLastError() != cudaSuccess || per_sm < 1) {
     std::snprintf(msg, msglen, "the fused kernel cannot be resident (smem %zu bytes)", smem);
@@ -956,8 +1096,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
     // f0 goes next to a copy of y_0, and the media are interleaved for the passes
     StepPlan pf = p;
     pf.f0 = w->init + w->E;
-    pf.f0_ycopy = w->init;
-    pf.f0_kb = w->kb;
+    pf.f0_aux = w->aux;      // increment form: y_0 is read only by the combine, from y_in
     if (launch_f0(pf, y_in, s) < 0) return -1;
     ++launches;
   }
@@ -973,7 +1112,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.slots = p.slots;
   P.hk = p.hk;
   P.hkf = p.hkf;
-  P.kb = w->kb;
+  P.aux = w->aux;
   P.init = w->init;
   P.lev = w->lev;
   P.ystar = w->ystar;
@@ -997,8 +1136,12 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   if (w->x2)
     k_combine_x2<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, reinterpret_cast<const float2*>(w->ystar), w->E,
                                       static_cast<double*>(y_out));
+  else if (w->combine_f64)
+    k_combine<true><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
+                                         static_cast<float*>(y_out));
   else
-    k_combine<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<float*>(y_out));
+    k_combine<false><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
+                                          static_cast<float*>(y_out));
   ++launches;
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return launches;

@@ -65,10 +65,10 @@ struct StepPlan {
   void* L0;                    // leap-frog level buffers, F x P each
   void* L1;
   double* acc;                 // FP64 combine accumulator, F x P
-  // optional extra outputs of the f0 kernel (FP32 acoustics, time-blocked path): a copy of
-  // y_in and the media as interleaved (kappa, b) pairs
-  float* f0_ycopy;
-  float2* f0_kb;
+  // optional output of the f0 kernel (FP32 2D acoustics, time-blocked path): per point
+  // (kappa, b, f0_p, f0_u) interleaved, f0_v in the f0 buffer's third field (its first two
+  // fields are then not written)
+  float4* f0_aux;
   // GBS_F32X2 workspace: y_in, kappa and b converted to FP32 pairs at the start of a step
   void* ds_y0;
   void* ds_kappa;
@@ -156,6 +156,8 @@ FusedWork* fused_create();
 // spin_limit: polls before a dependency wait gives up (GBS_ERR_TIMEOUT); inject_wait: test
 // hook making the first item wait on a flag that nothing sets (takes effect at prepare).
 void fused_set_test_hooks(FusedWork* w, long long spin_limit, int inject_wait);
+// FP32 states: sum the combine in FP64 (f64 = 1, the default) or in compensated FP32 pairs (0).
+void fused_set_combine(FusedWork* w, int f64);
 void fused_destroy(FusedWork* w);
 bool fused_supported(const StepPlan& p, const ProbDev* probs_h);
 // Tunable shape of the time-blocked schedule: row-segment height of a tile, the most leap-frog

@@ -15,11 +15,16 @@
 // exits.  Host code cannot use the name of the array as a device address (in
 // host code it names a host-side shadow), so the device address is looked up
 // with cudaGetSymbolAddress once per device, on the first call made while that
-// device is current.  That first call therefore must not happen during stream
-// capture.  All calls on a device share the one array: calls whose GPU work
-// overlaps in time (different streams, or different host threads) race on it.
-// The array keeps whatever the previous call left in it; nothing in it needs
-// to start at zero because every buffer is fully written before it is read.
+// device is current.  The small problem tables are copied into the array from
+// pageable host memory, so every call waits until the work queued earlier on
+// its stream has finished before it returns, and no call may be made while
+// its stream is being captured (such a call is refused with GBS_ERR_STATE
+// before anything is enqueued).  All calls on a device share the one array:
+// calls whose GPU work overlaps in time (different streams, or different host
+// threads) race on it.  The array keeps whatever the previous call left in it;
+// nothing in it needs to start at zero because every buffer is fully written
+// before it is read.  kappa and rho are used as given: unlike gbs_create, this
+// entry point does not check them for non-positive or non-finite values.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,8 +32,8 @@
 #include <cstring>
 #include <mutex>
 
-#include "gbs_dd.h"
 #include "gbs_internal.h"
+#include "gbs_weights.h"
 
 namespace {
 
@@ -66,8 +71,6 @@ gbs_status scratch_address(void** out) {
   *out = g_noalloc_ptr[dev];
   return GBS_OK;
 }
-
-gbs::dd inv_sq_n(int n) { return gbs::dd_from(1.0) / gbs::dd_from(double(n) * double(n)); }
 
 }  // namespace
 
@@ -123,30 +126,11 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
     slot.steps[k] = N;
   }
   {
-    dd x[GBS_MAX_SEQ], r[GBS_MAX_SEQ];
-    const int q = n_dep;
-    for (int i = 0; i < q; ++i) x[i] = inv_sq_n(slot.steps[i]);
-    for (int j = 0; j < q; ++j) {
-      dd rj = dd_from(j == 0 ? 1.0 : 0.0);
-      for (int i = 0; i < n_free; ++i) {
-        dd pw = dd_from(1.0);
-        const dd hx = inv_sq_n(slot.steps[n_dep + i]);
-        for (int e = 0; e < j; ++e) pw = pw * hx;
-        rj = rj - dd_from(c_free[i]) * pw;
-      }
-      r[j] = rj;
-    }
-    const int n = q - 1;  // dual Vandermonde solve, in place in r
-    for (int k = 0; k < n; ++k)
-      for (int i = n; i > k; --i) r[i] = r[i] - x[k] * r[i - 1];
-    for (int k = n - 1; k >= 0; --k) {
-      for (int i = k + 1; i <= n; ++i) r[i] = r[i] / (x[i] - x[i - k - 1]);
-      for (int i = k; i < n; ++i) r[i] = r[i] - r[i + 1];
-    }
-    for (int i = 0; i < q; ++i) slot.c[i] = r[i].hi + r[i].lo;
-    for (int i = 0; i < n_free; ++i) slot.c[n_dep + i] = c_free[i];
-    for (int k = 0; k < m; ++k)
-      if (!std::isfinite(slot.c[k])) return noalloc_fail(GBS_ERR_ORDER, "weights are not finite");
+    // c_dep from c_free in double-double and the order constraints with the rounded weights,
+    // exactly as gbs_set_weights does (Sec. 3.7)
+    char msg[200];
+    const gbs_status wst = scheme_weights(order_p, n_dep, n_free, slot.steps, c_free, slot.c, msg, sizeof msg);
+    if (wst != GBS_OK) return noalloc_fail(wst, msg);
     split_weights(slot);
   }
   // ---- layout inside the scratch array ----
@@ -159,7 +143,8 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
       const int64_t n = pb->shape[3 * p + k];
       if (k < pb->ndim) {
         if (n < R || n > (int64_t(1) << 30)) return noalloc_fail(GBS_ERR_INVALID, "grid size out of range");
-        if (!(pb->dx[3 * p + k] > 0)) return noalloc_fail(GBS_ERR_INVALID, "dx must be > 0");
+        if (!(pb->dx[3 * p + k] > 0) || !std::isfinite(pb->dx[3 * p + k]))
+          return noalloc_fail(GBS_ERR_INVALID, "dx must be finite and > 0");
         d.inv_dx[k] = 1.0 / pb->dx[3 * p + k];
       } else if (n != 1) {
         return noalloc_fail(GBS_ERR_INVALID, "unused dimensions must have size 1");
@@ -198,14 +183,26 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const char* a = static_cast<const char*>(y_in);
   const char* b = static_cast<const char*>(y_out);
   if (a != b && a < b + bytes && b < a + bytes) return noalloc_fail(GBS_ERR_INVALID, "y_in and y_out overlap partially");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the tables below are uploaded from pageable host memory, which a stream capture cannot
+    // record: refuse before anything is enqueued, so the caller's capture stays valid
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: cudaStreamIsCapturing failed");
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return noalloc_fail(GBS_ERR_STATE, "gbs_step_noalloc must not be called while its stream is being captured");
+  }
   void* base = nullptr;
   gbs_status st = scratch_address(&base);
   if (st != GBS_OK) return st;
   char* sc = static_cast<char*>(base);
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // host staging of the per-problem step tables: automatic arrays (about 66 KB of stack)
   double Hs[256];
-  static thread_local double hk[256 * GBS_MAX_SEQ];
-  static thread_local float2 hkf[256 * GBS_MAX_SEQ];
+  double hk[256 * GBS_MAX_SEQ];
+  float2 hkf[256 * GBS_MAX_SEQ];
   for (int p = 0; p < pb->batch; ++p) {
     Hs[p] = H;
     for (int k = 0; k < GBS_MAX_SEQ; ++k) {

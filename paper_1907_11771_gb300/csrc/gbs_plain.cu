@@ -116,16 +116,15 @@ __global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* _
   T f[kMaxFields];
   rhs_point<T, SYS, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx, kap, bb, f);
   T* f0 = static_cast<T*>(p.f0) + q.state_off;
+  if constexpr (SYS == SYS_ACOUSTIC && DIM == 2 && std::is_same<T, float>::value) {
+    if (p.f0_aux) {
+      p.f0_aux[q.media_off + L.i] = make_float4(kap, bb, f[0], f[1]);
+      f0[2 * q.pts + L.i] = f[2];
+      return;
+    }
+  }
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) f0[fl * q.pts + L.i] = f[fl];
-  if constexpr (SYS == SYS_ACOUSTIC && std::is_same<T, float>::value) {
-    if (p.f0_ycopy) {
-      float* yc = p.f0_ycopy + q.state_off;
-#pragma unroll
-      for (int fl = 0; fl < F; ++fl) yc[fl * q.pts + L.i] = float(y_in[q.state_off + fl * q.pts + L.i]);
-    }
-    if (p.f0_kb) p.f0_kb[q.media_off + L.i] = make_float2(float(kap), float(bb));
-  }
 }
 
 template <typename T, int SYS, int DIM>
@@ -141,10 +140,21 @@ __global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* _
   const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
   T* L1 = static_cast<T*>(p.L1) + q.state_off;
   const T* y0 = y_in + q.state_off;
+  if constexpr (std::is_same<T, float>::value) {
+    // increment form: d_1 = h f0 (y_0 is added back by the combine)
+    float hh, hl;
+    split_h(p.hk[L.prob * GBS_MAX_SEQ + k], hh, hl);
 #pragma unroll
-  for (int fl = 0; fl < F; ++fl) {
-    const int64_t e = fl * q.pts + L.i;
-    L1[e] = y0[e] + h * f0[e];
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * q.pts + L.i;
+      L1[e] = mul_split(hh, hl, f0[e]);
+    }
+  } else {
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) {
+      const int64_t e = fl * q.pts + L.i;
+      L1[e] = y0[e] + h * f0[e];
+    }
   }
 }
 
@@ -176,11 +186,23 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   }
   T f[kMaxFields];
   rhs_point<T, SYS, DIM, R>(cur, q.pts, g, inv_dx, kap, bb, f);
+  // FP32: increment form, d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n with d_0 = 0
+  constexpr bool kInc = std::is_same<T, float>::value;
+  float gh = 0.f, gl = 0.f;
+  if constexpr (kInc) split_h(2.0 * p.hk[L.prob * GBS_MAX_SEQ + k], gh, gl);
+  const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
+  T pv[kMaxFields];
+#pragma unroll
+  for (int fl = 0; fl < F; ++fl) {
+    const int64_t e = fl * q.pts + L.i;
+    if constexpr (kInc) pv[fl] = (n == 1 ? T(0) : prev[e]) + mul_split(gh, gl, f0[e]);
+    else pv[fl] = prev[e];
+  }
   if (n < N) {
 #pragma unroll
     for (int fl = 0; fl < F; ++fl) {
       const int64_t e = fl * q.pts + L.i;
-      dst[e] = prev[e] + h2 * f[fl];
+      dst[e] = pv[fl] + h2 * f[fl];
     }
     return;
   }
@@ -193,10 +215,10 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
 #pragma unroll
   for (int fl = 0; fl < F; ++fl) {
     const int64_t e = fl * q.pts + L.i;
-    const T ym = prev[e];
+    const T ym = kInc && n == 1 ? T(0) : prev[e];
     const T y0 = cur[e];
-    const T yp = ym + h2 * f[fl];
-    combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(ym, y0, yp), yo);
+    const T yp = pv[fl] + h2 * f[fl];
+    combine_last(acc, e, first, last, c, gragg_avg(ym, y0, yp), yo, kInc && first ? y_in[q.state_off + e] : T(0));
   }
 }
 
@@ -266,7 +288,7 @@ struct Vec16<dsf> {
 // its neighbours: FP32 2D 6, FP32 3D 5; 8-byte states 3 in 2D and 2 in 3D
 template <typename T, int DIM, int R>
 constexpr int lf_min_blocks() {
-  return sizeof(T) == 4 ? (DIM == 2 ? 6 : 5) : (DIM == 2 ? 3 : 2);
+  return sizeof(T) == 4 ? (DIM == 2 ? 5 : 4) : (DIM == 2 ? 3 : 2);
 }
 
 // TMA staging helpers (inline PTX): shared-window address, mbarrier, 4D tensor copy
@@ -332,15 +354,25 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     dzp[j - 1] = (zp - z) * nx * ny;
     dzm[j - 1] = (zm - z) * nx * ny;
   }
-  // point-wise operands of a row (previous level, media, and in 3D the z-neighbours of p and
-  // w), loaded one row ahead of their use; the first row's before the tile barrier
-  T nprev[F], nkv = T(0), nbv = T(0), nzp[R][2], nzm[R][2];
+  // FP32: increment form (gbs_stencil.cuh), d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n, d_0 = 0
+  constexpr bool kInc = std::is_same<T, float>::value;
+  const T* f0v = static_cast<const T*>(p.f0) + q.state_off;
+  float gh = 0.f, gl = 0.f;
+  if constexpr (kInc) split_h(2.0 * p.hk[lo * GBS_MAX_SEQ + k], gh, gl);
+  const bool prev_zero = kInc && n == 1;
+  // point-wise operands of a row (previous level, media, f0 in the increment form, and in 3D
+  // the z-neighbours of p and w), loaded one row ahead of their use; the first row's before the
+  // tile barrier
+  T nprev[F], nf0[F], nkv = T(0), nbv = T(0), nzp[R][2], nzm[R][2];
   auto fetch_row = [&](int i) {
     const int y = y0 + threadIdx.y + 8 * i;
     if (x >= nx || y >= ny) return;
     const Off o = o0 + (Off)(8 * i) * nx;
 #pragma unroll
-    for (int fl = 0; fl < F; ++fl) nprev[fl] = DIM == 3 ? (prev + fl * P)[o] : prev[fl * P + o];
+    for (int fl = 0; fl < F; ++fl) {
+      nprev[fl] = prev_zero ? T(0) : DIM == 3 ? (prev + fl * P)[o] : prev[fl * P + o];
+      if constexpr (kInc) nf0[fl] = DIM == 3 ? ldg(f0v + fl * P + o) : ldg(f0v + (fl * P + o));
+    }
     nkv = ldg(kap + o);
     nbv = ldg(bmed + o);
     if (DIM == 3) {
@@ -472,9 +504,13 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     const int ly = threadIdx.y + 8 * i;
     const int y = y0 + ly;
     if (y >= ny) break;
-    T pv[F], zpv[R][2], zmv[R][2];
+    T pv[F], pg[F], zpv[R][2], zmv[R][2];
 #pragma unroll
-    for (int fl = 0; fl < F; ++fl) pv[fl] = nprev[fl];
+    for (int fl = 0; fl < F; ++fl) {
+      pv[fl] = nprev[fl];
+      if constexpr (kInc) pg[fl] = pv[fl] + mul_split(gh, gl, nf0[fl]);
+      else pg[fl] = pv[fl];
+    }
     const T kv = nkv, bv = nbv;
     if (DIM == 3) {
 #pragma unroll
@@ -517,8 +553,8 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     if (n < N) {
 #pragma unroll
       for (int fl = 0; fl < F; ++fl) {
-        if (DIM == 3) (dst + fl * P)[o] = pv[fl] + h2 * f[fl];
-        else dst[fl * P + o] = pv[fl] + h2 * f[fl];
+        if (DIM == 3) (dst + fl * P)[o] = pg[fl] + h2 * f[fl];
+        else dst[fl * P + o] = pg[fl] + h2 * f[fl];
       }
     } else {
       double* acc = p.acc + q.state_off;
@@ -527,8 +563,9 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       for (int fl = 0; fl < F; ++fl) {
         const int64_t e = fl * P + o;
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
-        const T yp = pv[fl] + h2 * f[fl];
-        combine_last(acc, e, first, last, c, s.chi[k], s.clo[k], gragg_avg(pv[fl], yc, yp), yo);
+        const T yp = pg[fl] + h2 * f[fl];
+        combine_last(acc, e, first, last, c, gragg_avg(pv[fl], yc, yp), yo,
+                     kInc && first ? y_in[q.state_off + e] : T(0));
       }
     }
   }
@@ -1464,8 +1501,7 @@ int ds_prologue(const StepPlan& p, const void* y_in, void* y_pairs, void* f0_pai
   q.kappa = p.ds_kappa;
   q.b = p.ds_b;
   q.f0 = f0_pairs;
-  q.f0_ycopy = nullptr;
-  q.f0_kb = nullptr;
+  q.f0_aux = nullptr;
   return f0_sys<dsf>(q, y_pairs, s) < 0 ? -1 : 4;
 }
 

@@ -63,29 +63,41 @@ __device__ __forceinline__ void pair_combine_add(float c_hi, float c_lo, float y
   sl = __fsub_rn(sl, __fsub_rn(sh, t));
 }
 
-// The combine of the plain path's last leap-frog step of sequence k: y_out (+)= c_k y*_k.  FP32
-// states accumulate in FP32 pairs held in the accumulator's 8-byte slots; FP64 (and FP32-pair)
-// states in FP64.
+// FP32 states are advanced in increment form: every sequence carries d_n = y_n - y_0 instead of
+// y_n, with f(y_n) = f0 + A d_n (f is linear), so
+//   d_0 = 0,  d_1 = h f0,  d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n,  d* = (d_(N-1) + 2 d_N + d_(N+1)) / 4
+// and y(t + H) = y_0 + sum_k c_k d*_k (sum_k c_k = 1).  This is the same linear map as Sec. 2.1
+// eq. "GBS"; in FP32 each rounding is then relative to |d| rather than |y|, and the combine's
+// large alternating weights amplify those roundings, so the increment form lowers the FP32
+// error several-fold (a textbook device for extrapolation methods).  The FP64 and FP32-pair
+// paths keep the plain form.
+//
+// h = hi + lo: a double split into two floats (the FP32 kernels' step sizes).
+__host__ __device__ __forceinline__ void split_h(double h, float& hi, float& lo) {
+  hi = (float)h;
+  lo = (float)(h - (double)hi);
+}
+// fl(h f) for h = hi + lo: TwoProd of hi f by one FMA plus lo f, so the result is within about
+// one ulp of the exact product; a step size rounded to FP32 would instead scale every point of
+// a sequence by the same wrong factor, an error that adds up coherently over macro-steps.
+__device__ __forceinline__ float mul_split(float hi, float lo, float f) {
+  const float p = __fmul_rn(hi, f);
+  const float e = fmaf(hi, f, -p);
+  return __fadd_rn(p, fmaf(lo, f, e));
+}
+
+// The combine of the plain path's last leap-frog step of sequence k: y_out (+)= c_k y*_k in FP64.
+// FP32 states are in increment form (y*_k = y_0 + d*_k): the first sequence starts the
+// accumulator at y_0, each adds c_k d*_k (d*_k promoted exactly), the last rounds once to FP32.
 template <typename T, typename O>
-__device__ __forceinline__ void combine_last(double* acc, int64_t e, bool first, bool last, double c, float chi,
-                                             float clo, T ystar, O* yo) {
-  if constexpr (sizeof(T) == 4 && sizeof(O) == 4) {
-    float2* a = reinterpret_cast<float2*>(acc);
-    float sh = 0.f, sl = 0.f;
-    if (!first) {
-      const float2 v = a[e];
-      sh = v.x;
-      sl = v.y;
-    }
-    pair_combine_add(chi, clo, (float)ystar, sh, sl);
-    if (last) yo[e] = O(sh + sl);
-    else a[e] = make_float2(sh, sl);
-  } else {
-    const double ys = (double)ystar;
-    const double a2 = first ? c * ys : fma(c, ys, acc[e]);
-    if (last) yo[e] = static_cast<O>(a2);
-    else acc[e] = a2;
-  }
+__device__ __forceinline__ void combine_last(double* acc, int64_t e, bool first, bool last, double c, T ystar,
+                                             O* yo, T y0 = T(0)) {
+  const double ys = (double)ystar;
+  double a2;
+  if constexpr (sizeof(T) == 4 && sizeof(O) == 4) a2 = fma(c, ys, first ? (double)y0 : acc[e]);
+  else a2 = first ? c * ys : fma(c, ys, acc[e]);
+  if (last) yo[e] = static_cast<O>(a2);
+  else acc[e] = a2;
 }
 
 // Geometry of one point inside one problem.
