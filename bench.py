@@ -38,7 +38,8 @@ N_GAUSS = 16
 H_FRACTION = 0.8
 
 
-PREC_DESC = {0: "FP32 state + FP64 combine", 1: "FP64", 2: "FP64 states in FP32-pair arithmetic + FP64 combine"}
+PREC_DESC = {0: "FP32 state (increment form) + FP64 combine", 1: "FP64",
+             2: "FP64 states in FP32-pair arithmetic + FP64 combine"}
 
 
 def workload_desc(n=N_GRID, prec=0):
@@ -46,14 +47,32 @@ def workload_desc(n=N_GRID, prec=0):
             f"{PREC_DESC[prec]}, H = {H_FRACTION} x stability limit")
 
 
-# DRAM bytes (read + write) of one time-blocked pass-kernel launch per schedule (hseg, tmax,
-# schedule), from the ncu captures in profiles/k_passes_2d2048.md (2D 2048^2, FP32).  They
-# describe that kernel build only: empty this table when the kernel changes until re-measured.
+# The time-blocked kernel's sources: DRAM traffic measured by ncu belongs to one build of them.
+FUSED_SOURCES = ("paper_1907_11771_gb300/csrc/gbs_fused.cu", "paper_1907_11771_gb300/csrc/gbs_stencil.cuh",
+                 "paper_1907_11771_gb300/csrc/gbs_ds.cuh", "paper_1907_11771_gb300/csrc/gbs_internal.h")
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the time-blocked pass
+# kernel on the 2D 2048^2 FP32 workload, from one ncu capture per schedule (hseg, tmax, schedule),
+# keyed by the hash of FUSED_SOURCES they were measured on: another build reports no traffic.
 PASSES_2D2048_TRAFFIC = {
-    (256, 4, 0): 4.765e9 + 3.059e9, (192, 4, 0): 4.997e9 + 3.056e9, (128, 4, 0): 5.325e9 + 3.054e9,
-    (384, 4, 0): 4.605e9 + 3.068e9, (96, 4, 0): 5.829e9 + 3.055e9, (192, 4, 1): 4.515e9 + 3.056e9,
-    (256, 4, 1): 4.006e9 + 3.059e9,
+    ("3a2d734c42b7", 256, 4, 0): 5.108961792e9 + 3.074189824e9,
+    ("3a2d734c42b7", 192, 4, 1): 5.513983488e9 + 3.074993408e9,
+    ("3a2d734c42b7", 192, 4, 0): 5.220551680e9 + 3.077555200e9,
 }
+
+# Algorithmic minimum bytes per grid point per macro-step (FP32 states): the method must read
+# y_in and the two media and write y_out once, (F + 2 + F) x 4 bytes; 2D F = 3, 3D F = 4.
+ALG_MIN_BYTES_PER_POINT = {2: 32.0, 3: 40.0}
+
+
+def fused_source_hash():
+    """First 12 hex digits of the SHA-256 of the time-blocked kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in FUSED_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def peaks():
@@ -66,7 +85,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 25 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -83,7 +102,7 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -192,12 +211,38 @@ def pick_oracle_side(budget_s):
     return max(128, min(N_GRID, s))
 
 
-def cpu_baseline(budget_s=20.0):
+def _oracle_worker(side):
+    return oracle_macro_step_timing(side)
+
+
+def cpu_baseline(budget_s=15.0):
+    """The FP64 oracle on the host: one process (one core), and one process per core running
+    the same macro-step concurrently (the oracle is single-threaded numpy; its processes are
+    started with spawn, after the GPU work)."""
+    import multiprocessing as mp
     side = pick_oracle_side(budget_s)
     dt, upd = oracle_macro_step_timing(side)
-    return {"value": upd / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 macro-step of GBS_8,6 on a {side}x{side} grid of the same recipe "
-                      f"({upd} updates, {dt:.1f} s, numpy FP64, single-threaded)"}
+    single = {"value": upd / dt / 1e9, "cores": 1, "seconds": dt}
+    cores = os.cpu_count() or 1
+    side_all = pick_oracle_side(budget_s / 2)     # memory bandwidth is shared by the processes
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [side_all] * cores)
+        wall = time.perf_counter() - t0
+        all_cores = {"value": sum(u for _, u in res) / wall / 1e9, "cores": cores, "seconds": wall,
+                     "side": side_all}
+    except Exception as e:  # no process pool on this host: report the single-core figure only
+        all_cores = {"value": None, "cores": cores, "error": str(e)[:200]}
+    best = all_cores if all_cores.get("value") else single
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle",
+            "sample": (f"1 macro-step of GBS_8,6 on a {side_all}x{side_all} grid of the same recipe in each of "
+                       f"{cores} concurrent processes (numpy FP64, one core each; wall time incl. process start)"
+                       if best is all_cores else
+                       f"1 macro-step of GBS_8,6 on a {side}x{side} grid of the same recipe (numpy FP64)"),
+            "single_core": {"value": single["value"], "unit": UNIT, "cores": 1,
+                            "sample": f"1 macro-step on {side}x{side} ({upd} updates, {dt:.1f} s)"},
+            "all_cores": all_cores}
 
 
 def run_reference(args):
@@ -254,6 +299,8 @@ def make_workload(args, rank):
         shapes, sch = [(n, n)], S.GBS_8_6
         order = FD_ORDER
         desc = workload_desc(n, prec)
+        if prec == F32 and args.combine == "pairs":
+            desc = desc.replace("FP64 combine", "compensated FP32-pair combine")
         slots = None
     elif wl == "3d":
         n = args.grid if args.grid != N_GRID else 512
@@ -289,7 +336,8 @@ def make_workload(args, rank):
     Hs = [H_FRACTION * h for h in sol.stability_limit()]
     y = torch.tensor(np.asarray(y0).ravel(), dtype=tdt, device="cuda")
     cfg = {"workload": desc, "shapes": shapes if len(shapes) < 4 else f"{len(shapes)} problems",
-           "scheme": sch.name, "updates_per_step_per_gpu": upd}
+           "scheme": sch.name, "updates_per_step_per_gpu": upd,
+           "updates_per_point": upd / sum(int(np.prod(s)) for s in shapes), "shape_zyx": list(shapes[0])}
     return sol, y, (Hs if len(Hs) > 1 else Hs[0]), upd, cfg
 
 
@@ -343,6 +391,8 @@ def run_gpu(args):
     barrier()
     l0 = sol.kernel_launches
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # the clock sampler runs over the timed region and the kernel-timing pass after it (the same
+    # macro-steps again), so that short timed regions still get several samples under load
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         barrier()
@@ -353,32 +403,67 @@ def run_gpu(args):
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
-    launches = sol.kernel_launches - l0
+        launches = sol.kernel_launches - l0
+
+        # dominant-kernel roofline: CUDA events recorded by the library around each launch
+        sol.set_option("time_kernels", 1)
+        sol.kernel_time()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            sol.step(y, y, H, 1)
+        nl, kms, kbytes = sol.kernel_time()
+        sol.set_option("time_kernels", 0)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms_max = max_over_ranks(ms, ws, "cuda")
     value = whole_job_rate(ws, upd_per_step * args.steps, ms_max / 1e3)
 
-    # dominant-kernel roofline: CUDA events recorded by the library around each launch
-    sol.set_option("time_kernels", 1)
-    sol.kernel_time()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        sol.step(y, y, H, 1)
-    nl, kms, kbytes = sol.kernel_time()
-    sol.set_option("time_kernels", 0)
+    # the opt-in variant of the time-blocked FP32 path: the combine in compensated FP32 pairs
+    variant = None
+    if sol_kernel_is_fused(sol, B) and not (args.f64 or args.f32x2) and args.combine == "f64":
+        sol.set_option("combine", 1)
+        for _ in range(args.warmup):
+            sol.step(y, y, H, 1)
+        torch.cuda.synchronize()
+        barrier()
+        vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            vev[i][0].record(stream)
+            sol.step(y, y, H, 1)
+            vev[i][1].record(stream)
+        torch.cuda.synchronize()
+        vms = max_over_ranks(sum(a.elapsed_time(b) for a, b in vev), ws, "cuda")
+        sol.set_option("combine", 0)
+        variant = {"combine_dtype": "f32 pairs (compensated, about 2^-48 of sum_k |c_k d*_k|)",
+                   "value": whole_job_rate(ws, upd_per_step * args.steps, vms / 1e3), "unit": UNIT,
+                   "ms_per_step": vms / args.steps}
     peak, peak_kind = peaks()
-    achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
-    traffic = None
-    if (args.workload == "2d" and args.grid == N_GRID and not (args.f64 or args.f32x2)
-            and sol_kernel_is_fused(sol, B)):
-        traffic = PASSES_2D2048_TRAFFIC.get(tuple(sol.get_option(k) for k in ("hseg", "tmax", "schedule")))
+    fused = sol_kernel_is_fused(sol, B)
+    launch_s = kms / nl / 1e3 if nl else None
+    # one launch of the time-blocked kernel is a whole macro-step; the one-level kernel runs one
+    # leap-frog level of one sequence, nl / steps launches per macro-step
+    pts = upd_per_step / cfg["updates_per_point"]
+    per_launch_share = args.steps / nl if nl else 0.0
+    esz = 8 if (args.f64 or args.f32x2) else 4
+    alg_min = ALG_MIN_BYTES_PER_POINT[len(cfg["shape_zyx"])] * esz / 4 * pts * per_launch_share
+    sched_bytes = kbytes / nl if nl else None
+    achieved = alg_min / launch_s / 1e9 if nl else None
+    traffic, traffic_key = None, None
+    if args.workload == "2d" and args.grid == N_GRID and not (args.f64 or args.f32x2) and fused:
+        traffic_key = (fused_source_hash(),) + tuple(int(sol.get_option(k)) for k in ("hseg", "tmax", "schedule"))
+        traffic = PASSES_2D2048_TRAFFIC.get(traffic_key)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "traffic_source": "profiles/k_passes_2d2048.md (ncu, same kernel build and schedule)" if traffic else None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "kernel": "fused pass" if sol_kernel_is_fused(sol, B) else "tiled leap-frog step (k_lf_tiled)",
-            "algorithmic_bytes_per_launch": kbytes / nl if nl else None,
-            "avg_launch_ms": kms / nl if nl else None}
+            "kernel": "fused pass (k_passes)" if fused else "tiled leap-frog step (k_lf_tiled)",
+            "avg_launch_ms": launch_s * 1e3 if nl else None,
+            "achieved_basis": "algorithmic minimum: y_in, kappa, rho read and y_out written once per macro-step "
+                              f"({ALG_MIN_BYTES_PER_POINT[len(cfg['shape_zyx'])] * esz / 4:.0f} B per grid point)",
+            "algorithmic_min_bytes_per_launch": alg_min,
+            "schedule_bytes_per_launch": sched_bytes,
+            "frac_sched": sched_bytes / launch_s / 1e9 / peak if nl else None,
+            "frac_dram": traffic / launch_s / 1e9 / peak if (traffic and nl) else None,
+            "traffic_key": list(traffic_key) if traffic_key else None}
 
     # end to end through the C ABI with host buffers: every step copies its input state from
     # pinned host memory, runs one macro-step and copies its result back (gbs_step_host_stream:
@@ -414,6 +499,11 @@ def run_gpu(args):
                 "dtype": "f64" if args.f64 else "f32x2" if args.f32x2 else "f32",
                 "data": "synthetic", "config": cfg,
                 "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "e2e": e2e}
+        if variant is not None:
+            line["variant_pair_combine"] = variant
+        if ws == 1 and not args.no_tts and args.workload == "2d" and not (args.f64 or args.f32x2):
+            sol.close()
+            line["time_to_1e6"] = time_to_solution(args, levels=2, compact=True)
         if ws == 1 and not args.no_cpu_baseline and args.workload == "2d" and not (args.f64 or args.f32x2):
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -626,11 +716,17 @@ def run_oneway(args):
 
 
 def run_time_to_solution(args):
+    print(json.dumps(time_to_solution(args, args.tts_levels)), flush=True)
+    return 0
+
+
+def time_to_solution(args, levels, compact=False):
     """Time to a relative L2 error of 1e-6 at t = M0 H0 (2D acoustics, same recipe on an
     n x n grid): the fused FP32-state path, the plain FP64 path, and FP64 states in FP32-pair
     arithmetic on the plain and the fused (time-blocked) kernels, each swept over
-    H = H0 / 2^j (H0 = 0.8 x the GBS_8,6 stability limit), against an FP64 GBS_12,8
-    reference run at a quarter of its own 0.8 x limit and checked against one at an eighth."""
+    H = H0 / 2^j, j < levels (H0 = 0.8 x the GBS_8,6 stability limit), against an FP64 GBS_12,8
+    reference run at a quarter of its own 0.8 x limit and checked against one at an eighth.
+    compact: per path only the fastest time that reaches 1e-6 and the smallest error reached."""
     import numpy as np
     import torch
 
@@ -640,7 +736,6 @@ def run_time_to_solution(args):
     from paper_1907_11771_gb300 import schemes as S
     from paper_1907_11771_gb300.solver import GBSSolver
 
-    torch.cuda.set_device(0)
     Bld.build()
     n, M0 = args.tts_grid, args.tts_macro
     y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, SIGMA * n / N_GRID)
@@ -684,7 +779,7 @@ def run_time_to_solution(args):
     rel = lambda a: (f64.norms(a, ref)[0] / f64.norms(ref)[0]) ** 0.5
     ref_err = rel(ref2)
     rows = {}
-    paths = [("fused FP32 state + FP64-class combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
+    paths = [("fused FP32 state + FP64 combine", B.GBS_F32_STATE_F64_COMBINE, B.GBS_KERNEL_FUSED, torch.float32),
              ("plain FP64", B.GBS_F64, B.GBS_KERNEL_PLAIN, torch.float64),
              ("plain FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_PLAIN, torch.float64),
              ("fused FP32 pairs (FP64 states)", B.GBS_F32X2, B.GBS_KERNEL_FUSED, torch.float64)]
@@ -698,19 +793,25 @@ def run_time_to_solution(args):
             if r is not None:
                 tuned[name] = r["options"]
         rows[name] = []
-        for j in range(args.tts_levels):
+        for j in range(levels):
             M = M0 * 2 ** j
             out, secs = run(sol, T / M, M, dt)
             rows[name].append({"H_over_H0": 2.0 ** -j, "macro_steps": M, "seconds": secs, "rel_l2": rel(out),
                                "gpt_updates_per_s": scheme.updates_per_point * n * n * M / secs / 1e9})
         sol.close()
+    f64.close()
+    ref_sol.close()
     best = {k: min((r["seconds"] for r in v if r["rel_l2"] <= 1e-6), default=None) for k, v in rows.items()}
-    print(json.dumps({"study": "time to relative L2 error 1e-6", "grid": [n, n], "scheme": scheme.name,
-                      "t_final": T, "H0": T / M0,
-                      "macro_steps_at_H0": M0, "reference": f"GBS_12,8 FP64, {Mref} macro-steps",
-                      "reference_self_check_rel_l2": ref_err, "paths": rows, "time_to_1e-6_s": best,
-                      "autotuned_schedule": tuned}), flush=True)
-    return 0
+    out = {"study": "time to relative L2 error 1e-6", "grid": [n, n], "scheme": scheme.name,
+           "t_final": T, "H0": T / M0,
+           "macro_steps_at_H0": M0, "reference": f"GBS_12,8 FP64, {Mref} macro-steps",
+           "reference_self_check_rel_l2": ref_err, "time_to_1e-6_s": best, "autotuned_schedule": tuned}
+    if compact:
+        out["smallest_rel_l2"] = {k: min(r["rel_l2"] for r in v) for k, v in rows.items()}
+        out["H_over_H0_swept"] = [2.0 ** -j for j in range(levels)]
+    else:
+        out["paths"] = rows
+    return out
 
 
 def sol_kernel_is_fused(sol, B):
@@ -749,6 +850,8 @@ def main():
                     help="keep the default time-blocked schedule instead of autotuning it first")
     ap.add_argument("--time-to-solution", action="store_true",
                     help="run the time-to-1e-6 study (fused FP32 vs plain FP64) instead of the throughput bench")
+    ap.add_argument("--no-tts", action="store_true",
+                    help="leave the time-to-1e-6 race (1024^2, two step sizes) out of the default line")
     ap.add_argument("--tts-grid", type=int, default=1024)
     ap.add_argument("--tts-macro", type=int, default=100)
     ap.add_argument("--tts-levels", type=int, default=3)

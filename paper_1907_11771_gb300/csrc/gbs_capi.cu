@@ -62,9 +62,11 @@ struct gbs_ctx {
   double* d_H = nullptr;
   double* d_hk = nullptr;                 // per problem x GBS_MAX_SEQ: H / N_k
   float2* d_hkf = nullptr;                // the same as FP32 (h_k, 2 h_k)
+  float4* d_hkq = nullptr;                // FP32 kernels' split step constants (fp32_step_consts)
   std::vector<double> cur_H;
   std::vector<double> hk_host;
   std::vector<float2> hkf_host;
+  std::vector<float4> hkq_host;
   int* d_err = nullptr;
   double* d_red = nullptr;                // norm partials (4 * kNormBlocks) + 4 results
   double* d_cmax = nullptr;
@@ -233,7 +235,7 @@ void free_graphs(gbs_ctx* h) {
 
 void free_all(gbs_ctx* h) {
   free_graphs(h);
-  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
+  void* ptrs[] = {h->b, h->d_probs, h->d_slots, h->d_H, h->d_hk, h->d_hkf, h->d_hkq, h->d_err, h->d_red, h->d_cmax, h->f0, h->L0, h->L1,
                   h->acc, h->stage, h->stage2, h->levels, h->mu0, h->mu1, h->mu_shared, h->ds_y0, h->ds_kappa,
                   h->ds_b, h->gpair};
   for (void* p : ptrs)
@@ -322,17 +324,21 @@ gbs_status upload_hk(gbs_ctx* h) {
   if ((int)h->cur_H.size() != h->batch) return GBS_OK;
   h->hk_host.assign((size_t)h->batch * GBS_MAX_SEQ, 0.0);
   h->hkf_host.assign((size_t)h->batch * GBS_MAX_SEQ, make_float2(0.f, 0.f));
+  h->hkq_host.assign((size_t)h->batch * GBS_MAX_SEQ, make_float4(0.f, 0.f, 0.f, 0.f));
   for (int p = 0; p < h->batch; ++p) {
     const Slot& s = h->slots[h->slot_of[p]];
     for (int k = 0; k < s.m; ++k) {
       const double hk = h->cur_H[p] / s.steps[k];
       h->hk_host[(size_t)p * GBS_MAX_SEQ + k] = hk;
       h->hkf_host[(size_t)p * GBS_MAX_SEQ + k] = make_float2((float)hk, (float)(2.0 * hk));
+      h->hkq_host[(size_t)p * GBS_MAX_SEQ + k] = fp32_step_consts(h->probs[p], hk, h->R);
     }
   }
   CK(h, cudaMemcpyAsync(h->d_hk, h->hk_host.data(), sizeof(double) * h->hk_host.size(), cudaMemcpyHostToDevice,
                         h->stream));
   CK(h, cudaMemcpyAsync(h->d_hkf, h->hkf_host.data(), sizeof(float2) * h->hkf_host.size(), cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaMemcpyAsync(h->d_hkq, h->hkq_host.data(), sizeof(float4) * h->hkq_host.size(), cudaMemcpyHostToDevice,
                         h->stream));
   return GBS_OK;
 }
@@ -383,6 +389,7 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->H = h->d_H;
   p->hk = h->d_hk;
   p->hkf = h->d_hkf;
+  p->hkq = h->d_hkq;
   p->total_blocks = h->total_blocks;
   p->total_tiles = h->total_tiles;
   p->state_elems = h->state_elems;
@@ -580,6 +587,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
       q.n[d] = (int)pb->shape[3 * p + d];
       q.inv_dx[d] = d < h->ndim ? 1.0 / pb->dx[3 * p + d] : 0.0;
     }
+    fill_fp32_consts(q, h->ndim, h->R);
     q.pts = (int64_t)q.n[0] * q.n[1] * q.n[2];
     q.state_off = soff;
     q.media_off = moff;
@@ -608,6 +616,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
   if ((st = dalloc(h, &h->d_H, sizeof(double) * h->batch)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_hk, sizeof(double) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_hkf, sizeof(float2) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
+  if ((st = dalloc(h, &h->d_hkq, sizeof(float4) * h->batch * GBS_MAX_SEQ)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_err, 64)) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_red, sizeof(double) * (4 * kNormBlocks + 4))) != GBS_OK) return bail(st);
   if ((st = dalloc(h, &h->d_cmax, sizeof(double) * h->batch)) != GBS_OK) return bail(st);

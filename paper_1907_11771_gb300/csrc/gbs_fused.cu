@@ -87,6 +87,7 @@ struct Params {
   const SlotDev* slots;
   const double* hk;
   const float2* hkf;
+  const float4* hkq;     // FP32: split step constants per problem x sequence (fp32_step_consts)
   const float4* aux;     // FP32: per point (kappa, b, f0_p, f0_u), written by the f0 kernel
   const float* init;     // [2][E]: y_0, f0
   float* lev;            // [seq][set][2][E]
@@ -129,51 +130,52 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // 32 (w mod 4) .. 32 (w mod 4) + 31, so warps w and w + 4 take different halves of the columns.
 // Thread t of a warp reads and writes its own lane with the 32x32b shape.  Two CTAs per SM use
 // 2 kTmemCols <= 512 columns, so an allocation never waits.
-constexpr int kTmemCols = 128;
-constexpr int kGSlots = 16;   // ring of forcing rows (power of two > R T)
+constexpr int kTmemCols = 256;
+constexpr int kGSlots = 16;   // ring of per-row constants (power of two > R T), 8 words per row
 // No "memory" clobbers: these touch only tensor memory, and volatile asm statements keep their
 // order among themselves; a clobber would also pin every global and shared access around them.
-__device__ __forceinline__ void tmem_st4(uint32_t ta, float a, float b, float c, float d) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta), "r"(__float_as_uint(a)),
-               "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)));
+// A load's registers are valid only after tmem_wait_ld8, which takes them as read-write operands
+// so that no use is scheduled before it.
+__device__ __forceinline__ void tmem_st8(uint32_t ta, float a, float b, float c, float d, float e, float f, float g,
+                                         float h) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta),
+               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+               "r"(__float_as_uint(e)), "r"(__float_as_uint(f)), "r"(__float_as_uint(g)), "r"(__float_as_uint(h)));
 }
-// Load four words of this thread's lane; the registers are valid only after tmem_wait_ld, which
-// takes them as read-write operands so that no use is scheduled before it.
-__device__ __forceinline__ void tmem_ld4(uint32_t ta, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+struct Row8 {
+  uint32_t v[8];
+};
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, Row8& r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]),
+                 "=r"(r.v[7])
                : "r"(ta));
 }
-__device__ __forceinline__ float4 tmem_wait_ld(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b), "+r"(c), "+r"(d));
-  return make_float4(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c), __uint_as_float(d));
+__device__ __forceinline__ void tmem_wait_ld8(Row8& r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r.v[0]), "+r"(r.v[1]), "+r"(r.v[2]), "+r"(r.v[3]), "+r"(r.v[4]), "+r"(r.v[5]), "+r"(r.v[6]),
+                 "+r"(r.v[7]));
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 
 // Shared memory of one CTA (float2 words):
 //   level planes  [kTMax][U][kRow]        (p, u) of the newest U = 2R + 1 rows of levels 0..T-1,
 //                                          rows padded by kPad so every x-stencil stays inside
-//   media planes  [(kTMax+1)/2][U][kThreads]  the scaled media (-2h kappa/dx, -2h b/dx) of the
-//                                          rows being worked on; plane g serves levels 2g+1, 2g+2
+//   (FP32 pairs also:) media planes [U][kThreads] of float4, the scaled media of a pass's rows
 // A row's slot is its local row index mod U, a compile-time constant in a sweep unrolled by U,
 // so no ring index is computed at run time.  A level-t row is read by the x-stencils of level
 // t+1 R steps after it is written and by its own thread (the leap-frog "previous" u) 2R steps
 // after; it is overwritten U = 2R+1 steps after.  A barrier at least every R steps therefore
-// orders both the read after the write and the overwrite after the read.  Media are only read
-// by their own thread, so they need no barrier: level 2g copies the media of its row into
-// plane g, where levels 2g+1 and 2g+2 find them R and 2R steps later (the media of a row are
-// needed R T steps after they are loaded, longer than one plane keeps a row).
+// orders both the read after the write and the overwrite after the read.  The FP32 sweep keeps
+// the per-row constants (scaled media, forcing) in tensor memory instead (run_item).
 constexpr int kPad = 4;
 constexpr int kRow = kThreads + 2 * kPad;
 
-__host__ __device__ constexpr int media_planes() { return (kTMax + 1) / 2; }
-
-// finite-difference weights c_1..c_R as (c, c) pairs for the packed sums (orders 4 and 6)
-__constant__ float2 c_fd4[2] = {{2.f / 3.f, 2.f / 3.f}, {-1.f / 12.f, -1.f / 12.f}};
-__constant__ float2 c_fd6[3] = {{0.75f, 0.75f}, {-0.15f, -0.15f}, {1.f / 60.f, 1.f / 60.f}};
-
+// finite-difference weights as integers m_j over a common divisor (fd_int / fd_div: 8, -1 over 12;
+// 45, -9, 1 over 60), as (m, m) pairs for the packed sums; exact in FP32, the divisor is folded
+// into the per-row scaling
 template <int R>
-__device__ __forceinline__ float2 fdc(int j) { return R == 2 ? c_fd4[j - 1] : c_fd6[j - 1]; }
+__device__ __forceinline__ float2 fdc(int j) { return make_float2(fd_int<R>(j), fd_int<R>(j)); }
 
 // packed FP32 pairs (Blackwell f32x2 instructions): a - b, c * d + e, c * d
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
@@ -188,7 +190,7 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
   return d;
 }
 
-// x-derivative sums of (p, u) over a level-plane row, unscaled: sum_j c_j (row[+j] - row[-j]),
+// x-derivative sums of (p, u) over a level-plane row, unscaled: sum_j m_j (row[+j] - row[-j]),
 // the difference taken first (exact for smooth fields) and weighted in pairs
 template <int R>
 __device__ __forceinline__ float2 xsum2(const float2* row) {
@@ -210,11 +212,16 @@ __device__ __forceinline__ float2 ysum2(const float2 (&w)[2 * R + 1], int r) {
 
 // The FP32 sweep runs in increment form (gbs_stencil.cuh): the levels hold d_n = y_n - y_0, the
 // first pass starts from (d_0, d_1) = (0, h f0), and every leap-frog update adds the forcing
-// g = 2h f0 of its row.  g is computed when level 0 reaches a row and kept for the T levels that
-// pass over it later, in a ring of kGSlots rows per thread in tensor memory (tbase: this
-// thread's lane and column base): row r's slot is r mod kGSlots, and a row is needed for R T <
-// kGSlots steps.  A slot written at step s is read from step s + R on; every R steps the sweep
-// waits for its tensor-memory stores to complete before its barrier, so each read sees them.
+// g = 2h f0 of its row.  The stencil sums use integer weights; their divisor, 1 / dx and -2h
+// form one constant s2, and the scaled media s2 kappa and s2 b are kept as float pairs (hi +
+// lo, about 2^-48 relative), so that no rounding of the scaling is shared by the points and
+// steps of a sequence (that would perturb its operator coherently, which the combine's weights
+// and the modes near the stability limit amplify).  When level 0 reaches a row it computes the
+// row's eight constants (s2 kappa and s2 b as pairs, g), which the T levels that pass over the
+// row later read from a ring of kGSlots rows per thread in tensor memory (tbase: this thread's
+// lane and column base): row r's slot is r mod kGSlots, and a row is needed for R T < kGSlots
+// steps.  A slot written at step s is read from step s + R on; every R steps the sweep waits
+// for its tensor-memory stores to complete before its barrier, so each read sees them.
 template <int R, int T>
 __device__ __forceinline__ void run_item(const Params& P, const Item& it, const PassDesc& pd, float2* smem,
                                          uint32_t tbase) {
@@ -231,12 +238,10 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int Y0 = (sy * ny) / tg.nseg;
   const int hs = ((sy + 1) * ny) / tg.nseg - Y0;
   const int x = wrapi(x0 - R * T + tid, nx);
-  const float2 hf = P.hkf[it.prob * GBS_MAX_SEQ + it.seq];
-  const double hd = P.hk[it.prob * GBS_MAX_SEQ + it.seq];
-  float gh, gl;                                            // 2h as a float pair
-  split_h(2.0 * hd, gh, gl);
-  const float mh = -hf.y * float(q.inv_dx[0]);            // -2h / dx
-  const float rxy = float(q.inv_dx[1] / q.inv_dx[0]);      // y-stencil weight relative to x
+  const float4 hq = P.hkq[it.prob * GBS_MAX_SEQ + it.seq];
+  const float gh = hq.x, gl = hq.y;                        // 2h as a float pair
+  const float sh2 = -hq.z, sl2 = -hq.w;                    // s2 = -2h / (div dx) as a float pair
+  const float rxy = q.rr[1];                               // y-stencil weight relative to x (dx / dy)
   const float4* auxm = P.aux + q.media_off;               // (kappa, b, f0_p, f0_u) per point
   const float* f0v = P.init + P.E + q.state_off + 2 * (int64_t)PPn;   // f0_v
   // the two input levels (d_(n-1), d_n) are E apart (a first pass reads only f0: d_0 = 0,
@@ -248,7 +253,6 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
   const int64_t E = P.E;
   const bool out_col = tid >= R * T && tid < R * T + wout;
   float2* const lvl = smem + kPad + tid;                                  // plane t, slot r: lvl[(t U + r) kRow]
-  float2* const med = smem + kTMax * U * kRow + tid;                      // plane g, slot r: med[(g U + r) kThreads]
 
   // (p, v) windows of levels 0..T-1.  Level t computes local row s - R T - R t at sweep step
   // s.  Rows before a level's first valid row (s < 2 R t) are computed from not-yet-valid
@@ -311,23 +315,27 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
     for (int uu = 0; uu < U; ++uu) {
       const int s = sb + uu;
       if (s >= S) break;
-      // ---- level 0 (local row s - R T), its forcing, level -1, media ----
+      // ---- level 0 (local row s - R T), the row's constants, level -1 ----
       const int r0 = (uu + OFF - R * T) % U;
       float p0 = n0p, u0 = n0u, v0 = n0v;
       // the forcing g = 2h f0; in a first pass level 0 is d_1 = h f0 = g / 2
       const float gp = mul_split(gh, gl, na.z);
       const float gu = mul_split(gh, gl, na.w);
       const float gv = mul_split(gh, gl, nfv);
-      const float2 nm = make_float2(na.x, na.y);
       if (pd.first) {
         p0 = 0.5f * gp;
         u0 = 0.5f * gu;
         v0 = 0.5f * gv;
       }
-      tmem_st4(tbase + 4u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T) & (kGSlots - 1)), gp, gu, gv, 0.f);
+      {
+        // s2 kappa and s2 b as pairs: the rounded product plus its exact error and the lo part
+        const float kh = __fmul_rn(sh2, na.x), bh = __fmul_rn(sh2, na.y);
+        const float kl = fmaf(sl2, na.x, fmaf(sh2, na.x, -kh)), bl = fmaf(sl2, na.y, fmaf(sh2, na.y, -bh));
+        tmem_st8(tbase + 8u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T) & (kGSlots - 1)), kh, bh, kl, bl, gp, gu,
+                 gv, 0.f);
+      }
       w[0][r0] = make_float2(p0, v0);
       lvl[r0 * kRow] = make_float2(p0, u0);
-      med[r0 * kThreads] = __fmul2_rn(make_float2(mh, mh), nm);
       const float2 am_pv = make_float2(n1p, n1v);
       const float am_u = n1u;
       // ---- prefetch step s + 1 (rows wrap, so the extra fetch after the last step is in bounds) ----
@@ -342,10 +350,8 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
 #pragma unroll
       for (int t = 1; t <= T; ++t) {
         const int r = (uu + OFF - R * T - R * t) % U;   // slot of this level's row
-        const float2 km = med[(((t - 1) / 2) * U + r) * kThreads];
-        if (t % 2 == 0 && t < T) med[((t / 2) * U + r) * kThreads] = km;
-        uint32_t g0, g1, g2, g3;   // this row's forcing, loaded while the stencil sums run
-        tmem_ld4(tbase + 4u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T - R * t) & (kGSlots - 1)), g0, g1, g2, g3);
+        Row8 rc;   // this row's constants, loaded while the stencil sums run
+        tmem_ld8(tbase + 8u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T - R * t) & (kGSlots - 1)), rc);
         const float2 sxv = xsum2<R>(lvl + ((t - 1) * U + r) * kRow);   // (sum_x p, sum_x u)
         const float2 syv = ysum2<R>(w[t - 1], r);                       // (sum_y p, sum_y v)
         float2 ppv;
@@ -357,10 +363,14 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
           ppv = w[t - 2][r];
           pu = lvl[((t - 2) * U + r) * kRow].y;
         }
-        const float4 g = tmem_wait_ld(g0, g1, g2, g3);
-        const float np = fmaf(km.x, fmaf(rxy, syv.y, sxv.y), ppv.x + g.x);
-        const float nu = fmaf(km.y, sxv.x, pu + g.y);
-        const float nv = fmaf(km.y * rxy, syv.x, ppv.y + g.z);
+        tmem_wait_ld8(rc);
+        const float kh = __uint_as_float(rc.v[0]), bh = __uint_as_float(rc.v[1]);
+        const float kl = __uint_as_float(rc.v[2]), bl = __uint_as_float(rc.v[3]);
+        // d_(n+1) = d_(n-1) + g + s2 (kappa (sum_x u + rxy sum_y v), b sum_x p, b rxy sum_y p)
+        const float sp = fmaf(rxy, syv.y, sxv.y), sv = rxy * syv.x;
+        const float np = fmaf(kh, sp, fmaf(kl, sp, ppv.x + __uint_as_float(rc.v[4])));
+        const float nu = fmaf(bh, sxv.x, fmaf(bl, sxv.x, pu + __uint_as_float(rc.v[5])));
+        const float nv = fmaf(bh, sv, fmaf(bl, sv, ppv.y + __uint_as_float(rc.v[6])));
         if (t < T) {
           w[t][r] = make_float2(np, nv);
           lvl[(t * U + r) * kRow] = make_float2(np, nu);
@@ -754,7 +764,7 @@ __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch
 size_t ring_bytes(int R, bool x2) {
   const int u = 2 * R + 1;
   if (x2) return (size_t)(kTX2 * u * kRow + u * kThreads) * sizeof(float4);
-  return (size_t)(kTMax * u * kRow + media_planes() * u * kThreads) * sizeof(float2);
+  return (size_t)(kTMax * u * kRow) * sizeof(float2);
 }
 
 // GBS_F32X2: y_out (FP64) = sum_k c_k y*_k from the averages held as FP32 pairs, summed in
@@ -1112,6 +1122,7 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   P.slots = p.slots;
   P.hk = p.hk;
   P.hkf = p.hkf;
+  P.hkq = p.hkq;
   P.aux = w->aux;
   P.init = w->init;
   P.lev = w->lev;

@@ -21,7 +21,27 @@ struct ProbDev {
   int64_t tblk_begin;  // first block of this problem in the x-y tiled grid
   int tiles_x, tiles_y;  // x-y tiles per z plane (kTileX x kTileY points each)
   double inv_dx[3];
+  // FP32 kernels (integer-weight stencil sums, gbs_plain.cu): dx_0 / dx_d per axis, and
+  // 1 / (div dx_0) split into two floats (div = 12 or 60, the weights' common divisor)
+  float rr[3];
+  float f0s[2];
 };
+
+// The FP32 kernels' per-problem constants above (host; R the stencil radius).
+inline void fill_fp32_consts(ProbDev& q, int ndim, int R) {
+  for (int d = 0; d < 3; ++d) q.rr[d] = d < ndim ? (float)(q.inv_dx[d] / q.inv_dx[0]) : 0.f;
+  const double c = q.inv_dx[0] / (R == 2 ? 12.0 : 60.0);
+  q.f0s[0] = (float)c;
+  q.f0s[1] = (float)(c - (double)q.f0s[0]);
+}
+
+// The FP32 kernels' per-sequence step constants (host): 2h and 2h / (div dx_0) of sequence k of
+// problem q, each split into two floats (hi, lo).
+inline float4 fp32_step_consts(const ProbDev& q, double hk, int R) {
+  const double g = 2.0 * hk, sc = g * q.inv_dx[0] / (R == 2 ? 12.0 : 60.0);
+  const float gh = (float)g, sh = (float)sc;
+  return make_float4(gh, (float)(g - (double)gh), sh, (float)(sc - (double)sh));
+}
 
 // One weight slot: m sequences with step counts and FP64 weights, in
 // combine order (dependent weights first, then free ones).
@@ -52,6 +72,7 @@ struct StepPlan {
   const double* H;             // per problem
   const double* hk;            // per problem x GBS_MAX_SEQ: h_k = H / N_k (host-computed)
   const float2* hkf;           // the same as FP32 pairs (h_k, 2 h_k)
+  const float4* hkq;           // FP32 paths, per problem x GBS_MAX_SEQ: fp32_step_consts
   int64_t total_blocks;        // point-parallel blocks over the whole batch
   int64_t total_tiles;         // x-y tiled blocks over the whole batch (2D/3D)
   int64_t state_elems;         // scalars in one state buffer (sum of F * pts)

@@ -151,6 +151,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
       }
       d.n[k] = (int)n;
     }
+    fill_fp32_consts(d, pb->ndim, R);
     d.pts = (int64_t)d.n[0] * d.n[1] * d.n[2];
     if (d.pts >= (int64_t(1) << 31)) return noalloc_fail(GBS_ERR_INVALID, "a problem has 2^31 or more points");
     d.slot = 0;
@@ -167,7 +168,8 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const size_t o_H = align256(o_slot + sizeof(SlotDev));
   const size_t o_hk = align256(o_H + sizeof(double) * pb->batch);
   const size_t o_hkf = align256(o_hk + sizeof(double) * pb->batch * GBS_MAX_SEQ);
-  const size_t o_b = align256(o_hkf + sizeof(float2) * pb->batch * GBS_MAX_SEQ);
+  const size_t o_hkq = align256(o_hkf + sizeof(float2) * pb->batch * GBS_MAX_SEQ);
+  const size_t o_b = align256(o_hkq + sizeof(float4) * pb->batch * GBS_MAX_SEQ);
   const size_t o_f0 = align256(o_b + (pb->system == GBS_ACOUSTIC ? moff * esz : 0));
   const size_t o_L0 = align256(o_f0 + soff * esz);
   const size_t o_L1 = align256(o_L0 + soff * esz);
@@ -199,15 +201,17 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   gbs_status st = scratch_address(&base);
   if (st != GBS_OK) return st;
   char* sc = static_cast<char*>(base);
-  // host staging of the per-problem step tables: automatic arrays (about 66 KB of stack)
+  // host staging of the per-problem step tables: automatic arrays (about 130 KB of stack)
   double Hs[256];
   double hk[256 * GBS_MAX_SEQ];
   float2 hkf[256 * GBS_MAX_SEQ];
+  float4 hkq[256 * GBS_MAX_SEQ];
   for (int p = 0; p < pb->batch; ++p) {
     Hs[p] = H;
     for (int k = 0; k < GBS_MAX_SEQ; ++k) {
       hk[p * GBS_MAX_SEQ + k] = k < m ? H / slot.steps[k] : 0.0;
       hkf[p * GBS_MAX_SEQ + k] = make_float2((float)hk[p * GBS_MAX_SEQ + k], (float)(2.0 * hk[p * GBS_MAX_SEQ + k]));
+      hkq[p * GBS_MAX_SEQ + k] = fp32_step_consts(probs[p], hk[p * GBS_MAX_SEQ + k], R);
     }
   }
   // pageable sources: each copy returns once its data are staged, so the stack arrays may go
@@ -217,6 +221,8 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
       cudaMemcpyAsync(sc + o_hk, hk, sizeof(double) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaMemcpyAsync(sc + o_hkf, hkf, sizeof(float2) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(sc + o_hkq, hkq, sizeof(float4) * pb->batch * GBS_MAX_SEQ, cudaMemcpyHostToDevice, s) !=
           cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: table upload failed");
@@ -241,6 +247,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.H = reinterpret_cast<const double*>(sc + o_H);
   p.hk = reinterpret_cast<const double*>(sc + o_hk);
   p.hkf = reinterpret_cast<const float2*>(sc + o_hkf);
+  p.hkq = reinterpret_cast<const float4*>(sc + o_hkq);
   p.total_blocks = blk;
   p.total_tiles = tiles;
   p.state_elems = soff;

@@ -99,6 +99,36 @@ __device__ __forceinline__ void load_inv_dx(const ProbDev& q, T* inv_dx) {
   inv_dx[2] = T(q.inv_dx[2]);
 }
 
+// FP32 right-hand sides in integer-weight form: the stencil weights as integers over a common
+// divisor (fd_int, fd_div), so t = div dx_0 f(y) carries no rounded coefficient; the caller
+// applies 1 / (div dx_0), times 2h in a leap-frog update, as a constant split into two floats
+// (mul_split, or two FMAs), so that no rounding is shared by every point of a sequence (such a
+// rounding perturbs the operator coherently, and modes near the stability limit amplify it).
+// rr[d] = dx_0 / dx_d (ProbDev::rr; 1 for equal spacings).
+template <int R>
+__device__ __forceinline__ float isum_point(const float* __restrict__ f, const PointGeo& g, int d) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j)
+    s = fmaf(fd_int<R>(j), ldg(f + g.i + nb_off(g.c[d], j, g.n[d], g.st[d])) - ldg(f + g.i + nb_off(g.c[d], -j, g.n[d], g.st[d])), s);
+  return s;
+}
+template <int SYS, int DIM, int R>
+__device__ __forceinline__ void rhs_point_int(const float* __restrict__ y, int64_t P, const PointGeo& g,
+                                              const float* rr, float kap, float bb, float* t) {
+  if (SYS == SYS_WAVE1D) {
+    t[0] = isum_point<R>(y + P, g, 0);
+    t[1] = isum_point<R>(y, g, 0);
+  } else {
+    float sdiv = 0.f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) sdiv = fmaf(rr[d], isum_point<R>(y + (1 + d) * P, g, d), sdiv);
+    t[0] = -kap * sdiv;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) t[1 + d] = -bb * (rr[d] * isum_point<R>(y, g, d));
+  }
+}
+
 template <typename T, int SYS, int DIM, int R>
 __global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* __restrict__ y_in) {
   const Loc L = locate(p);
@@ -114,7 +144,14 @@ __global__ void __launch_bounds__(kPlainBlock) k_f0(const StepPlan p, const T* _
     bb = ldg(static_cast<const T*>(p.b) + q.media_off + L.i);
   }
   T f[kMaxFields];
-  rhs_point<T, SYS, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx, kap, bb, f);
+  if constexpr (std::is_same<T, float>::value) {
+    float t[kMaxFields];
+    rhs_point_int<SYS, DIM, R>(y_in + q.state_off, q.pts, g, q.rr, kap, bb, t);
+#pragma unroll
+    for (int fl = 0; fl < F; ++fl) f[fl] = mul_split(q.f0s[0], q.f0s[1], t[fl]);
+  } else {
+    rhs_point<T, SYS, DIM, R>(y_in + q.state_off, q.pts, g, inv_dx, kap, bb, f);
+  }
   T* f0 = static_cast<T*>(p.f0) + q.state_off;
   if constexpr (SYS == SYS_ACOUSTIC && DIM == 2 && std::is_same<T, float>::value) {
     if (p.f0_aux) {
@@ -141,13 +178,12 @@ __global__ void __launch_bounds__(kPlainBlock) k_fe(const StepPlan p, const T* _
   T* L1 = static_cast<T*>(p.L1) + q.state_off;
   const T* y0 = y_in + q.state_off;
   if constexpr (std::is_same<T, float>::value) {
-    // increment form: d_1 = h f0 (y_0 is added back by the combine)
-    float hh, hl;
-    split_h(p.hk[L.prob * GBS_MAX_SEQ + k], hh, hl);
+    // increment form: d_1 = h f0 = (2h f0) / 2 (y_0 is added back by the combine)
+    const float4 hq = p.hkq[L.prob * GBS_MAX_SEQ + k];
 #pragma unroll
     for (int fl = 0; fl < F; ++fl) {
       const int64_t e = fl * q.pts + L.i;
-      L1[e] = mul_split(hh, hl, f0[e]);
+      L1[e] = 0.5f * mul_split(hq.x, hq.y, f0[e]);
     }
   } else {
 #pragma unroll
@@ -184,12 +220,26 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     kap = ldg(static_cast<const T*>(p.kappa) + q.media_off + L.i);
     bb = ldg(static_cast<const T*>(p.b) + q.media_off + L.i);
   }
-  T f[kMaxFields];
-  rhs_point<T, SYS, DIM, R>(cur, q.pts, g, inv_dx, kap, bb, f);
-  // FP32: increment form, d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n with d_0 = 0
+  // FP32: increment form, d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n with d_0 = 0, the right-hand side
+  // in integer-weight form scaled by 2h / (div dx_0) as a float pair
   constexpr bool kInc = std::is_same<T, float>::value;
-  float gh = 0.f, gl = 0.f;
-  if constexpr (kInc) split_h(2.0 * p.hk[L.prob * GBS_MAX_SEQ + k], gh, gl);
+  T f[kMaxFields];
+  float gh = 0.f, gl = 0.f, sch = 0.f, scl = 0.f;
+  if constexpr (kInc) {
+    const float4 hq = p.hkq[L.prob * GBS_MAX_SEQ + k];
+    gh = hq.x;
+    gl = hq.y;
+    sch = hq.z;
+    scl = hq.w;
+    rhs_point_int<SYS, DIM, R>(cur, q.pts, g, q.rr, kap, bb, f);
+  } else {
+    rhs_point<T, SYS, DIM, R>(cur, q.pts, g, inv_dx, kap, bb, f);
+  }
+  // the leap-frog update prev + 2h f (FP32: the pair scaling of the integer-weight form)
+  auto lf_update = [&](T pv, T fv) -> T {
+    if constexpr (kInc) return fmaf(sch, fv, fmaf(scl, fv, pv));
+    else return pv + h2 * fv;
+  };
   const T* f0 = static_cast<const T*>(p.f0) + q.state_off;
   T pv[kMaxFields];
 #pragma unroll
@@ -202,7 +252,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
 #pragma unroll
     for (int fl = 0; fl < F; ++fl) {
       const int64_t e = fl * q.pts + L.i;
-      dst[e] = pv[fl] + h2 * f[fl];
+      dst[e] = lf_update(pv[fl], f[fl]);
     }
     return;
   }
@@ -217,7 +267,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const int64_t e = fl * q.pts + L.i;
     const T ym = kInc && n == 1 ? T(0) : prev[e];
     const T y0 = cur[e];
-    const T yp = pv[fl] + h2 * f[fl];
+    const T yp = lf_update(pv[fl], f[fl]);
     combine_last(acc, e, first, last, c, gragg_avg(ym, y0, yp), yo, kInc && first ? y_in[q.state_off + e] : T(0));
   }
 }
@@ -357,8 +407,15 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   // FP32: increment form (gbs_stencil.cuh), d_(n+1) = d_(n-1) + 2h f0 + 2h A d_n, d_0 = 0
   constexpr bool kInc = std::is_same<T, float>::value;
   const T* f0v = static_cast<const T*>(p.f0) + q.state_off;
-  float gh = 0.f, gl = 0.f;
-  if constexpr (kInc) split_h(2.0 * p.hk[lo * GBS_MAX_SEQ + k], gh, gl);
+  float gh = 0.f, gl = 0.f, sch = 0.f, scl = 0.f;
+  if constexpr (kInc) {
+    // the forcing's 2h, and -2h / (div dx_0) for the integer-weight stencil sums, as float pairs
+    const float4 hq = p.hkq[lo * GBS_MAX_SEQ + k];
+    gh = hq.x;
+    gl = hq.y;
+    sch = -hq.z;
+    scl = -hq.w;
+  }
   const bool prev_zero = kInc && n == 1;
   // point-wise operands of a row (previous level, media, f0 in the increment form, and in 3D
   // the z-neighbours of p and w), loaded one row ahead of their use; the first row's before the
@@ -495,7 +552,10 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     }
   }
   __syncthreads();
-  const T idx = T(q.inv_dx[0]), idy = T(q.inv_dx[1]), idz = T(q.inv_dx[2]);
+  // FP32 (integer-weight form): idx unused, idy and idz the spacing ratios dx_0 / dx_d
+  const T idx = T(q.inv_dx[0]);
+  const T idy = kInc ? T(q.rr[1]) : T(q.inv_dx[1]);
+  const T idz = kInc ? T(q.rr[2]) : T(q.inv_dx[2]);
   if (x >= nx) return;
   const double c = s.c[k];
   const bool first = (k == 0), last = (k == s.m - 1);
@@ -523,38 +583,64 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     }
     if (i + 1 < kTileRows) fetch_row(i + 1);
     const int r = ly + R, cc = threadIdx.x + HX;
+    // stencil sums: FP32 states with the integer weights (times div), otherwise the weights
     T sxu = T(0), sxp = T(0), syv = T(0), syp = T(0);
 #pragma unroll
     for (int j = 1; j <= R; ++j) {
-      const T a = T(fd_coef<R>(j));
+      const T a = kInc ? T(fd_int<R>(j)) : T(fd_coef<R>(j));
       sxp += a * (sh[0][r][cc + j] - sh[0][r][cc - j]);
       sxu += a * (sh[1][r][cc + j] - sh[1][r][cc - j]);
       syp += a * (sh[0][r + j][cc] - sh[0][r - j][cc]);
       syv += a * (sh[2][r + j][cc] - sh[2][r - j][cc]);
     }
     const Off o = o0 + (Off)(8 * i) * nx;
-    T div = sxu * idx + syv * idy;
-    T szp = T(0);
+    T szp = T(0), szw = T(0);
     if (DIM == 3) {
-      T szw = T(0);
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
-        const T a = T(fd_coef<R>(j));
+        const T a = kInc ? T(fd_int<R>(j)) : T(fd_coef<R>(j));
         szp += a * (zpv[j - 1][0] - zmv[j - 1][0]);
         szw += a * (zpv[j - 1][1] - zmv[j - 1][1]);
       }
-      div += szw * idz;
     }
     T f[kMaxFields];
-    f[0] = -kv * div;
-    f[1] = -bv * (sxp * idx);
-    f[2] = -bv * (syp * idy);
-    if (DIM == 3) f[3] = -bv * (szp * idz);
+    // FP32: the scaled media s kappa and s b (s = -2h / (div dx_0)) as float pairs, the rounded
+    // product plus its exact error and the lo part
+    float kh = 0.f, kl = 0.f, bh = 0.f, bl = 0.f;
+    if constexpr (kInc) {
+      // the stencil sums of div dx_0 f(d_n) without the media; idy, idz are dx_0 / dx_d here
+      T sd = fmaf(idy, syv, sxu);
+      if (DIM == 3) sd = fmaf(idz, szw, sd);
+      f[0] = sd;
+      f[1] = sxp;
+      f[2] = idy * syp;
+      if (DIM == 3) f[3] = idz * szp;
+      kh = __fmul_rn(sch, kv);
+      kl = fmaf(scl, kv, fmaf(sch, kv, -kh));
+      bh = __fmul_rn(sch, bv);
+      bl = fmaf(scl, bv, fmaf(sch, bv, -bh));
+    } else {
+      T div = sxu * idx + syv * idy;
+      if (DIM == 3) div += szw * idz;
+      f[0] = -kv * div;
+      f[1] = -bv * (sxp * idx);
+      f[2] = -bv * (syp * idy);
+      if (DIM == 3) f[3] = -bv * (szp * idz);
+    }
+    // prev + 2h f (FP32: the pair-scaled media times the stencil sums)
+    auto lf_update = [&](int fl, T pv_, T fv) -> T {
+      if constexpr (kInc) {
+        const float mh = fl == 0 ? kh : bh, ml = fl == 0 ? kl : bl;
+        return fmaf(mh, fv, fmaf(ml, fv, pv_));
+      } else {
+        return pv_ + h2 * fv;
+      }
+    };
     if (n < N) {
 #pragma unroll
       for (int fl = 0; fl < F; ++fl) {
-        if (DIM == 3) (dst + fl * P)[o] = pg[fl] + h2 * f[fl];
-        else dst[fl * P + o] = pg[fl] + h2 * f[fl];
+        if (DIM == 3) (dst + fl * P)[o] = lf_update(fl, pg[fl], f[fl]);
+        else dst[fl * P + o] = lf_update(fl, pg[fl], f[fl]);
       }
     } else {
       double* acc = p.acc + q.state_off;
@@ -563,7 +649,7 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       for (int fl = 0; fl < F; ++fl) {
         const int64_t e = fl * P + o;
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
-        const T yp = pg[fl] + h2 * f[fl];
+        const T yp = lf_update(fl, pg[fl], f[fl]);
         combine_last(acc, e, first, last, c, gragg_avg(pv[fl], yc, yp), yo,
                      kInc && first ? y_in[q.state_off + e] : T(0));
       }
