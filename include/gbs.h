@@ -182,6 +182,32 @@ gbs_status gbs_stability_limit(gbs_handle h, double* H_max);
  * (a used slot has no weights), GBS_ERR_CUDA (launch failure). */
 gbs_status gbs_step(gbs_handle h, const void* y_in, void* y_out, double H, int n_macro);
 
+/* Sequence-parallel macro-step, first half (Sec. 3.6: the sequences of one
+ * macro-step are independent, and the paper spreads them over cores, folding
+ * pairs whose step counts add up to N_max onto one core).  Runs one macro-step
+ * of size H for the sequences k whose bit (seq_mask >> k) & 1 is set (k = the
+ * position in each problem's scheme, dependent sequences first) and writes
+ * their share of the combine into partial: an FP64 array in the state layout
+ * (state_elems doubles, device, owned by the caller).  The shares of all ranks
+ * -- disjoint masks covering every sequence -- summed element by element (an
+ * FP64 all-reduce), then given to gbs_combine_partial, give the macro-step's
+ * result.  For FP32 states the share is sum_k c_k (y*_k - y_0) in the increment
+ * form; for FP64 and FP32-pair states sum_k c_k y*_k.  One macro-step per call;
+ * y_in is not modified.  A mask different from the previous call's re-plans
+ * the time-blocked kernel's schedule (host work, and an allocation if it
+ * needs more room).  Errors: GBS_ERR_INVALID (NULL handle or pointers, a mask
+ * selecting no sequence, the spectral system), GBS_ERR_STATE (a slot without
+ * weights), GBS_ERR_NOMEM, GBS_ERR_CUDA. */
+gbs_status gbs_step_partial(gbs_handle h, const void* y_in, double* partial, double H, uint32_t seq_mask);
+
+/* Sequence-parallel macro-step, second half: y_out = y_in + total for FP32
+ * states (increment form), y_out = total for FP64 and FP32-pair states, total
+ * being the element-wise FP64 sum of every rank's gbs_step_partial share for
+ * the same y_in and H (the combine of Sec. 2.1 / 3.2 completed), rounded once
+ * to the state type.  y_out == y_in is allowed.  Asynchronous.  Errors:
+ * GBS_ERR_INVALID, GBS_ERR_STATE, GBS_ERR_CUDA. */
+gbs_status gbs_combine_partial(gbs_handle h, const void* y_in, const double* total, void* y_out);
+
 /* As gbs_step with one H per problem (host array of `batch` doubles): the
  * macro-step of Sec. 2.1 / 3.2 for each problem with its own section length.
  * Errors as gbs_step, and GBS_ERR_INVALID for a NULL array or an H that is

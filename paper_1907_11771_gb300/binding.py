@@ -53,6 +53,8 @@ _SIGS = {
     "gbs_stability_limit": (_I, [_P, ctypes.POINTER(_D)]),
     "gbs_step": (_I, [_P, _P, _P, _D, _I]),
     "gbs_step_batch": (_I, [_P, _P, _P, ctypes.POINTER(_D), _I]),
+    "gbs_step_partial": (_I, [_P, _P, _P, _D, ctypes.c_uint32]),
+    "gbs_combine_partial": (_I, [_P, _P, _P, _P]),
     "gbs_step_host": (_I, [_P, _P, _P, _D, _I]),
     "gbs_step_host_stream": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _D, _I]),
     "gbs_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _P, _I, _P]),
@@ -182,6 +184,14 @@ def gbs_step(h, y_in, y_out, H, n_macro):
 
 def gbs_step_batch(h, y_in, y_out, H, n_macro):
     _check(h, lib().gbs_step_batch(h, _ptr(y_in), _ptr(y_out), _arr(_D, [float(v) for v in H]), int(n_macro)))
+
+
+def gbs_step_partial(h, y_in, partial, H, seq_mask):
+    _check(h, lib().gbs_step_partial(h, _ptr(y_in), _ptr(partial), float(H), int(seq_mask) & 0xFFFFFFFF))
+
+
+def gbs_combine_partial(h, y_in, total, y_out):
+    _check(h, lib().gbs_combine_partial(h, _ptr(y_in), _ptr(total), _ptr(y_out)))
 
 
 def gbs_step_host(h, y_in_host, y_out_host, H, n_macro):

@@ -107,6 +107,7 @@ struct gbs_ctx {
   alignas(64) unsigned char lf_tmap[2][128] = {};
   int64_t opt_spin_limit = 1 << 20;
   int opt_inject_wait = 0;
+  uint32_t fused_mask = ~0u;              // sequences of the prepared time-blocked schedule
   int opt_combine = 0;                    // time-blocked FP32 path: 0 = FP64 combine, 1 = compensated
                                           // FP32 pairs
   std::vector<cudaEvent_t> tev;           // event pairs for kernel timing
@@ -400,6 +401,8 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   p->L1 = h->L1;
   p->acc = h->acc;
   p->err = h->d_err;
+  p->seq_mask = ~0u;
+  p->partial = 0;
   if (tma_in_use(h)) {
     p->lf_tmap[0] = h->lf_tmap[0];
     p->lf_tmap[1] = h->lf_tmap[1];
@@ -451,7 +454,7 @@ gbs_status prepare_fused(gbs_ctx* h) {
   }
   CK(h, cudaStreamSynchronize(h->stream));
   char msg[256] = {0};
-  const FusedTune tune{h->opt_hseg, h->opt_tmax ? h->opt_tmax : fused_max_levels(), h->opt_schedule};
+  const FusedTune tune{h->opt_hseg, h->opt_tmax ? h->opt_tmax : fused_max_levels(), h->opt_schedule, h->fused_mask};
   const int r = fused_prepare(h->fw, p, h->probs.data(), sd, tune, msg, sizeof msg);
   if (r == -2) return fail(h, GBS_ERR_NOMEM, "%s", msg);
   if (r < 0) return fail(h, GBS_ERR_CUDA, "%s", msg);
@@ -826,6 +829,10 @@ gbs_status gbs_step_batch(gbs_handle h, const void* y_in, void* y_out, const dou
     if (a != b) CK(h, cudaMemcpyAsync(y_out, y_in, bytes, cudaMemcpyDeviceToDevice, h->stream));
     return GBS_OK;
   }
+  if (h->fused_mask != ~0u) {   // a partial step planned the time-blocked kernel for fewer sequences
+    h->fused_mask = ~0u;
+    if ((st = prepare_fused(h)) != GBS_OK) return st;
+  }
   for (int it = 0; it < n_macro; ++it) {
     st = run_macro(h, p, it == 0 ? y_in : y_out, y_out);
     if (st != GBS_OK) return st;
@@ -837,6 +844,46 @@ gbs_status gbs_step(gbs_handle h, const void* y_in, void* y_out, double H, int n
   if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
   std::vector<double> Hs(h->batch, H);
   return gbs_step_batch(h, y_in, y_out, Hs.data(), n_macro);
+}
+
+gbs_status gbs_step_partial(gbs_handle h, const void* y_in, double* partial, double H, uint32_t seq_mask) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!y_in || !partial) return fail(h, GBS_ERR_INVALID, "state pointers must not be NULL");
+  if (h->system == GBS_ONEWAY_SPECTRAL) return fail(h, GBS_ERR_INVALID, "partial steps need a finite-difference system");
+  if ((seq_mask & ((1u << GBS_MAX_SEQ) - 1u)) == 0) return fail(h, GBS_ERR_INVALID, "the sequence mask selects no sequence");
+  StepPlan p;
+  gbs_status st = build_plan(h, &p);
+  if (st != GBS_OK) return st;
+  std::vector<double> Hs(h->batch, H);
+  if ((st = set_H(h, Hs.data())) != GBS_OK) return st;
+  // problems whose slot has none of the selected sequences contribute zero
+  CK(h, cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)h->state_elems, h->stream));
+  const bool fused = use_fused(h, p) && !h->ds;
+  if (fused && h->fused_mask != seq_mask) {   // plan the time-blocked kernel for these sequences
+    h->fused_mask = seq_mask;
+    if ((st = prepare_fused(h)) != GBS_OK) return st;
+  }
+  p.seq_mask = seq_mask;
+  p.partial = 1;
+  p.acc = partial;
+  const int n = fused && h->fw_ready ? fused_partial_step(h->fw, p, y_in, partial, h->stream, h->d_err)
+                                     : plain_macro_step(p, y_in, const_cast<void*>(y_in), h->stream);
+  if (n < 0) return fail(h, GBS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += n;
+  return GBS_OK;
+}
+
+gbs_status gbs_combine_partial(gbs_handle h, const void* y_in, const double* total, void* y_out) {
+  if (!h) return fail(nullptr, GBS_ERR_INVALID, "handle is NULL");
+  if (!y_in || !total || !y_out) return fail(h, GBS_ERR_INVALID, "pointers must not be NULL");
+  if (h->system == GBS_ONEWAY_SPECTRAL) return fail(h, GBS_ERR_INVALID, "partial steps need a finite-difference system");
+  StepPlan p;
+  gbs_status st = build_plan(h, &p);
+  if (st != GBS_OK) return st;
+  if (finish_partial(p, y_in, total, y_out, h->stream) < 0)
+    return fail(h, GBS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += 1;
+  return GBS_OK;
 }
 
 gbs_status gbs_step_host(gbs_handle h, const void* y_in_host, void* y_out_host, double H, int n_macro) {

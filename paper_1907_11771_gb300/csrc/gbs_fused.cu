@@ -761,6 +761,21 @@ __global__ void __launch_bounds__(256) k_combine(const ProbDev* probs, int batch
   }
 }
 
+// A partial step's combine share: partial = sum_k c_k d*_k over the sequences in mask (FP64,
+// ascending k, the averages promoted exactly), without y_0; the sum of every rank's share is
+// finished by finish_partial.
+__global__ void __launch_bounds__(256) k_combine_partial(const ProbDev* probs, int batch, const SlotDev* slots,
+                                                         const float* __restrict__ dstar, int64_t E, uint32_t mask,
+                                                         double* __restrict__ partial) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const SlotDev& s = slots[probs[problem_of(probs, batch, e)].slot];
+    double a = 0.0;
+    for (int k = 0; k < s.m; ++k)
+      if ((mask >> k) & 1u) a = fma(s.c[k], promote(__ldcs(dstar + (int64_t)k * E + e)), a);
+    partial[e] = a;
+  }
+}
+
 size_t ring_bytes(int R, bool x2) {
   const int u = 2 * R + 1;
   if (x2) return (size_t)(kTX2 * u * kRow + u * kThreads) * sizeof(float4);
@@ -812,6 +827,7 @@ struct FusedWork {
   bool x2 = false;        // GBS_F32X2: levels, averages and inputs as FP32 pairs
   double alg_bytes = 0;   // algorithmic bytes of one k_passes launch
   int combine_f64 = 1;    // FP32 states: combine in FP64 (1) or in compensated FP32 pairs (0)
+  uint32_t seq_mask = ~0u;   // the sequences the prepared schedule computes
   long long spin_limit = fused::kSpinLimit;
   int inject_wait = 0;    // test hook: item 0 also waits on a flag that nothing sets
 };
@@ -909,6 +925,7 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   }
   w->E = p.state_elems;
   w->R = p.R;
+  w->seq_mask = tune.seq_mask;
   w->hseg = hseg;
   w->m_max = p.max_m;
   // pass descriptors per (slot, seq, pass)
@@ -934,6 +951,7 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
     tg[q] = tiles_of(probs_h[q].n[0], probs_h[q].n[1], hseg, p.R * tmax);
     const SlotDev& s = slots_h[probs_h[q].slot];
     for (int k = 0; k < s.m; ++k) {
+      if (!((tune.seq_mask >> k) & 1u)) continue;   // a partial step leaves it to another rank
       const int np = (int)pass_plan(s.steps[k], tmax).size();
       for (int qq = 0; qq < np; ++qq)
         for (int t = 0; t < tg[q].nst * tg[q].nseg; ++t) keys.push_back({np - qq, q, k, qq, t});
@@ -1094,7 +1112,42 @@ int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const
   return 0;
 }
 
+namespace {
+// f0 (and the pair inputs) and the pass kernel of one macro-step; returns launches or -1
+int fused_passes(FusedWork* w, const StepPlan& p, const void* y_in, cudaStream_t s, int* err);
+}
+
 int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err) {
+  using namespace fused;
+  int launches = fused_passes(w, p, y_in, s, err);
+  if (launches < 0) return -1;
+  if (w->x2)
+    k_combine_x2<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, reinterpret_cast<const float2*>(w->ystar), w->E,
+                                      static_cast<double*>(y_out));
+  else if (w->combine_f64)
+    k_combine<true><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
+                                         static_cast<float*>(y_out));
+  else
+    k_combine<false><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
+                                          static_cast<float*>(y_out));
+  ++launches;
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+int fused_partial_step(FusedWork* w, const StepPlan& p, const void* y_in, double* partial, cudaStream_t s, int* err) {
+  using namespace fused;
+  if (w->x2) return -1;
+  int launches = fused_passes(w, p, y_in, s, err);
+  if (launches < 0) return -1;
+  k_combine_partial<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, w->seq_mask, partial);
+  ++launches;
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return launches;
+}
+
+namespace {
+int fused_passes(FusedWork* w, const StepPlan& p, const void* y_in, cudaStream_t s, int* err) {
   using namespace fused;
   int launches = 0;
   if (w->x2) {
@@ -1144,18 +1197,9 @@ int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_
   }
   timing_end(p, u, s, w->alg_bytes);
   ++launches;
-  if (w->x2)
-    k_combine_x2<<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, reinterpret_cast<const float2*>(w->ystar), w->E,
-                                      static_cast<double*>(y_out));
-  else if (w->combine_f64)
-    k_combine<true><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
-                                         static_cast<float*>(y_out));
-  else
-    k_combine<false><<<1024, 256, 0, s>>>(p.probs, p.batch, p.slots, w->ystar, w->E, static_cast<const float*>(y_in),
-                                          static_cast<float*>(y_out));
-  ++launches;
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return launches;
 }
+}  // namespace
 
 }  // namespace gbs

@@ -111,7 +111,19 @@ struct StepPlan {
   // bounded wait on the copy latches GBS_ERR_TIMEOUT in
   const void* lf_tmap[2];
   int* err;
+  // sequence-parallel partial steps: bit k set = sequence k of every problem's slot is computed
+  // (all bits: a whole macro-step); partial = 1: the combine accumulates only those sequences'
+  // share in acc (no y_0 term, no y_out written)
+  uint32_t seq_mask;
+  int partial;
 };
+
+// First and last sequence a step computes among the slot's m sequences (device).
+__device__ __forceinline__ void seq_first_last(const StepPlan& p, int k, int m, bool& first, bool& last) {
+  const unsigned msk = p.seq_mask & ((1u << m) - 1u);   // m <= GBS_MAX_SEQ = 16
+  first = k == __ffs(msk) - 1;
+  last = !p.partial && k == 31 - __clz(msk);
+}
 
 // Tensor map of one FP32 level buffer [F][nz][ny][nx] for the tiled leap-frog step's staging
 // box (the tile's 40 staged columns x 32 + 2R rows x one z-plane x the fields p, u, v); writes
@@ -188,11 +200,17 @@ struct FusedTune {
   int hseg;
   int tmax;
   int schedule;
+  uint32_t seq_mask;   // sequences scheduled (bit k: sequence k); all bits for whole macro-steps
 };
 int fused_prepare(FusedWork* w, const StepPlan& p, const ProbDev* probs_h, const SlotDev* slots_h,
                   const FusedTune& tune, char* msg, size_t msglen);
 int fused_max_levels();   // largest tmax the kernel was compiled for
 int fused_macro_step(FusedWork* w, const StepPlan& p, const void* y_in, void* y_out, cudaStream_t s, int* err);
+// FP32 states: the sequences of the prepared mask only, their combine share written to partial
+// (FP64, state layout): sum_k c_k d*_k over those sequences.
+int fused_partial_step(FusedWork* w, const StepPlan& p, const void* y_in, double* partial, cudaStream_t s, int* err);
+// y_out = y_in (increment form) or 0 (others) + total, total the FP64 sum of every rank's partial
+int finish_partial(const StepPlan& p, const void* y_in, const double* total, void* y_out, cudaStream_t s);
 
 // Adjoint of one macro-step with stored forward levels (plain kernels).
 struct AdjPlan {

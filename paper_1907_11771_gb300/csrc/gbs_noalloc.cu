@@ -97,6 +97,18 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   if ((pb->system == GBS_ACOUSTIC) != (kappa != nullptr && rho != nullptr))
     return noalloc_fail(GBS_ERR_INVALID, "acoustics needs kappa and rho; the 1D wave system takes none");
   if (!y_in || !y_out) return noalloc_fail(GBS_ERR_INVALID, "state pointers must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the tables below are uploaded from pageable host memory, which a stream capture cannot
+    // record: refuse before anything is enqueued, so the caller's capture stays valid
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: cudaStreamIsCapturing failed");
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return noalloc_fail(GBS_ERR_STATE, "gbs_step_noalloc must not be called while its stream is being captured");
+  }
   for (const void* ptr : {kappa, rho, static_cast<const void*>(y_in), static_cast<const void*>(y_out)}) {
     if (!ptr) continue;
     cudaPointerAttributes at;
@@ -185,18 +197,6 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   const char* a = static_cast<const char*>(y_in);
   const char* b = static_cast<const char*>(y_out);
   if (a != b && a < b + bytes && b < a + bytes) return noalloc_fail(GBS_ERR_INVALID, "y_in and y_out overlap partially");
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  {
-    // the tables below are uploaded from pageable host memory, which a stream capture cannot
-    // record: refuse before anything is enqueued, so the caller's capture stays valid
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
-      cudaGetLastError();
-      return noalloc_fail(GBS_ERR_CUDA, "gbs_step_noalloc: cudaStreamIsCapturing failed");
-    }
-    if (cs != cudaStreamCaptureStatusNone)
-      return noalloc_fail(GBS_ERR_STATE, "gbs_step_noalloc must not be called while its stream is being captured");
-  }
   void* base = nullptr;
   gbs_status st = scratch_address(&base);
   if (st != GBS_OK) return st;
@@ -258,6 +258,7 @@ extern "C" gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa,
   p.L1 = sc + o_L1;
   p.acc = reinterpret_cast<double*>(sc + o_acc);
   p.max_m = m;
+  p.seq_mask = ~0u;
   for (int k = 0; k < m; ++k) p.max_steps_k[k] = slot.steps[k];
   for (int it = 0; it < n_macro; ++it) {
     if (plain_macro_step(p, it == 0 ? y_in : y_out, y_out, s) < 0) {

@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
   // n == N: y_(N+1), averaging y* = (y_(N-1) + 2 y_N + y_(N+1)) / 4 in the state type,
   // then the FP64 combine.
   const double c = s.c[k];
-  const bool first = (k == 0), last = (k == s.m - 1);
+  bool first, last;
+  seq_first_last(p, k, s.m, first, last);
   double* acc = p.acc + q.state_off;
   auto* yo = y_out + q.state_off;
 #pragma unroll
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_lf(const StepPlan p, const T* y
     const T ym = kInc && n == 1 ? T(0) : prev[e];
     const T y0 = cur[e];
     const T yp = lf_update(pv[fl], f[fl]);
-    combine_last(acc, e, first, last, c, gragg_avg(ym, y0, yp), yo, kInc && first ? y_in[q.state_off + e] : T(0));
+    combine_last(acc, e, first, last, c, gragg_avg(ym, y0, yp), yo,
+                 kInc && first && !p.partial ? y_in[q.state_off + e] : T(0));
   }
 }
 
@@ -558,7 +560,8 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   const T idz = kInc ? T(q.rr[2]) : T(q.inv_dx[2]);
   if (x >= nx) return;
   const double c = s.c[k];
-  const bool first = (k == 0), last = (k == s.m - 1);
+  bool first, last;
+  seq_first_last(p, k, s.m, first, last);
 #pragma unroll
   for (int i = 0; i < kTileRows; ++i) {
     const int ly = threadIdx.y + 8 * i;
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
         const T yp = lf_update(fl, pg[fl], f[fl]);
         combine_last(acc, e, first, last, c, gragg_avg(pv[fl], yc, yp), yo,
-                     kInc && first ? y_in[q.state_off + e] : T(0));
+                     kInc && first && !p.partial ? y_in[q.state_off + e] : T(0));
       }
     }
   }
@@ -775,7 +778,8 @@ __global__ void __launch_bounds__(256, DIM == 3 ? 3 : 4) k_lf_tiled_x2(const Ste
   const dsf idx = dsf(q.inv_dx[0]), idy = dsf(q.inv_dx[1]), idz = dsf(q.inv_dx[2]);
   if (x >= nx) return;
   const double c = s.c[k];
-  const bool first = (k == 0), last = (k == s.m - 1);
+  bool first, last;
+  seq_first_last(p, k, s.m, first, last);
 #pragma unroll
   for (int i = 0; i < kTileRows; ++i) {
     const int ly = threadIdx.y + 8 * i;
@@ -1425,6 +1429,7 @@ int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStrea
   k_f0<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in);
   ++launches;
   for (int k = 0; k < p.max_m; ++k) {
+    if (!((p.seq_mask >> k) & 1u)) continue;   // a partial step leaves this sequence to another rank
     k_fe<T, SYS, DIM><<<grid, block, 0, st>>>(p, y_in, k);
     ++launches;
     for (int n = 1; n <= p.max_steps_k[k]; ++n) {
@@ -1660,4 +1665,27 @@ int lf_tma_encode(void* map, void* base, int nx, int ny, int nz, int F, int R) {
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+}  // namespace gbs
+
+namespace gbs {
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) k_finish_partial(const T* y_in, const double* __restrict__ total, T* y_out,
+                                                        int64_t n, int inc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y_out[e] = T(inc ? (double)y_in[e] + total[e] : total[e]);
+}
+}  // namespace
+
+// The end of a sequence-parallel macro-step: total is the FP64 sum of every rank's combine share;
+// FP32 states (increment form) add y_in, FP64 and FP32-pair states hold sum_k c_k y*_k already.
+int finish_partial(const StepPlan& p, const void* y_in, const double* total, void* y_out, cudaStream_t s) {
+  if (p.f64)
+    k_finish_partial<double><<<1024, 256, 0, s>>>(static_cast<const double*>(y_in), total, static_cast<double*>(y_out),
+                                                  p.state_elems, 0);
+  else
+    k_finish_partial<float><<<1024, 256, 0, s>>>(static_cast<const float*>(y_in), total, static_cast<float*>(y_out),
+                                                 p.state_elems, 1);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 }  // namespace gbs

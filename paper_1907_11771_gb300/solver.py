@@ -77,6 +77,12 @@ class GBSSolver:
         else:
             B.gbs_step(self.h, y_in, y_out, H, n_macro)
 
+    def step_partial(self, y_in, partial, H, seq_mask):
+        B.gbs_step_partial(self.h, y_in, partial, H, seq_mask)
+
+    def combine_partial(self, y_in, total, y_out):
+        B.gbs_combine_partial(self.h, y_in, total, y_out)
+
     def step_host(self, y_in_host, y_out_host, H, n_macro=1):
         B.gbs_step_host(self.h, y_in_host, y_out_host, H, n_macro)
 
