@@ -11,10 +11,8 @@ Paper passages followed:
 * Sec. 2.1 / Sec. 3.2: the extrapolated result is sum_k c_k y*_k.  The sum is
   taken in FP64 in the order the sequences are given.
 
-Precision: the whole computation runs in the dtype of ``y`` (FP64 normally).
-With ``state_dtype=np.float32`` the FE/LF/averaging arithmetic is done in
-FP32 and only the weighted sum is accumulated in FP64 (then rounded back to
-the state dtype) -- an emulation of an FP32-state / FP64-combine path.
+Precision: the whole computation runs in the dtype of ``y`` (FP64; complex128
+for the spectral test problem's modes).
 
 The adjoint is the exact transpose of these steps, derived by hand (reverse
 accumulation through the recurrences); the gradient with respect to kappa
@@ -35,23 +33,20 @@ def gbs_sequence(f, y0, H, N, f0=None):
     return (ys[N - 1] + dt(2) * ys[N] + ys[N + 1]) / dt(4)   # averaging
 
 
-def gbs_macro_step(f, y, H, steps, c, state_dtype=None):
-    """sum_k c_k y*_k for the sequences ``steps`` with weights ``c``; FP64 sum.
+def gbs_macro_step(f, y, H, steps, c):
+    """sum_k c_k y*_k for the sequences ``steps`` with weights ``c``, summed in ascending k.
     Sec. 2.1 eq. "GBS" per sequence, combined as in Sec. 3.2."""
-    sdt = np.dtype(state_dtype) if state_dtype is not None else y.dtype
-    ys = y.astype(sdt)
-    f0 = f(ys)                                     # shared first evaluation
-    acc_dt = np.result_type(np.float64, sdt)       # FP64 (complex128 for complex states)
-    acc = np.zeros(y.shape, dtype=acc_dt)
+    f0 = f(y)                                      # shared first evaluation
+    acc = np.zeros_like(y)
     for N, ck in zip(steps, c):
-        acc = acc + float(ck) * gbs_sequence(f, ys, H, N, f0).astype(acc_dt)
-    return acc.astype(sdt)
+        acc = acc + float(ck) * gbs_sequence(f, y, H, N, f0)
+    return acc
 
 
-def gbs_run(f, y, H, steps, c, n_macro, state_dtype=None):
+def gbs_run(f, y, H, steps, c, n_macro):
     """n_macro consecutive macro-steps (the time interval split into sections, Sec. 2.1)."""
     for _ in range(n_macro):
-        y = gbs_macro_step(f, y, H, steps, c, state_dtype)
+        y = gbs_macro_step(f, y, H, steps, c)
     return y
 
 

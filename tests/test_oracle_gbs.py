@@ -241,15 +241,3 @@ def test_misfit_gradient_central_differences():
         fd = (run(kappa + eps * d)[0] - run(kappa - eps * d)[0]) / (2 * eps)
         assert np.sum(g * d) == pytest.approx(fd, rel=1e-6)
 
-
-def test_fp32_emulation_stays_close_to_fp64():
-    # Not a pin: records that the FP32-state / FP64-combine emulation tracks FP64 to ~1e-6.
-    n = 256
-    y0, dx = inputs.wave1d_initial(n)
-    _, steps, c = SQ8
-    cf = W.to_fp64(c)
-    f = lambda y: mol.rhs_wave1d(y, y.dtype.type(dx), 4)
-    y64 = G.gbs_run(f, y0, 0.05, steps, cf, 10)
-    y32 = G.gbs_run(f, y0.astype(np.float32), 0.05, steps, cf, 10, state_dtype=np.float32)
-    rel = np.linalg.norm(y32 - y64) / np.linalg.norm(y64)
-    assert 1e-9 < rel < 1e-5
