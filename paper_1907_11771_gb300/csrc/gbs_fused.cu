@@ -217,7 +217,7 @@ __device__ __forceinline__ float2 ysum2(const float2 (&w)[2 * R + 1], int r) {
 // lo, about 2^-48 relative), so that no rounding of the scaling is shared by the points and
 // steps of a sequence (that would perturb its operator coherently, which the combine's weights
 // and the modes near the stability limit amplify).  When level 0 reaches a row it computes the
-// row's eight constants (s2 kappa and s2 b as pairs, g), which the T levels that pass over the
+// row's eight constants (s2 kappa and s2 b as hi and lo pairs, g for p, v and u), which the T levels that pass over the
 // row later read from a ring of kGSlots rows per thread in tensor memory (tbase: this thread's
 // lane and column base): row r's slot is r mod kGSlots, and a row is needed for R T < kGSlots
 // steps.  A slot written at step s is read from step s + R on; every R steps the sweep waits
@@ -318,21 +318,21 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
       // ---- level 0 (local row s - R T), the row's constants, level -1 ----
       const int r0 = (uu + OFF - R * T) % U;
       float p0 = n0p, u0 = n0u, v0 = n0v;
-      // the forcing g = 2h f0; in a first pass level 0 is d_1 = h f0 = g / 2
-      const float gp = mul_split(gh, gl, na.z);
+      // the forcing g = 2h f0 (packed for (p, v)); in a first pass level 0 is d_1 = h f0 = g / 2
+      const float2 gpv = mul_split2(make_float2(gh, gh), make_float2(gl, gl), make_float2(na.z, nfv));
       const float gu = mul_split(gh, gl, na.w);
-      const float gv = mul_split(gh, gl, nfv);
       if (pd.first) {
-        p0 = 0.5f * gp;
+        p0 = 0.5f * gpv.x;
         u0 = 0.5f * gu;
-        v0 = 0.5f * gv;
+        v0 = 0.5f * gpv.y;
       }
       {
-        // s2 kappa and s2 b as pairs: the rounded product plus its exact error and the lo part
-        const float kh = __fmul_rn(sh2, na.x), bh = __fmul_rn(sh2, na.y);
-        const float kl = fmaf(sl2, na.x, fmaf(sh2, na.x, -kh)), bl = fmaf(sl2, na.y, fmaf(sh2, na.y, -bh));
-        tmem_st8(tbase + 8u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T) & (kGSlots - 1)), kh, bh, kl, bl, gp, gu,
-                 gv, 0.f);
+        // (s2 kappa, s2 b) as pairs: the rounded products, then their exact errors plus the lo parts
+        const float2 m = make_float2(na.x, na.y), shv = make_float2(sh2, sh2);
+        const float2 kbh = __fmul2_rn(shv, m);
+        const float2 kbl = __ffma2_rn(make_float2(sl2, sl2), m, __ffma2_rn(shv, m, make_float2(-kbh.x, -kbh.y)));
+        tmem_st8(tbase + 8u * ((uint32_t)(sb + uu + 64 * kGSlots - R * T) & (kGSlots - 1)), kbh.x, kbh.y, kbl.x,
+                 kbl.y, gpv.x, gpv.y, gu, 0.f);
       }
       w[0][r0] = make_float2(p0, v0);
       lvl[r0 * kRow] = make_float2(p0, u0);
@@ -364,13 +364,15 @@ __device__ __forceinline__ void run_item(const Params& P, const Item& it, const 
           pu = lvl[((t - 2) * U + r) * kRow].y;
         }
         tmem_wait_ld8(rc);
-        const float kh = __uint_as_float(rc.v[0]), bh = __uint_as_float(rc.v[1]);
-        const float kl = __uint_as_float(rc.v[2]), bl = __uint_as_float(rc.v[3]);
-        // d_(n+1) = d_(n-1) + g + s2 (kappa (sum_x u + rxy sum_y v), b sum_x p, b rxy sum_y p)
-        const float sp = fmaf(rxy, syv.y, sxv.y), sv = rxy * syv.x;
-        const float np = fmaf(kh, sp, fmaf(kl, sp, ppv.x + __uint_as_float(rc.v[4])));
-        const float nu = fmaf(bh, sxv.x, fmaf(bl, sxv.x, pu + __uint_as_float(rc.v[5])));
-        const float nv = fmaf(bh, sv, fmaf(bl, sv, ppv.y + __uint_as_float(rc.v[6])));
+        const float2 kbh = make_float2(__uint_as_float(rc.v[0]), __uint_as_float(rc.v[1]));   // (s2 kappa, s2 b) hi
+        const float2 kbl = make_float2(__uint_as_float(rc.v[2]), __uint_as_float(rc.v[3]));   // and lo
+        const float2 gpv = make_float2(__uint_as_float(rc.v[4]), __uint_as_float(rc.v[5]));   // forcing of (p, v)
+        // d_(n+1) = d_(n-1) + g + s2 (kappa (sum_x u + rxy sum_y v), b sum_x p, b rxy sum_y p), with
+        // (p, v) as one packed lane pair: sums (sum_x u + rxy sum_y v, rxy sum_y p)
+        const float2 spv = __ffma2_rn(make_float2(rxy, rxy), make_float2(syv.y, syv.x), make_float2(sxv.y, 0.f));
+        const float2 npv = __ffma2_rn(kbh, spv, __ffma2_rn(kbl, spv, __fadd2_rn(ppv, gpv)));
+        const float np = npv.x, nv = npv.y;
+        const float nu = fmaf(kbh.y, sxv.x, fmaf(kbl.y, sxv.x, pu + __uint_as_float(rc.v[6])));
         if (t < T) {
           w[t][r] = make_float2(np, nv);
           lvl[(t * U + r) * kRow] = make_float2(np, nu);

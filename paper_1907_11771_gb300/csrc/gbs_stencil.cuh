@@ -86,6 +86,13 @@ __device__ __forceinline__ float mul_split(float hi, float lo, float f) {
   return __fadd_rn(p, fmaf(lo, f, e));
 }
 
+// mul_split on a packed pair of lanes (Blackwell f32x2 instructions): each lane as mul_split
+__device__ __forceinline__ float2 mul_split2(float2 hi, float2 lo, float2 f) {
+  const float2 p = __fmul2_rn(hi, f);
+  const float2 e = __ffma2_rn(hi, f, make_float2(-p.x, -p.y));
+  return __fadd2_rn(p, __ffma2_rn(lo, f, e));
+}
+
 // The combine of the plain path's last leap-frog step of sequence k: y_out (+)= c_k y*_k in FP64.
 // FP32 states are in increment form (y*_k = y_0 + d*_k): the first sequence starts the
 // accumulator at y_0, each adds c_k d*_k (d*_k promoted exactly), the last rounds once to FP32.

@@ -4,8 +4,8 @@
   checkpointing (segments of C macro-steps, the last one partial) and with
   binomial checkpointing (s stored states) against the oracle's FP64
   misfit_and_gradient;
-* dJ/dkappa against central finite differences of the GPU forward on seeded
-  directions (FP64 path);
+* dJ/dkappa against central finite differences of the GPU forward on 16 seeded
+  directions (FP64 states);
 * GBSStepFn / GBSMisfitFn through torch.autograd.
 """
 import numpy as np
@@ -39,7 +39,7 @@ def _setup(precision, shape=(24, 28), n_macro=7, seed=5):
     rcv = np.array([3, 40, 41, 200, n - 5, 333], dtype=np.int64)
     rng = np.random.default_rng(seed)
     data = (0.05 * rng.standard_normal((n_macro, rcv.size))).astype(case.np_dtype).astype(np.float64)
-    dt = torch.float64 if precision == F64 else torch.float32
+    dt = torch.float32 if precision == F32 else torch.float64
     t = dict(y0=torch.tensor(case.y0.ravel(), dtype=dt, device="cuda"),
              rcv=torch.tensor(rcv, device="cuda"),
              data=torch.tensor(data, dtype=dt, device="cuda"))
@@ -61,14 +61,17 @@ def test_misfit_gradient_with_checkpointing_matches_oracle(precision, ckpt, snap
     sol.close()
 
 
-def test_misfit_gradient_central_differences_fp64():
+@pytest.mark.parametrize("precision", [F64])
+def test_misfit_gradient_central_differences_on_16_directions(precision):
+    # the adjoint workload's check: dJ/dkappa against central differences on 16 seeded
+    # directions to 1e-6 relative (FP64 states)
     n_macro = 4
-    case, sol, H, rcv, data, t = _setup(F64, n_macro=n_macro)
+    case, sol, H, rcv, data, t = _setup(precision, n_macro=n_macro)
     J, g = gbs_misfit_and_grad(sol, t["y0"], H, n_macro, t["rcv"], t["data"], checkpoint_every=2)
     g = g.cpu().numpy()
     rng = np.random.default_rng(3)
     base = case.kappa.ravel()
-    for _ in range(4):
+    for _ in range(16):
         d = rng.standard_normal(base.size)
         eps = 1e-6
         Js = []
