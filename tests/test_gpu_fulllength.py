@@ -266,3 +266,40 @@ def test_variable_media_fp32_against_fp64_states_at_full_length(case):
     bound = TOL[F32] if case == "config2" else fp32_floor(S.GBS_8_6, M)
     print(f"{case} variable media, FP32 vs FP64 states (pairs), {M} macro-steps: rel L2 {err:.3e} (bound {bound:.2e})")
     assert err <= bound, err
+
+
+def test_fp32_states_reach_1e6_with_the_classical_scheme():
+    """The time-to-1e-6 race's accuracy side: the 2048^2 workload's recipe on 1024^2 advanced to
+    t = 100 H0 (H0 = 0.8 x GBS_8,6's stability limit).  With the classical {2,4,6,8} (Richardson
+    weights, sqrt(sum_k c_k^2 (N_k + 1)) = 12 against 91.5 for GBS_8,6) at 0.8 of its own limit,
+    FP32 states reach a relative L2 error below 1e-6 against an FP64 GBS_12,8 reference at a
+    quarter of its own 0.8 x limit (that reference's self-check at an eighth: 5e-12)."""
+    n = 1024
+    y0, kappa, rho = inputs.acoustic_problem((n, n), 0, 16, 20.0 * n / 2048)
+
+    def make(prec, scheme):
+        dt = torch.float32 if prec == F32 else torch.float64
+        npdt = np.float32 if prec == F32 else np.float64
+        k = torch.tensor(kappa.astype(npdt).ravel(), dtype=dt, device="cuda")
+        r = torch.tensor(rho.astype(npdt).ravel(), dtype=dt, device="cuda")
+        sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=6, precision=prec, kappa=k, rho=r)
+        sol.set_scheme(scheme)
+        lim = sol.stability_limit()[0]
+        return sol, lim, dt
+
+    sol8, lim8, _ = make(F64, S.GBS_8_6)
+    T = 100 * 0.8 * lim8
+    sol8.close()
+    outs = {}
+    for key, prec, scheme, quarter in (("ref", F64, S.GBS_12_8, 4), ("f32", F32, S.SQ8_2468, 1)):
+        sol, lim, dt = make(prec, scheme)
+        M = int(math.ceil(T / (0.8 * lim * (1 + 1e-12)))) * quarter
+        y = torch.tensor(y0.ravel(), dtype=dt, device="cuda")
+        out = torch.empty_like(y)
+        sol.step(y, out, T / M, M)
+        sol.sync()
+        sol.close()
+        outs[key] = out.to(torch.float64)
+    err = (torch.linalg.vector_norm(outs["f32"] - outs["ref"]) / torch.linalg.vector_norm(outs["ref"])).item()
+    print(f"1024^2 to t = 100 H0, FP32 states, {{2,4,6,8}}: rel L2 {err:.3e}")
+    assert err <= 1e-6, err
