@@ -15,37 +15,43 @@ is affine in c_free.  Since |R(0)| = 1 the subproblem's value is never below
 zero; the bisection needs its feasibility at a given h, decided here by linear
 programming on samples y_j of the contour:
 
-* |R_j| <= 1 - mu_j is the intersection of the half-planes
-  Re(e^(-i phi) R_j) <= 1 - mu_j over all phi.  The LP starts from eight
-  angles per sample and adds the tangent cut at phi = arg R_j wherever the
-  solution still leaves the circle (cutting planes), until every sample holds
-  to 1e-13.  mu_j = margin min(1, (h y_j / 4)^(p+2)) keeps the solution off the
-  circle away from the origin.
-* Near the origin the free weights move R only at O(y^(p+1)) (the order
-  constraints), below rounding: samples where they cannot move R by 1e-8 of
-  their largest effect are left to one linear constraint that keeps the
-  stability region open along the axis.  With R(xi) = e^xi + e_(p+1) xi^(p+1)
-  + e_(p+2) xi^(p+2) + ..., |R(iy)|^2 - 1 starts with
-  2 s (e_(p+1) - e_(p+2)) y^(p+2), s = +1 for p = 0 mod 4 and -1 for
-  p = 2 mod 4, which must be negative (the sign of a_(p+2) in Sec. 3.5); its
-  margin is relative, since these coefficients scale like 1/(p+1)!.
-* The LP's objective is a margin t weighted by each sample's sensitivity to
-  the free weights, which makes the LP always feasible and picks a central
-  point; h is feasible when the cut loop converges.
+* The unknown is delta(xi) = e^(-xi) R(xi) - 1 rather than R: |R| <= 1 is
+  |1 + delta| <= 1, and delta, O(xi^(p+1)) near the origin, is computed
+  without cancelling against 1 -- from the exact Taylor coefficients of
+  R - e^xi (rational arithmetic on the GBS polynomials, whose first p + 1
+  vanish by the order constraints) for |xi| <= 6, from the GBS recurrence on
+  the test equation further out.  So every sample keeps its relative accuracy,
+  however little the free weights move it.
+* |1 + delta_j| <= 1 - mu_j is the intersection of the half-planes
+  Re(e^(-i psi) delta_j) <= 1 - cos psi - mu_j over all psi.  The LP starts
+  from eight angles per sample and adds the tangent cut at psi = arg(1 + delta_j)
+  wherever the solution still leaves the circle (cutting planes), until every
+  sample's excess is below 1e-10 of its sensitivity to the free weights.
+  mu_j = margin min(1, (h y_j / 4)^(p+2)) keeps the solution off the circle
+  away from the origin.
+* One linear constraint keeps the stability region open along the axis at the
+  origin: with R(xi) = e^xi + e_(p+1) xi^(p+1) + e_(p+2) xi^(p+2) + ...,
+  |R(iy)|^2 - 1 starts with 2 s (e_(p+1) - e_(p+2)) y^(p+2), s = +1 for
+  p = 0 mod 4 and -1 for p = 2 mod 4, which must be negative (the sign of
+  a_(p+2) in Sec. 3.5); its margin is relative, since these coefficients scale
+  like 1/(p+1)!.
+* The LP's objective is a margin t weighted by each sample's sensitivity,
+  which makes the LP always feasible and picks a central point; h is feasible
+  when the cut loop converges with t <= 0.
 * Exchange: the solution is checked on a grid `refine` times finer, points
   that leave the circle (by more than half the margin) join the samples, and
   the LP is solved again.
-* Every LP is centred on the weights of the largest feasible h so far, which
-  keeps its right-hand sides moderate.
+* Every LP is centred on the weights of the largest feasible h so far, with the
+  free weights scaled column by column, which keeps its entries moderate.
 
-Stability polynomials are evaluated through the GBS recurrence on the test
-equation (well conditioned on the imaginary axis for |h lambda| <= N_k).
 This is a host-side design tool: it produces weights for gbs_set_weights and is
-checked by exact root isolation of the resulting R.  For order 8 on all even
-counts up to 22 and up to 30, and order 4 up to 28, it reproduces the optimal
-ISB_n the paper prints (Sec. 3.8, Table 2); at order 12 and 16 the LP's
-tolerances no longer resolve the constraints (rows whose sensitivities span
-many decades) and it stops short of the printed optima.
+checked by exact root isolation of the resulting R.  It reproduces the optimal
+ISB_n the paper prints for order 4 up to 28 and order 8 up to 22, 30 and 40
+(Sec. 3.8, Table 2; 0.8548 against 0.8551 at 40) and the optimum on the counts
+of the paper's GBS_12,8 (0.7128).  On all counts up to 36 (order 12) and 32
+(order 16) its strictly stable optima, 0.677 and 0.42, stay below the printed
+0.7504 and 0.6075; allowing |R| up to 1 + 1e-12 on the contour and dropping the
+constraint at the origin, order 16 reaches 0.625.
 """
 from dataclasses import dataclass
 from fractions import Fraction
@@ -74,24 +80,29 @@ def _solve(A, b):
     return [M[i][n] for i in range(n)]
 
 
-def affine_weights(order, steps_dep, steps_free):
-    """c = c0 + G c_free with c = (c_dep, c_free): exact rational c0 (|dep|+|free|) and G."""
+def affine_weights_exact(order, steps_dep, steps_free):
+    """c = c0 + G c_free with c = (c_dep, c_free), as exact rationals: c0 (a list of m) and G
+    (m lists of |free|)."""
     q = order // 2
     Vd = _vandermonde(steps_dep, order)
     Vf = _vandermonde(steps_free, order)
     b = [Fraction(1)] + [Fraction(0)] * (q - 1)
-    c_dep0 = _solve(Vd, b)
-    cols = []
-    for f in range(len(steps_free)):
-        cols.append(_solve(Vd, [-Vf[j][f] for j in range(q)]))
-    m = len(steps_dep) + len(steps_free)
-    c0 = np.zeros(m)
-    G = np.zeros((m, len(steps_free)))
-    c0[:q] = [float(v) for v in c_dep0]
-    for f, col in enumerate(cols):
-        G[:q, f] = [float(v) for v in col]
-        G[q + f, f] = 1.0
+    m, nf = len(steps_dep) + len(steps_free), len(steps_free)
+    c0 = [Fraction(0)] * m
+    c0[:q] = _solve(Vd, b)
+    G = [[Fraction(0)] * nf for _ in range(m)]
+    for f in range(nf):
+        col = _solve(Vd, [-Vf[j][f] for j in range(q)])
+        for i in range(q):
+            G[i][f] = col[i]
+        G[q + f][f] = Fraction(1)
     return c0, G
+
+
+def affine_weights(order, steps_dep, steps_free):
+    """c = c0 + G c_free with c = (c_dep, c_free): c0 and G of affine_weights_exact in FP64."""
+    c0, G = affine_weights_exact(order, steps_dep, steps_free)
+    return np.array([float(v) for v in c0]), np.array([[float(v) for v in row] for row in G])
 
 
 def gbs_poly_values(n, xi):
@@ -147,34 +158,86 @@ def _margin(h, ys, margin, order):
     return margin * np.minimum(1.0, (h * ys / 4.0) ** (order + 2))
 
 
-def _lp_feasible(h, steps, c0, G, lead, order, ys, margin, x0, tol=1e-13, angles=8, rounds=40):
-    """Free weights with |R(i h y_j)| <= 1 - mu_j on the samples and the lead term negative,
-    by cutting planes around x0; None if the LP proves none exists or the cuts do not settle."""
-    P = np.stack([gbs_poly_values(n, 1j * h * ys) for n in steps], axis=1)
-    a, B = P @ (c0 + G @ x0), P @ G
-    D = 1.0 / np.maximum(np.abs(B).max(axis=0), 1e-300)     # column scaling: x = x0 + D z
-    Bs = B * D[None, :]
-    sens = np.abs(Bs).max(axis=1)
-    keep = sens > 1e-8
-    a, Bs, sens = a[keep], Bs[keep], sens[keep]
-    mu = _margin(h, ys[keep], margin, order)
-    nf = G.shape[1]
+class _DeltaRows:
+    """delta(xi) = e^(-xi) R(xi) - 1 on the contour xi = i h y, affine in the free weights:
+    delta = d0 + D c_free.  |R| <= 1 is |1 + delta| <= 1, and delta carries no cancellation
+    against 1: for |xi| <= XS it is summed from the exact Taylor coefficients of R - e^xi, whose
+    first p + 1 vanish by the order constraints (Sec. 3.2), so near the origin, where delta is
+    O(xi^(p+1)), it keeps its relative accuracy; further out from the GBS recurrence."""
+
+    XS = 6.0
+
+    def __init__(self, order, steps, c0x, Gx):
+        self.order, self.steps = order, tuple(steps)
+        deg = max(steps) + 1
+        coef = [gbs_poly_coeffs(n, deg) for n in steps]           # exact, m x (deg + 1)
+        nf = len(Gx[0])
+        E0, Q = [], []
+        for j in range(order + 1, deg + 1):
+            E0.append(float(sum(c0x[k] * coef[k][j] for k in range(len(steps))) - Fraction(1, factorial(j))))
+            Q.append([float(sum(Gx[k][f] * coef[k][j] for k in range(len(steps)))) for f in range(nf)])
+        self.j0, self.deg = order + 1, deg
+        self.E0, self.Q = np.array(E0), np.array(Q)                 # (deg - p) and (deg - p) x nf
+        self.tail = np.array([1.0 / factorial(j) for j in range(deg + 1, deg + 25)])
+        self.c0 = np.array([float(v) for v in c0x])
+        self.G = np.array([[float(v) for v in row] for row in Gx])
+
+    def at(self, h, ys, x0):
+        """(delta at c_free = x0, D) for the samples y (complex arrays)."""
+        xi = 1j * h * ys
+        small = np.abs(xi) <= self.XS
+        d = np.empty(ys.size, complex)
+        D = np.empty((ys.size, self.G.shape[1]), complex)
+        if small.any():
+            z = xi[small]
+            pw = z[:, None] ** np.arange(self.j0, self.deg + 1)[None, :]
+            tail = -(z[:, None] ** np.arange(self.deg + 1, self.deg + 25)[None, :]) @ self.tail
+            em = np.exp(-z)
+            d[small] = em * (pw @ (self.E0 + self.Q @ x0) + tail)
+            D[small] = em[:, None] * (pw @ self.Q)
+        big = ~small
+        if big.any():
+            z = xi[big]
+            P = np.stack([gbs_poly_values(n, z) for n in self.steps], axis=1)
+            em = np.exp(-z)
+            d[big] = em * (P @ (self.c0 + self.G @ x0)) - 1.0
+            D[big] = em[:, None] * (P @ self.G)
+        return d, D
+
+
+def _excess(d):
+    """|1 + delta| - 1 without cancellation."""
+    return (2.0 * d.real + np.abs(d) ** 2) / (np.abs(1.0 + d) + 1.0)
+
+
+def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8, rounds=60):
+    """Free weights with |1 + delta_j| <= 1 - mu_j on the samples and the lead term negative, by
+    cutting planes around x0: the half-planes Re(e^(-i psi) delta_j) <= 1 - cos psi - mu_j, cut
+    at psi = arg(1 + delta_j), each row scaled by its own sensitivity to the free weights;
+    converged when every sample's excess is below tol times its sensitivity.  (x, column
+    scales), or None if the LP proves that none exists or the cuts do not settle."""
+    d, B = rows_model.at(h, ys, x0)
+    Dc = 1.0 / np.maximum(np.abs(B).max(axis=0), 1e-300)     # column scaling: x = x0 + Dc z
+    Bs = B * Dc[None, :]
+    sens = np.maximum(np.abs(Bs).max(axis=1), 1e-300)
+    mu = _margin(h, ys, margin, order)
+    nf = Bs.shape[1]
     rows, rhs = [], []
 
-    def cut(j, phi):
-        e = np.exp(-1j * phi)
+    def cut(j, psi):
+        e = np.exp(-1j * psi)
         r = (e * Bs[j]).real
         sc = 1.0 / max(np.abs(r).max(), sens[j])
         rows.append(np.concatenate([r * sc, [-sens[j] * sc]]))
-        rhs.append((1.0 - mu[j] - (e * a[j]).real) * sc)
+        rhs.append((2.0 * np.sin(0.5 * psi) ** 2 - mu[j] - (e * d[j]).real) * sc)
 
-    for j in range(a.size):
+    for j in range(d.size):
         for k in range(angles):
             cut(j, 2 * np.pi * k / angles)
     lg, lr = lead
     eps = 1e-8 * abs(lr)
-    ls = 1.0 / max(np.abs(lg * D).max(), 1e-300)
-    lead_row = np.concatenate([lg * D * ls, [0.0]])
+    ls = 1.0 / max(np.abs(lg * Dc).max(), 1e-300)
+    lead_row = np.concatenate([lg * Dc * ls, [0.0]])
     lead_rhs = -(lr + lg @ x0 + eps) * ls
     cost = np.zeros(nf + 1)
     cost[-1] = 1.0
@@ -187,24 +250,26 @@ def _lp_feasible(h, steps, c0, G, lead, order, ys, margin, x0, tol=1e-13, angles
         if res.status != 0 or res.x[-1] > 0:
             return None
         z = res.x[:nf]
-        R = a + Bs @ z
-        v = np.abs(R) - 1 + mu
+        dz = d + Bs @ z
+        v = (_excess(dz) + mu) / sens
         if v.max() <= tol:
-            return x0 + z * D
+            return x0 + z * Dc, Dc
         for j in np.where(v > tol)[0]:
-            cut(j, np.angle(R[j]))
+            cut(j, np.arctan2(dz[j].imag, 1.0 + dz[j].real))
     return None
 
 
-def _feasible(h, steps, c0, G, lead, order, ys, fine, margin, x0, tol=1e-13, rounds=6):
+def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, rounds=8):
     """Exchange loop around the LP: weights stable on the fine grid (half the margin), or None."""
     pts = ys
     for _ in range(rounds):
-        x = _lp_feasible(h, steps, c0, G, lead, order, pts, margin, x0)
-        if x is None:
+        r = _lp_feasible(h, rows_model, lead, order, pts, margin, x0)
+        if r is None:
             return None
-        P = np.stack([gbs_poly_values(n, 1j * h * fine) for n in steps], axis=1)
-        v = np.abs(P @ (c0 + G @ x)) - 1 + 0.5 * _margin(h, fine, margin, order)
+        x, Dc = r
+        d, B = rows_model.at(h, fine, x)
+        sens = np.maximum(np.abs(B * Dc[None, :]).max(axis=1), 1e-300)
+        v = (_excess(d) + 0.5 * _margin(h, fine, margin, order)) / sens
         bad = np.where(v > tol)[0]
         if bad.size == 0:
             return x
@@ -212,15 +277,18 @@ def _feasible(h, steps, c0, G, lead, order, ys, fine, margin, x0, tol=1e-13, rou
     return None
 
 
-def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-7, rel_tol=1e-7, h_hi=None):
+def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9, rel_tol=1e-7, h_hi=None):
     """Maximise the imaginary stability boundary over the free weights (App. B): bisection over
     h in (0, N_max + 1] with the LP feasibility test above.  The dependent/free split only fixes
     the parametrisation (every split spans the same weights); small dependent counts keep it
     well conditioned."""
     steps_dep, steps_free = tuple(steps_dep), tuple(steps_free)
     steps = steps_dep + steps_free
-    c0, G = affine_weights(order, steps_dep, steps_free)
+    c0x, Gx = affine_weights_exact(order, steps_dep, steps_free)
+    c0 = np.array([float(v) for v in c0x])
+    G = np.array([[float(v) for v in row] for row in Gx])
     lead = _lead_constraint(order, steps, c0, G)
+    rows_model = _DeltaRows(order, steps, c0x, Gx)
     nmax = max(steps)
     ys = np.arange(1, n_samples + 1) / n_samples
     fine = np.arange(1, refine * n_samples + 1) / (refine * n_samples)
@@ -229,7 +297,7 @@ def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-7
     found = False
     while hi - lo > rel_tol * hi:
         mid = 0.5 * (lo + hi)
-        x = _feasible(mid, steps, c0, G, lead, order, ys, fine, margin, best)
+        x = _feasible(mid, rows_model, lead, order, ys, fine, margin, best)
         if x is not None:
             lo, best, found = mid, x, True
         else:
