@@ -370,11 +370,13 @@ def run_gpu(args):
         sol.set_option("tmax", args.tmax)
     if args.schedule >= 0:
         sol.set_option("schedule", args.schedule)
+    if args.zseg:
+        sol.set_option("zseg", args.zseg)
     if args.tma != -1:
         sol.set_option("tma", args.tma)
     if args.combine == "pairs":
         sol.set_option("combine", 1)
-    if not (args.hseg or args.tmax or args.schedule >= 0 or args.no_autotune):
+    if not (args.hseg or args.tmax or args.zseg or args.schedule >= 0 or args.no_autotune):
         from paper_1907_11771_gb300 import autotune as AT
         r = AT.autotune(sol, y, H, cache=os.path.join(tempfile.gettempdir(), "gbs_gb300_tune.json"))
         if r is not None:
@@ -457,7 +459,8 @@ def run_gpu(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "kernel": "fused pass (k_passes)" if fused else "tiled leap-frog step (k_lf_tiled)",
+            "kernel": ("3D time-blocked pass (k_tb3)" if len(cfg["shape_zyx"]) == 3 else "fused pass (k_passes)")
+                      if fused else "tiled leap-frog step (k_lf_tiled)",
             "avg_launch_ms": launch_s * 1e3 if nl else None,
             "achieved_basis": "algorithmic minimum: y_in, kappa, rho read and y_out written once per macro-step "
                               f"({ALG_MIN_BYTES_PER_POINT[len(cfg['shape_zyx'])] * esz / 4:.0f} B per grid point)",
@@ -853,6 +856,7 @@ def main():
     ap.add_argument("--f64", action="store_true", help="FP64 state (plain kernels)")
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
+    ap.add_argument("--zseg", type=int, default=0, help="z-planes per block of the 3D time-blocked passes (0: default)")
     ap.add_argument("--tmax", type=int, default=0, help="most leap-frog levels per time-blocked pass (0: default)")
     ap.add_argument("--schedule", type=int, default=-1, help="work-queue order of the time-blocked kernel (-1: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -285,8 +285,15 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * GBS_ERR_UNSTABLE when H exceeds gbs_stability_limit), "time_kernels" = 0/1
  * (record CUDA events around every launch of the dominant kernel -- the
  * leap-frog step kernel, or the time-blocked pass kernel -- on the handle's
- * stream; graph replay is bypassed while it is on), "hseg" = row-segment height of
- * the time-blocked tiles (16..65536, default 256), "tmax" = most leap-frog levels per
+ * stream; graph replay is bypassed while it is on).  GBS_KERNEL_FUSED selects the
+ * time-blocked kernels: for 2D acoustics the persistent dataflow kernel below (also chosen by
+ * GBS_KERNEL_AUTO), for 3D acoustics with FP32 states the z-sweeping pass kernel, two
+ * leap-frog levels per pass (Sec. 2.1 eq. "GBS"), whose results equal the one-level kernel's
+ * bit for bit; it needs a second pair of level buffers (gbs_workspace_bytes counts them),
+ * allocated when it is selected.  On GB300 the 3D pass kernel is slower than the one-level
+ * kernel, so GBS_KERNEL_AUTO keeps the latter in 3D.  "zseg" = z-planes per block of the 3D
+ * pass kernel (1..65536, default 128).  "hseg" = row-segment height of
+ * the 2D time-blocked tiles (16..65536, default 256), "tmax" = most leap-frog levels per
  * time-blocked pass (0 = the kernel's largest, 4; or 2), "schedule" = order of the
  * time-blocked work queue (0 = longest remaining chain of passes first, the default;
  * 1 = pass by pass across all sequences) -- these three only shape the schedule and are

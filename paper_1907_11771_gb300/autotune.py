@@ -1,9 +1,10 @@
 """Autotuner for the time-blocked schedule.
 
-The time-blocked kernel's work decomposition has three knobs that change its speed but not its
-results beyond rounding order: the row-segment height of a tile ("hseg"), the most leap-frog
+The 2D time-blocked kernel's work decomposition has three knobs that change its speed but not
+its results beyond rounding order: the row-segment height of a tile ("hseg"), the most leap-frog
 levels per pass ("tmax"; deeper passes move fewer bytes but widen the halo) and the order of
-the work queue ("schedule").  The plain one-step-per-launch kernels are one more candidate: with
+the work queue ("schedule").  The 3D pass kernel has one, the z-planes per block ("zseg": longer
+segments repeat fewer warm-up planes, shorter ones give more blocks to fill the GPU).  The plain one-step-per-launch kernels are one more candidate: with
 few sequences on a small grid the time-blocked kernel has too few independent items and waits on
 its dependencies, and the plain kernels are faster.  ``autotune`` times every candidate on the
 caller's own problem
@@ -20,6 +21,12 @@ import torch
 
 DEFAULT_SPACE = {"hseg": [96, 128, 192, 256, 384], "tmax": [4, 2], "schedule": [0, 1]}
 KNOBS = ("hseg", "tmax", "schedule")
+DEFAULT_SPACE_3D = {"zseg": [32, 64, 128, 256, 512]}
+KNOBS_3D = ("zseg",)
+
+
+def _knobs(solver):
+    return KNOBS_3D if getattr(solver, "ndim", 2) == 3 else KNOBS
 
 
 def default_cache_path():
@@ -91,7 +98,7 @@ def event_timer(solver, y, H, reps=3, warmup=1, flush_bytes=256 << 20):
 
 def _apply(solver, options):
     from . import binding as B
-    for k in KNOBS:
+    for k in _knobs(solver):
         solver.set_option(k, options[k])
     solver.set_option("kernel", options.get("kernel", B.GBS_KERNEL_FUSED))
 
@@ -109,7 +116,8 @@ def autotune(solver, y=None, H=None, space=None, cache=None, timer=None, key=Non
     from . import binding as B
     if not solver.uses_fused():
         return None
-    space = dict(DEFAULT_SPACE if space is None else space)
+    knobs = _knobs(solver)
+    space = dict((DEFAULT_SPACE_3D if knobs == KNOBS_3D else DEFAULT_SPACE) if space is None else space)
     if cache is None:
         cache = default_cache_path()
     key = key or workload_key(solver)
@@ -122,8 +130,8 @@ def autotune(solver, y=None, H=None, space=None, cache=None, timer=None, key=Non
         timer = event_timer(solver, y, H)
     rows = []
     solver.set_option("kernel", B.GBS_KERNEL_FUSED)
-    for values in itertools.product(*(space[k] for k in KNOBS)):
-        opts = dict(zip(KNOBS, values))
+    for values in itertools.product(*(space[k] for k in knobs)):
+        opts = dict(zip(knobs, values))
         for k, v in opts.items():
             solver.set_option(k, v)
         rows.append({"options": dict(opts, kernel=B.GBS_KERNEL_FUSED), "seconds": float(timer())})

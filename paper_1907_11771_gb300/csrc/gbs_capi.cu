@@ -14,6 +14,7 @@
 
 #include "gbs_dd.h"
 #include "gbs_internal.h"
+#include "gbs_tb3.h"
 #include "gbs_weights.h"
 
 using namespace gbs;
@@ -91,6 +92,8 @@ struct gbs_ctx {
   float2* gpair = nullptr;                // FP32 path: per-sequence gradient sums as (hi, lo) pairs
   FusedWork* fw = nullptr;                // time-blocked path: schedule and level store
   bool fw_ready = false;
+  Tb3Work* tb3 = nullptr;                 // 3D time-blocked passes: tiles and second level pair
+  bool tb3_ready = false;
   // execution
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
@@ -99,6 +102,7 @@ struct gbs_ctx {
   int opt_check_stability = 0;
   int opt_time_kernels = 0;
   int opt_hseg = 256;
+  int opt_zseg = 128;                     // 3D time-blocked passes: z-planes per block
   int opt_tmax = 0;                       // 0: the kernel's largest pass depth
   int opt_schedule = 0;
   int opt_tma = -1;                       // tensor-map staging of the FP32 tiled step: -1 where measured
@@ -253,6 +257,8 @@ void free_all(gbs_ctx* h) {
   h->tev.clear();
   fused_destroy(h->fw);
   h->fw = nullptr;
+  tb3_destroy(h->tb3);
+  h->tb3 = nullptr;
 }
 
 struct Sizes {
@@ -435,13 +441,13 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
 // (Re)build the time-blocked schedule when it applies (set-up time: may allocate).
 gbs_status prepare_fused(gbs_ctx* h) {
   h->fw_ready = false;
+  h->tb3_ready = false;
   if (h->opt_kernel == GBS_KERNEL_PLAIN) return GBS_OK;
   StepPlan p;
   if (build_plan(h, &p) != GBS_OK) {  // some slot without weights yet: nothing to prepare
     h->err.clear();
     return GBS_OK;
   }
-  if (!fused_supported(p, h->probs.data())) return GBS_OK;
   SlotDev sd[GBS_MAX_SLOTS];
   std::memset(sd, 0, sizeof sd);
   for (int i = 0; i < GBS_MAX_SLOTS; ++i) {
@@ -452,8 +458,21 @@ gbs_status prepare_fused(gbs_ctx* h) {
     }
     split_weights(sd[i]);
   }
-  CK(h, cudaStreamSynchronize(h->stream));
   char msg[256] = {0};
+  // 3D: the pass kernel only when asked for (GBS_KERNEL_FUSED); under GBS_KERNEL_AUTO the
+  // one-level kernel, measured faster on GB300
+  if (tb3_supported(p, h->probs.data(), sd, GBS_MAX_SLOTS)) {
+    if (h->opt_kernel != GBS_KERNEL_FUSED) return GBS_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int r = tb3_prepare(h->tb3, p, h->probs.data(), sd, h->opt_zseg, msg, sizeof msg);
+    if (r == -2) return fail(h, GBS_ERR_NOMEM, "%s", msg);
+    if (r < 0) return fail(h, GBS_ERR_CUDA, "%s", msg);
+    h->tb3_ready = true;
+    ++h->sched_version;
+    return GBS_OK;
+  }
+  if (!fused_supported(p, h->probs.data())) return GBS_OK;
+  CK(h, cudaStreamSynchronize(h->stream));
   const FusedTune tune{h->opt_hseg, h->opt_tmax ? h->opt_tmax : fused_max_levels(), h->opt_schedule, h->fused_mask};
   const int r = fused_prepare(h->fw, p, h->probs.data(), sd, tune, msg, sizeof msg);
   if (r == -2) return fail(h, GBS_ERR_NOMEM, "%s", msg);
@@ -476,10 +495,13 @@ gbs_status set_H(gbs_ctx* h, const double* H) {
   return upload_hk(h);
 }
 
-bool use_fused(gbs_ctx* h, const StepPlan&) { return h->opt_kernel != GBS_KERNEL_PLAIN && h->fw_ready; }
+bool use_fused(gbs_ctx* h, const StepPlan&) {
+  return h->opt_kernel != GBS_KERNEL_PLAIN && (h->fw_ready || h->tb3_ready);
+}
 
 // Enqueue one macro-step on stream s (no graph).  Returns launches or -1.
 int enqueue_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo, cudaStream_t s, int kernel) {
+  if (kernel == GBS_KERNEL_FUSED && h->tb3_ready) return tb3_macro_step(h->tb3, p, yi, yo, s);
   if (kernel == GBS_KERNEL_FUSED) return fused_macro_step(h->fw, p, yi, yo, s, h->d_err);
   return plain_macro_step(p, yi, yo, s);
 }
@@ -548,6 +570,8 @@ size_t gbs_workspace_bytes(const gbs_problem* pb, int max_steps) {
   bytes += 8 * s.state_elems;             // acc
   bytes += s.media_elems * esz;           // b
   if (pb->precision == GBS_F32X2) bytes += 8 * (s.state_elems + 2 * s.media_elems);   // pair copies
+  if (pb->system == GBS_ACOUSTIC && pb->ndim == 3 && pb->precision == GBS_F32_STATE_F64_COMBINE)
+    bytes += tb3_workspace_bytes(s.state_elems);   // the 3D time-blocked passes' second level pair
   if (pb->enable_adjoint) {
     bytes += (size_t)(max_steps + 2 + 3) * s.state_elems * esz;
     if (pb->precision == GBS_F32_STATE_F64_COMBINE) bytes += 8 * s.media_elems;   // gradient pairs
@@ -670,6 +694,7 @@ gbs_status gbs_create(const gbs_problem* pb, const void* kappa, const void* rho,
                 lf_tma_encode(h->lf_tmap[1], h->L1, (int)q.n[0], (int)q.n[1], (int)q.n[2], h->F, h->R) == 0;
   }
   h->fw = fused_create();
+  h->tb3 = tb3_create();
   if (h->system == GBS_ONEWAY_SPECTRAL && spectral_setup() < 0) {
     fail(h, GBS_ERR_CUDA, "the spectral kernel cannot get its shared memory");
     return bail(GBS_ERR_CUDA);
@@ -859,15 +884,16 @@ gbs_status gbs_step_partial(gbs_handle h, const void* y_in, double* partial, dou
   // problems whose slot has none of the selected sequences contribute zero
   CK(h, cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)h->state_elems, h->stream));
   const bool fused = use_fused(h, p) && !h->ds;
-  if (fused && h->fused_mask != seq_mask) {   // plan the time-blocked kernel for these sequences
+  if (fused && h->fw_ready && h->fused_mask != seq_mask) {   // plan the time-blocked kernel for these sequences
     h->fused_mask = seq_mask;
     if ((st = prepare_fused(h)) != GBS_OK) return st;
   }
   p.seq_mask = seq_mask;
   p.partial = 1;
   p.acc = partial;
-  const int n = fused && h->fw_ready ? fused_partial_step(h->fw, p, y_in, partial, h->stream, h->d_err)
-                                     : plain_macro_step(p, y_in, const_cast<void*>(y_in), h->stream);
+  const int n = fused && h->fw_ready    ? fused_partial_step(h->fw, p, y_in, partial, h->stream, h->d_err)
+                : fused && h->tb3_ready ? tb3_macro_step(h->tb3, p, y_in, const_cast<void*>(y_in), h->stream)
+                                        : plain_macro_step(p, y_in, const_cast<void*>(y_in), h->stream);
   if (n < 0) return fail(h, GBS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += n;
   return GBS_OK;
@@ -1013,7 +1039,13 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
       StepPlan p;
       gbs_status st = build_plan(h, &p);
       if (st != GBS_OK) return st;
-      if (!fused_supported(p, h->probs.data()))
+      SlotDev sd[GBS_MAX_SLOTS];
+      std::memset(sd, 0, sizeof sd);
+      for (int i = 0; i < GBS_MAX_SLOTS; ++i) {
+        sd[i].m = h->slots[i].m;
+        for (int k = 0; k < h->slots[i].m; ++k) sd[i].steps[k] = h->slots[i].steps[k];
+      }
+      if (!fused_supported(p, h->probs.data()) && !tb3_supported(p, h->probs.data(), sd, GBS_MAX_SLOTS))
         return fail(h, GBS_ERR_INVALID, "the time-blocked kernel does not support this problem");
     }
     h->opt_kernel = (int)value;
@@ -1026,6 +1058,11 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
   } else if (!std::strcmp(name, "hseg")) {
     if (value < 16 || value > 65536) return fail(h, GBS_ERR_INVALID, "hseg must be in [16, 65536]");
     h->opt_hseg = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
+  } else if (!std::strcmp(name, "zseg")) {
+    if (value < 1 || value > 65536) return fail(h, GBS_ERR_INVALID, "zseg must be in [1, 65536]");
+    h->opt_zseg = (int)value;
     gbs_status st = prepare_fused(h);
     if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "tmax")) {
@@ -1080,6 +1117,7 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "check_stability")) *value = h->opt_check_stability;
   else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
   else if (!std::strcmp(name, "hseg")) *value = h->opt_hseg;
+  else if (!std::strcmp(name, "zseg")) *value = h->opt_zseg;
   else if (!std::strcmp(name, "tmax")) *value = h->opt_tmax ? h->opt_tmax : fused_max_levels();
   else if (!std::strcmp(name, "schedule")) *value = h->opt_schedule;
   else if (!std::strcmp(name, "tma")) *value = tma_in_use(h) ? 1 : 0;

@@ -72,3 +72,16 @@ def test_autotune_picks_the_plain_kernels_when_faster(tmp_path):
     s3 = FakeSolver()
     r3 = A.autotune(s3, cache=False, timer=lambda: _cost(s3.opts, plain_cost=-1.0), key="x", plain=False)
     assert r3["options"]["kernel"] == FUSED
+
+
+def test_autotune_3d_varies_only_the_z_segment(tmp_path):
+    s = FakeSolver()
+    s.ndim = 3
+    s.opts["zseg"] = 128
+    calls = []
+    cost = lambda o: 10.0 if o["kernel"] == PLAIN else abs(o["zseg"] - 64) / 64.0
+    timer = lambda: (calls.append(dict(s.opts)), cost(s.opts))[1]
+    r = A.autotune(s, cache=str(tmp_path / "t.json"), timer=timer, key="w3")
+    assert r["options"] == {"zseg": 64, "kernel": FUSED}
+    assert len(calls) == len(A.DEFAULT_SPACE_3D["zseg"]) + 1
+    assert all(c["hseg"] == 256 and c["tmax"] == 4 for c in calls)   # the 2D knobs stay untouched
