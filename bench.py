@@ -372,6 +372,10 @@ def run_gpu(args):
         sol.set_option("schedule", args.schedule)
     if args.zseg:
         sol.set_option("zseg", args.zseg)
+    if args.seqfuse != -1:
+        sol.set_option("seqfuse", args.seqfuse)
+    if args.seqgroup != -1:
+        sol.set_option("seqgroup", args.seqgroup)
     if args.tma != -1:
         sol.set_option("tma", args.tma)
     if args.combine == "pairs":
@@ -460,7 +464,8 @@ def run_gpu(args):
             "frac": achieved / peak if achieved else None, "traffic": traffic,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
             "kernel": ("3D time-blocked pass (k_tb3)" if len(cfg["shape_zyx"]) == 3 else "fused pass (k_passes)")
-                      if fused else "tiled leap-frog step (k_lf_tiled)",
+                      if fused else ("sequence-fused tiled leap-frog step (k_lf_tiled_seqs)" if sol.get_option("seqfuse")
+                                     else "tiled leap-frog step (k_lf_tiled)"),
             "avg_launch_ms": launch_s * 1e3 if nl else None,
             "achieved_basis": "algorithmic minimum: y_in, kappa, rho read and y_out written once per macro-step "
                               f"({ALG_MIN_BYTES_PER_POINT[len(cfg['shape_zyx'])] * esz / 4:.0f} B per grid point)",
@@ -497,6 +502,8 @@ def run_gpu(args):
         cfg.update({"combine_dtype": ("f32 pairs (double-single, ~48-bit)" if fused and args.combine == "pairs"
                                       else "f64"),
                     "kernel": roof["kernel"], "l2": "flushed (256 MB write) before every timed step",
+                    "sequence_fused": {"in_use": int(sol.get_option("seqfuse")),
+                                       "group": int(sol.get_option("seqgroup"))},
                     "parallelism": f"replicas x{ws}"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -857,6 +864,9 @@ def main():
     ap.add_argument("--f32x2", action="store_true", help="FP64 states computed in FP32 pairs (plain kernels)")
     ap.add_argument("--hseg", type=int, default=0, help="row-segment height of the time-blocked tiles (0: default)")
     ap.add_argument("--zseg", type=int, default=0, help="z-planes per block of the 3D time-blocked passes (0: default)")
+    ap.add_argument("--seqfuse", type=int, choices=[-1, 0, 1], default=-1,
+                    help="one-level kernels: all sequences of a level per launch (1), one (0), by dimension (-1)")
+    ap.add_argument("--seqgroup", type=int, default=-1, help="most sequences per fused one-level launch (-1: default)")
     ap.add_argument("--tmax", type=int, default=0, help="most leap-frog levels per time-blocked pass (0: default)")
     ap.add_argument("--schedule", type=int, default=-1, help="work-queue order of the time-blocked kernel (-1: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

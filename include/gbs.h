@@ -292,7 +292,17 @@ gbs_status gbs_norms(gbs_handle h, const void* a, const void* b, double* out);
  * bit for bit; it needs a second pair of level buffers (gbs_workspace_bytes counts them),
  * allocated when it is selected.  On GB300 the 3D pass kernel is slower than the one-level
  * kernel, so GBS_KERNEL_AUTO keeps the latter in 3D.  "zseg" = z-planes per block of the 3D
- * pass kernel (1..65536, default 128).  "hseg" = row-segment height of
+ * pass kernel (1..65536, default 128).  "seqfuse" = -1/0/1 (default -1: on in 2D, off in 3D,
+ * where it measured slower on GB300): where the one-level
+ * kernels run FP32 2D/3D acoustics, give every sequence its own pair of level buffers (2 m
+ * states, m the scheme's sequence count, allocated when the weights are set and not counted by
+ * gbs_workspace_bytes) so that one launch per leap-frog level advances all sequences that have
+ * that level, reading f0 and the media from DRAM once for all of them; the results are those of
+ * one sequence per launch up to the order of the FP64 combine's terms (sequences finish in
+ * step-count order).  Without the memory the step runs one sequence per launch;
+ * gbs_get_option answers 1 only where the fused launches are in use.  "seqgroup" = most
+ * sequences per fused launch (-1 = by dimension, the default: all of a level's in 2D, 4 in 3D,
+ * where a launch's z-neighbour planes must stay in the L2 cache; 0 = all; 1..16).  "hseg" = row-segment height of
  * the 2D time-blocked tiles (16..65536, default 256), "tmax" = most leap-frog levels per
  * time-blocked pass (0 = the kernel's largest, 4; or 2), "schedule" = order of the
  * time-blocked work queue (0 = longest remaining chain of passes first, the default;

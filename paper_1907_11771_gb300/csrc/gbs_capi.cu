@@ -14,6 +14,7 @@
 
 #include "gbs_dd.h"
 #include "gbs_internal.h"
+#include "gbs_seqfuse.h"
 #include "gbs_tb3.h"
 #include "gbs_weights.h"
 
@@ -94,6 +95,15 @@ struct gbs_ctx {
   bool fw_ready = false;
   Tb3Work* tb3 = nullptr;                 // 3D time-blocked passes: tiles and second level pair
   bool tb3_ready = false;
+  // sequence-fused one-level steps (FP32 2D/3D acoustics on the one-level kernels): a level pair
+  // per sequence, and the tensor map over all of them
+  void* Lms = nullptr;
+  int64_t Lms_elems = 0;
+  bool ms_ready = false;
+  bool ms_tma = false;
+  alignas(64) unsigned char ms_tmap[128] = {};
+  int opt_seqfuse = -1;                   // -1: by dimension (2D on; 3D off, measured slower on GB300)
+  int opt_seqgroup = -1;                  // most sequences per fused launch: -1 = by dimension
   // execution
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
@@ -259,6 +269,8 @@ void free_all(gbs_ctx* h) {
   h->fw = nullptr;
   tb3_destroy(h->tb3);
   h->tb3 = nullptr;
+  if (h->Lms) cudaFree(h->Lms);
+  h->Lms = nullptr;
 }
 
 struct Sizes {
@@ -438,8 +450,65 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
   return GBS_OK;
 }
 
-// (Re)build the time-blocked schedule when it applies (set-up time: may allocate).
+gbs_status prepare_time_blocked(gbs_ctx* h);
+
+// The sequence-fused one-level step's level pairs (set-up time: may allocate), where the
+// one-level kernels run FP32 2D/3D acoustics; without the memory for them the step runs one
+// sequence per launch.
+gbs_status prepare_seqfuse(gbs_ctx* h) {
+  const bool was = h->ms_ready;
+  h->ms_ready = false;
+  const bool want = h->opt_seqfuse > 0 || (h->opt_seqfuse < 0 && h->ndim == 2);
+  bool applies = want && h->system == GBS_ACOUSTIC && h->ndim >= 2 && h->esz == 4 && !h->ds &&
+                 !h->f64 && !(h->opt_kernel != GBS_KERNEL_PLAIN && (h->fw_ready || h->tb3_ready));
+  for (int i = 0; i < GBS_MAX_SLOTS && applies; ++i)   // distinct step counts within every slot
+    for (int a = 0; a < h->slots[i].m && applies; ++a)
+      for (int b = a + 1; b < h->slots[i].m; ++b)
+        if (h->slots[i].steps[a] == h->slots[i].steps[b]) applies = false;
+  StepPlan p;
+  if (!applies || build_plan(h, &p) != GBS_OK) {
+    h->err.clear();
+    if (h->Lms && !applies) {
+      CK(h, cudaStreamSynchronize(h->stream));
+      cudaFree(h->Lms);
+      h->Lms = nullptr;
+      h->Lms_elems = 0;
+    }
+    if (was) ++h->sched_version;
+    return GBS_OK;
+  }
+  const int64_t need = 2 * (int64_t)p.max_m * h->state_elems;
+  if (h->Lms_elems < need) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->Lms) cudaFree(h->Lms);
+    h->Lms = nullptr;
+    h->Lms_elems = 0;
+    if (cudaMalloc(&h->Lms, sizeof(float) * (size_t)need) != cudaSuccess) {
+      cudaGetLastError();   // not enough memory: one sequence per launch
+      h->Lms = nullptr;
+      ++h->sched_version;
+      return GBS_OK;
+    }
+    h->Lms_elems = need;
+  }
+  h->ms_tma = false;
+  if (h->batch == 1 && h->probs[0].n[0] % 4 == 0) {
+    const ProbDev& q = h->probs[0];
+    h->ms_tma = lf_tma_encode(h->ms_tmap, h->Lms, (int)q.n[0], (int)q.n[1], (int)q.n[2], h->F * 2 * p.max_m, h->R) == 0;
+  }
+  h->ms_ready = true;
+  ++h->sched_version;
+  return GBS_OK;
+}
+
 gbs_status prepare_fused(gbs_ctx* h) {
+  gbs_status st = prepare_time_blocked(h);
+  if (st != GBS_OK) return st;
+  return prepare_seqfuse(h);
+}
+
+// (Re)build the time-blocked schedule when it applies (set-up time: may allocate).
+gbs_status prepare_time_blocked(gbs_ctx* h) {
   h->fw_ready = false;
   h->tb3_ready = false;
   if (h->opt_kernel == GBS_KERNEL_PLAIN) return GBS_OK;
@@ -495,6 +564,19 @@ gbs_status set_H(gbs_ctx* h, const double* H) {
   return upload_hk(h);
 }
 
+// Sequences per fused launch in 3D, where each launch's z-neighbour planes stay in the cache
+// only while the group is small.
+constexpr int kSeqGroup3D = 4;
+
+// The one-level path: sequence-fused where its level pairs are ready.
+int plain_step(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo, cudaStream_t s) {
+  if (!h->ms_ready) return plain_macro_step(p, yi, yo, s);
+  const bool map = h->ms_tma && (h->opt_tma == 1 || (h->opt_tma < 0 && h->ndim == 3));
+  const int group = h->opt_seqgroup >= 0 ? h->opt_seqgroup : h->ndim == 3 ? kSeqGroup3D : 0;
+  const SeqLevels lv{h->Lms, h->state_elems, map ? h->ms_tmap : nullptr, group};
+  return plain_macro_step_seqfused(p, lv, yi, yo, s);
+}
+
 bool use_fused(gbs_ctx* h, const StepPlan&) {
   return h->opt_kernel != GBS_KERNEL_PLAIN && (h->fw_ready || h->tb3_ready);
 }
@@ -503,7 +585,7 @@ bool use_fused(gbs_ctx* h, const StepPlan&) {
 int enqueue_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo, cudaStream_t s, int kernel) {
   if (kernel == GBS_KERNEL_FUSED && h->tb3_ready) return tb3_macro_step(h->tb3, p, yi, yo, s);
   if (kernel == GBS_KERNEL_FUSED) return fused_macro_step(h->fw, p, yi, yo, s, h->d_err);
-  return plain_macro_step(p, yi, yo, s);
+  return plain_step(h, p, yi, yo, s);
 }
 
 gbs_status run_macro(gbs_ctx* h, const StepPlan& p, const void* yi, void* yo) {
@@ -893,7 +975,7 @@ gbs_status gbs_step_partial(gbs_handle h, const void* y_in, double* partial, dou
   p.acc = partial;
   const int n = fused && h->fw_ready    ? fused_partial_step(h->fw, p, y_in, partial, h->stream, h->d_err)
                 : fused && h->tb3_ready ? tb3_macro_step(h->tb3, p, y_in, const_cast<void*>(y_in), h->stream)
-                                        : plain_macro_step(p, y_in, const_cast<void*>(y_in), h->stream);
+                                        : plain_step(h, p, y_in, const_cast<void*>(y_in), h->stream);
   if (n < 0) return fail(h, GBS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += n;
   return GBS_OK;
@@ -1060,6 +1142,14 @@ gbs_status gbs_set_option(gbs_handle h, const char* name, int64_t value) {
     h->opt_hseg = (int)value;
     gbs_status st = prepare_fused(h);
     if (st != GBS_OK) return st;
+  } else if (!std::strcmp(name, "seqgroup")) {
+    if (value < -1 || value > GBS_MAX_SEQ) return fail(h, GBS_ERR_INVALID, "seqgroup must be in [-1, %d]", GBS_MAX_SEQ);
+    h->opt_seqgroup = (int)value;
+  } else if (!std::strcmp(name, "seqfuse")) {
+    if (value != 0 && value != 1) return fail(h, GBS_ERR_INVALID, "seqfuse must be 0 or 1");
+    h->opt_seqfuse = (int)value;
+    gbs_status st = prepare_fused(h);
+    if (st != GBS_OK) return st;
   } else if (!std::strcmp(name, "zseg")) {
     if (value < 1 || value > 65536) return fail(h, GBS_ERR_INVALID, "zseg must be in [1, 65536]");
     h->opt_zseg = (int)value;
@@ -1118,6 +1208,8 @@ gbs_status gbs_get_option(gbs_handle h, const char* name, int64_t* value) {
   else if (!std::strcmp(name, "time_kernels")) *value = h->opt_time_kernels;
   else if (!std::strcmp(name, "hseg")) *value = h->opt_hseg;
   else if (!std::strcmp(name, "zseg")) *value = h->opt_zseg;
+  else if (!std::strcmp(name, "seqfuse")) *value = h->ms_ready ? 1 : 0;
+  else if (!std::strcmp(name, "seqgroup")) *value = h->opt_seqgroup >= 0 ? h->opt_seqgroup : h->ndim == 3 ? kSeqGroup3D : 0;
   else if (!std::strcmp(name, "tmax")) *value = h->opt_tmax ? h->opt_tmax : fused_max_levels();
   else if (!std::strcmp(name, "schedule")) *value = h->opt_schedule;
   else if (!std::strcmp(name, "tma")) *value = tma_in_use(h) ? 1 : 0;

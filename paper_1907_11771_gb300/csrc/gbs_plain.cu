@@ -20,6 +20,7 @@
 
 #include "gbs_ds.cuh"
 #include "gbs_internal.h"
+#include "gbs_seqfuse.h"
 #include "gbs_stencil.cuh"
 
 namespace gbs {
@@ -349,29 +350,57 @@ __device__ __forceinline__ unsigned smem_u32(const void* ptr) {
 }
 constexpr long long kTmaSpin = 1ll << 22;   // try_wait polls before a copy counts as lost
 
-template <typename T, int DIM, int R, bool kVec, bool kTma>
-__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
-    k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n,
-               const __grid_constant__ CUtensorMap tmap) {
-  constexpr int Hh = kTileY + 2 * R;
-  // staged columns: HX on each side of the tile (>= R and a whole number of 16-byte vectors)
-  constexpr int HX = 4, WS = kTileX + 2 * HX;
-  // 128-byte aligned: the tensor copy's destination (its box is [3][Hh][WS], x fastest)
-  __shared__ __align__(128) T sh[3][Hh][WS];
-  __shared__ __align__(8) unsigned long long tma_bar;
-  // problem of this block (binary search over the tiled-grid offsets)
+// First and last sequence to finish among the slot's scheduled sequences when all of them
+// advance level by level together (a sequence-fused step): by step count, ties in index order.
+__device__ __forceinline__ void seq_first_last_by_steps(const StepPlan& p, const SlotDev& s, int k, bool& first,
+                                                        bool& last) {
+  const unsigned msk = p.seq_mask & ((1u << s.m) - 1u);
+  const int N = s.steps[k];
+  first = true;
+  last = !p.partial;
+  for (int i = 0; i < s.m; ++i) {
+    if (!((msk >> i) & 1u) || i == k) continue;
+    if (s.steps[i] < N || (s.steps[i] == N && i < k)) first = false;
+    if (s.steps[i] > N || (s.steps[i] == N && i > k)) last = false;
+  }
+}
+
+// kMulti: the sequence-fused variant (several sequences per launch, own level pairs), given one
+// resident block per SM less for the registers its loop over the sequences keeps live
+// staging tile of k_lf_tiled: HX columns on each side of the tile (>= R and a whole number of
+// 16-byte vectors), R rows above and below
+template <typename T, int R>
+struct LfTile {
+  static constexpr int Hh = kTileY + 2 * R, HX = 4, WS = kTileX + 2 * HX;
+  using Arr = T[3][Hh][WS];
+};
+
+// Problem of a tiled-grid block (binary search over the tiled-grid offsets).
+__device__ __forceinline__ int tiled_problem(const StepPlan& p, int64_t blk) {
   int lo = 0, hi = p.batch - 1;
-  const int64_t blk = blockIdx.x;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (p.probs[mid].tblk_begin <= blk) lo = mid;
     else hi = mid - 1;
   }
+  return lo;
+}
+
+// One leap-frog level n of sequence k over one tile (the body of k_lf_tiled): stage the tile of
+// y_n, then update each of the thread's rows.  `uses` counts the earlier copies on tma_bar in
+// this block (0: the barrier is initialised here).  Returns false when a tensor copy did not
+// complete in time (GBS_ERR_TIMEOUT latched; the block must stop).
+template <typename T, int DIM, int R, bool kVec, bool kTma>
+__device__ __forceinline__ bool lf_tile_level(const StepPlan& p, const T* y_in, typename out_of<T>::type* y_out,
+                                              int k, int n, const CUtensorMap& tmap, const SeqLevels& lv,
+                                              typename LfTile<T, R>::Arr& sh, unsigned long long& tma_bar,
+                                              int uses, int lo, int64_t blk) {
+  constexpr int Hh = LfTile<T, R>::Hh, HX = LfTile<T, R>::HX, WS = LfTile<T, R>::WS;
   const ProbDev& q = p.probs[lo];
   const SlotDev& s = p.slots[q.slot];
-  if (k >= s.m) return;
+  if (k >= s.m) return true;
   const int N = s.steps[k];
-  if (n > N) return;
+  if (n > N) return true;
   const int tile = (int)(blk - q.tblk_begin);
   const int tx = tile % q.tiles_x;
   const int rest = tile / q.tiles_x;
@@ -387,8 +416,9 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   const Off plane = (Off)z * nx * ny;
   T h, h2;
   step_sizes(p, lo, k, h, h2);
-  T* const L0 = static_cast<T*>(p.L0) + q.state_off;
-  T* const L1 = static_cast<T*>(p.L1) + q.state_off;
+  // level buffers: the handle's pair, or sequence k's own pair in a sequence-fused step
+  T* const L0 = (lv.base ? static_cast<T*>(lv.base) + (2 * k) * lv.stride : static_cast<T*>(p.L0)) + q.state_off;
+  T* const L1 = (lv.base ? static_cast<T*>(lv.base) + (2 * k + 1) * lv.stride : static_cast<T*>(p.L1)) + q.state_off;
   const T* cur = (n & 1) ? L1 : L0;
   T* dst = (n & 1) ? L0 : L1;                          // y_(n+1) overwrites y_(n-1)
   const T* prev = (n == 1) ? (y_in + q.state_off) : dst;
@@ -492,12 +522,16 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
     if (inside) {
       const unsigned bar = smem_u32(&tma_bar);
       const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
-      if (lead) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      if (uses == 0) {
+        if (lead) {
+          asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+          asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+      } else if (lead) {   // the tile's earlier reads (ordered by the caller's barrier) before the copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      __syncthreads();
       if (lead) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"((unsigned)sizeof(sh))
@@ -505,7 +539,8 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(&sh[0][0][0])),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 - HX), "r"(y0 - R), "r"(z), "r"(0), "r"(bar)
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 - HX), "r"(y0 - R), "r"(z),
+            "r"(lv.base ? (2 * k + (n & 1)) * F : 0), "r"(bar)
             : "memory");
       }
       fetch_row(0);
@@ -513,14 +548,14 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       for (long long it = 0; it < kTmaSpin && !ready; ++it)
         asm volatile(
             "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, P;\n\t}"
             : "=r"(ready)
-            : "r"(bar)
+            : "r"(bar), "r"((unsigned)(uses & 1))
             : "memory");
       if (__syncthreads_or(!ready)) {
         if (lead) atomicCAS(p.err, 0, (int)GBS_ERR_TIMEOUT);
-        return;
+        return false;
       }
     } else {
       stage_vectors();
@@ -558,10 +593,11 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
   const T idx = T(q.inv_dx[0]);
   const T idy = kInc ? T(q.rr[1]) : T(q.inv_dx[1]);
   const T idz = kInc ? T(q.rr[2]) : T(q.inv_dx[2]);
-  if (x >= nx) return;
+  if (x >= nx) return true;
   const double c = s.c[k];
   bool first, last;
-  seq_first_last(p, k, s.m, first, last);
+  if (lv.base) seq_first_last_by_steps(p, s, k, first, last);
+  else seq_first_last(p, k, s.m, first, last);
 #pragma unroll
   for (int i = 0; i < kTileRows; ++i) {
     const int ly = threadIdx.y + 8 * i;
@@ -658,6 +694,37 @@ __global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
       }
     }
   }
+  return true;
+}
+
+template <typename T, int DIM, int R, bool kVec, bool kTma>
+__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
+    k_lf_tiled(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, int k, int n,
+               const __grid_constant__ CUtensorMap tmap) {
+  // 128-byte aligned: the tensor copy's destination (its box is [3][Hh][WS], x fastest)
+  __shared__ __align__(128) typename LfTile<T, R>::Arr sh;
+  __shared__ __align__(8) unsigned long long tma_bar;
+  const int64_t blk = blockIdx.x;
+  lf_tile_level<T, DIM, R, kVec, kTma>(p, y_in, y_out, k, n, tmap, SeqLevels{nullptr, 0, nullptr}, sh, tma_bar, 0,
+                                       tiled_problem(p, blk), blk);
+}
+
+// The sequence-fused step: level n of every sequence of kmask (na of them), each from its own
+// level pair (lv), one block per tile and sequence with the sequence index running fastest, so
+// that the na blocks of a tile run side by side and their reads of the tile's f0 and media after
+// the first are served by the cache.  At most one scheduled sequence finishes at level n (step
+// counts are distinct), so the blocks' combine updates never meet.
+template <typename T, int DIM, int R, bool kVec, bool kTma>
+__global__ void __launch_bounds__(256, lf_min_blocks<T, DIM, R>())
+    k_lf_tiled_seqs(const StepPlan p, const T* y_in, typename out_of<T>::type* y_out, uint32_t kmask, int na, int n,
+                    const __grid_constant__ CUtensorMap tmap, const SeqLevels lv) {
+  __shared__ __align__(128) typename LfTile<T, R>::Arr sh;
+  __shared__ __align__(8) unsigned long long tma_bar;
+  const int64_t blk = blockIdx.x / na;
+  uint32_t km = kmask;
+  for (int i = blockIdx.x % na; i > 0; --i) km &= km - 1;   // the (blockIdx.x mod na)-th sequence
+  lf_tile_level<T, DIM, R, kVec, kTma>(p, y_in, y_out, __ffs(km) - 1, n, tmap, lv, sh, tma_bar, 0,
+                                       tiled_problem(p, blk), blk);
 }
 
 // Tiled leap-frog step for 2D/3D acoustics in FP32 pairs (GBS_F32X2), two pair values per
@@ -1421,13 +1488,68 @@ __global__ void k_inject(T* lam, const int64_t* idx, int n, const T* resid, int6
 const CUtensorMap kNoTensorMap{};
 
 template <typename T, int SYS, int DIM, int R>
-int macro_step_t(const StepPlan& p, const void* y_in_v, void* y_out_v, cudaStream_t st) {
+int macro_step_t(const StepPlan& p, const SeqLevels& lv, const void* y_in_v, void* y_out_v, cudaStream_t st) {
   const T* y_in = static_cast<const T*>(y_in_v);
   auto* y_out = static_cast<typename out_of<T>::type*>(y_out_v);
   const dim3 grid((unsigned)p.total_blocks), block(kPlainBlock);
   int launches = 0;
   k_f0<T, SYS, DIM, R><<<grid, block, 0, st>>>(p, y_in);
   ++launches;
+  if constexpr (std::is_same<T, float>::value && SYS == SYS_ACOUSTIC && DIM >= 2) {
+    if (lv.base) {
+      // sequence-fused: every scheduled sequence has its own level pair; the Forward-Euler
+      // levels, then one launch per leap-frog level n advancing every sequence that has it
+      int nmax = 0;
+      for (int k = 0; k < p.max_m; ++k) {
+        if (!((p.seq_mask >> k) & 1u)) continue;
+        StepPlan q = p;
+        q.L1 = static_cast<float*>(lv.base) + (2 * k + 1) * lv.stride;
+        k_fe<T, SYS, DIM><<<grid, block, 0, st>>>(q, y_in, k);
+        ++launches;
+        nmax = std::max(nmax, p.max_steps_k[k]);
+      }
+      for (int n = 1; n <= nmax; ++n) {
+        uint32_t all = 0;
+        for (int k = 0; k < p.max_m; ++k)
+          if (((p.seq_mask >> k) & 1u) && p.max_steps_k[k] >= n) all |= 1u << k;
+        while (all) {
+          // the next group of at most lv.group sequences
+          uint32_t kmask = 0;
+          for (int c = 0; all && (lv.group <= 0 || c < lv.group); ++c) {
+            kmask |= all & (0u - all);
+            all &= all - 1;
+          }
+          double bytes = 0.0;
+          int64_t any = 0;
+          for (int k = 0; k < p.max_m; ++k) {
+            if (!((kmask >> k) & 1u)) continue;
+            const int64_t pts = p.active_pts[k * (GBS_MAX_STEPS + 1) + n];
+            // per sequence: y_(n-1) and y_n read, y_(n+1) written; f0 and the media once per
+            // point for the group (the problems of its largest sequence count, exact for a
+            // single problem or one weight slot)
+            bytes += 12.0 * p.F * (double)pts;
+            any = std::max(any, pts);
+          }
+          bytes += 4.0 * (p.F + 2) * (double)any;
+          const int na = __builtin_popcount(kmask);
+          const int u = timing_begin(p, st);
+          if (p.nx_vec && lv.tmap)
+            k_lf_tiled_seqs<T, DIM, R, true, true><<<(unsigned)(p.total_tiles * na), dim3(kTileX, 8), 0, st>>>(
+                p, y_in, y_out, kmask, na, n, *static_cast<const CUtensorMap*>(lv.tmap), lv);
+          else if (p.nx_vec)
+            k_lf_tiled_seqs<T, DIM, R, true, false><<<(unsigned)(p.total_tiles * na), dim3(kTileX, 8), 0, st>>>(
+                p, y_in, y_out, kmask, na, n, kNoTensorMap, lv);
+          else
+            k_lf_tiled_seqs<T, DIM, R, false, false><<<(unsigned)(p.total_tiles * na), dim3(kTileX, 8), 0, st>>>(
+                p, y_in, y_out, kmask, na, n, kNoTensorMap, lv);
+          timing_end(p, u, st, p.tev ? bytes : 0.0);
+          ++launches;
+        }
+      }
+      if (cudaPeekAtLastError() != cudaSuccess) return -1;
+      return launches;
+    }
+  }
   for (int k = 0; k < p.max_m; ++k) {
     if (!((p.seq_mask >> k) & 1u)) continue;   // a partial step leaves this sequence to another rank
     k_fe<T, SYS, DIM><<<grid, block, 0, st>>>(p, y_in, k);
@@ -1518,18 +1640,18 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
 }
 
 template <typename T>
-int macro_step_sys(const StepPlan& p, const void* yi, void* yo, cudaStream_t s) {
+int macro_step_sys(const StepPlan& p, const SeqLevels& lv, const void* yi, void* yo, cudaStream_t s) {
   if (p.system == GBS_WAVE1D) {
-    return p.R == 2 ? macro_step_t<T, SYS_WAVE1D, 1, 2>(p, yi, yo, s)
-                    : macro_step_t<T, SYS_WAVE1D, 1, 3>(p, yi, yo, s);
+    return p.R == 2 ? macro_step_t<T, SYS_WAVE1D, 1, 2>(p, lv, yi, yo, s)
+                    : macro_step_t<T, SYS_WAVE1D, 1, 3>(p, lv, yi, yo, s);
   }
   switch (p.ndim * 10 + p.R) {
-    case 12: return macro_step_t<T, SYS_ACOUSTIC, 1, 2>(p, yi, yo, s);
-    case 13: return macro_step_t<T, SYS_ACOUSTIC, 1, 3>(p, yi, yo, s);
-    case 22: return macro_step_t<T, SYS_ACOUSTIC, 2, 2>(p, yi, yo, s);
-    case 23: return macro_step_t<T, SYS_ACOUSTIC, 2, 3>(p, yi, yo, s);
-    case 32: return macro_step_t<T, SYS_ACOUSTIC, 3, 2>(p, yi, yo, s);
-    case 33: return macro_step_t<T, SYS_ACOUSTIC, 3, 3>(p, yi, yo, s);
+    case 12: return macro_step_t<T, SYS_ACOUSTIC, 1, 2>(p, lv, yi, yo, s);
+    case 13: return macro_step_t<T, SYS_ACOUSTIC, 1, 3>(p, lv, yi, yo, s);
+    case 22: return macro_step_t<T, SYS_ACOUSTIC, 2, 2>(p, lv, yi, yo, s);
+    case 23: return macro_step_t<T, SYS_ACOUSTIC, 2, 3>(p, lv, yi, yo, s);
+    case 32: return macro_step_t<T, SYS_ACOUSTIC, 3, 2>(p, lv, yi, yo, s);
+    case 33: return macro_step_t<T, SYS_ACOUSTIC, 3, 3>(p, lv, yi, yo, s);
   }
   return -1;
 }
@@ -1611,10 +1733,16 @@ int plain_macro_step(const StepPlan& p, const void* y_in, void* y_out, cudaStrea
       q.b = p.ds_b;
       extra += 2;
     }
-    const int l = macro_step_sys<dsf>(q, p.ds_y0, y_out, s);
+    const int l = macro_step_sys<dsf>(q, SeqLevels{nullptr, 0, nullptr}, p.ds_y0, y_out, s);
     return l < 0 ? l : l + extra;
   }
-  return p.f64 ? macro_step_sys<double>(p, y_in, y_out, s) : macro_step_sys<float>(p, y_in, y_out, s);
+  const SeqLevels none{nullptr, 0, nullptr};
+  return p.f64 ? macro_step_sys<double>(p, none, y_in, y_out, s) : macro_step_sys<float>(p, none, y_in, y_out, s);
+}
+
+int plain_macro_step_seqfused(const StepPlan& p, const SeqLevels& lv, const void* y_in, void* y_out, cudaStream_t s) {
+  if (p.system != GBS_ACOUSTIC || p.ndim < 2 || p.f64 || p.ds || !lv.base) return plain_macro_step(p, y_in, y_out, s);
+  return macro_step_sys<float>(p, lv, y_in, y_out, s);
 }
 
 int inject(int f64, void* lam, const int64_t* idx, int n, const void* values, int64_t n_valid, int* err,

@@ -36,6 +36,16 @@ def oracle_scheme(scheme):
     return steps, OW.to_fp64(c)
 
 
+def fp32_floor(scheme, n_macro):
+    """4 x 2^-24 x sqrt(sum_k c_k^2 (N_k + 1)) x sqrt(M): the FP32 rounding floor of M macro-steps
+    (four roundings of 2^-24 per leap-frog update, independent across the N_k + 1 updates of a
+    sequence and across macro-steps, amplified by the weights c_k)."""
+    import math
+    steps, c = oracle_scheme(scheme)
+    amp = math.sqrt(sum(float(ck) ** 2 * (n + 1) for n, ck in zip(steps, c)))
+    return 4 * 2.0 ** -24 * amp * math.sqrt(n_macro)
+
+
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()

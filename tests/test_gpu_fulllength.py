@@ -41,7 +41,7 @@ from paper_1907_11771_gb300 import binding as B
 from paper_1907_11771_gb300 import inputs
 from paper_1907_11771_gb300 import schemes as S
 from paper_1907_11771_gb300.solver import GBSSolver
-from tests.gpu_common import oracle_scheme, rel_l2
+from tests.gpu_common import fp32_floor, oracle_scheme, rel_l2
 
 pytestmark = pytest.mark.gpu
 F64, X2, F32 = B.GBS_F64, B.GBS_F32X2, B.GBS_F32_STATE_F64_COMBINE
@@ -55,13 +55,6 @@ def _built():
     build.build()
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-
-
-def fp32_floor(scheme, n_macro):
-    """4 x 2^-24 x sqrt(sum_k c_k^2 (N_k + 1)) x sqrt(M): the FP32 rounding floor (module doc)."""
-    steps, c = oracle_scheme(scheme)
-    amp = math.sqrt(sum(float(ck) ** 2 * (n + 1) for n, ck in zip(steps, c)))
-    return 4 * 2.0 ** -24 * amp * math.sqrt(n_macro)
 
 
 def symbol(order, th):
