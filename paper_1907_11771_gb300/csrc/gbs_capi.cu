@@ -436,8 +436,10 @@ gbs_status build_plan(gbs_ctx* h, StepPlan* p) {
     }
   }
   p->active_pts = h->active_pts.data();
-  // plain leap-frog step: read y_(n-1) and y_n, write y_(n+1) (F fields each), read the media
-  p->unit_bytes = (double)h->esz * (3.0 * h->F + (h->system == GBS_ACOUSTIC ? 2.0 : 0.0));
+  // plain leap-frog step: read y_(n-1) and y_n, write y_(n+1) (F fields each), read the media,
+  // and FP32 states (increment form) read f0
+  p->unit_bytes = (double)h->esz * (3.0 * h->F + (h->system == GBS_ACOUSTIC ? 2.0 : 0.0) +
+                                    (h->esz == 4 && !h->ds ? h->F : 0.0));
   // adjoint reverse step: read M[j+1] and M[j+2], write M[j] (F fields each), the media, the
   // forward level's velocities (divergence for the gradient), FP64 gradient read and write
   p->adj_unit_bytes = (double)h->esz * (3.0 * h->F + 2.0 + h->ndim) + 16.0;

@@ -138,7 +138,7 @@ def test_adjoint_of_a_pair_handle_is_the_fp64_adjoint():
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
-def test_time_blocked_kernel_refused_for_fp64_states_and_3d():
+def test_time_blocked_kernel_refused_for_fp64_states_and_3d_pairs():
     for shape, prec in (((64, 64), F64), ((8, 40, 40), X2)):
         case = AcousticCase(shape, 6, prec)
         sol = case.solver()
