@@ -533,7 +533,8 @@ def run_adjoint(args):
     a checkpoint every C, then the backward sweep recomputing each segment and running the
     adjoint macro-steps; with --adj-snapshots S a binomial schedule of S stored states instead),
     2D acoustics n x n (default 1024^2), 4th-order FD, rho = 1, 16-Gaussian kappa, Gaussian
-    pressure source sigma = 8, 64 receivers on the row 3n/4, GBS_8,6 in FP32.  Counted work: M
+    pressure source sigma = 8, 64 receivers on the row 3n/4, GBS_8,6 in FP32 (--f64: FP64 states;
+    --f32x2: FP64 states in FP32 pairs, forward and adjoint in pair arithmetic).  Counted work: M
     forward plus M adjoint macro-steps of P x 143 updates; the checkpoint recomputation is
     overhead.  Observed data: a forward run of the same solver with a perturbed
     kappa (kappa + 0.05 x one more seeded Gaussian)."""
@@ -553,20 +554,25 @@ def run_adjoint(args):
     M, C = args.adj_macro, args.adj_checkpoint
     SN = args.adj_snapshots or None
     ckpt_desc = f"binomial checkpointing with {SN} stored states" if SN else f"checkpoint every {C}"
-    y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, 8.0, const_rho=True, dtype=np.float32)
+    prec = B.GBS_F64 if args.f64 else B.GBS_F32X2 if args.f32x2 else B.GBS_F32_STATE_F64_COMBINE
+    dt = np.float32 if prec == B.GBS_F32_STATE_F64_COMBINE else np.float64
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    esz = 4 if dt == np.float32 else 8
+    prec_name = {B.GBS_F64: "FP64", B.GBS_F32X2: "FP64 states in FP32 pairs"}.get(prec, "FP32")
+    y0, kappa, rho = inputs.acoustic_problem((n, n), 0, N_GAUSS, 8.0, const_rho=True, dtype=dt)
     bump = inputs.smooth_media((n, n), 1, 7, 1.0) - 1.0        # one more seeded Gaussian
     tk = torch.tensor(kappa.ravel(), device="cuda")
     tr = torch.tensor(rho.ravel(), device="cuda")
-    sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=4, precision=B.GBS_F32_STATE_F64_COMBINE,
+    sol = GBSSolver(B.GBS_ACOUSTIC, [(n, n)], [(1.0, 1.0)], fd_order=4, precision=prec,
                     kappa=tk, rho=tr, enable_adjoint=True)
     sol.set_scheme(S.GBS_8_6)
     H = H_FRACTION * sol.stability_limit()[0]
     rcv = torch.tensor(inputs.line_receivers(n, 64), device="cuda")
     y = torch.tensor(y0.ravel(), device="cuda")
     # observed data from the perturbed medium
-    k_true = torch.tensor((kappa + 0.05 * np.asarray(bump, dtype=np.float32)).ravel(), device="cuda")
+    k_true = torch.tensor((kappa + 0.05 * np.asarray(bump, dtype=dt)).ravel(), device="cuda")
     sol.set_media(k_true, tr)
-    data = torch.empty(M, rcv.numel(), dtype=torch.float32, device="cuda")
+    data = torch.empty(M, rcv.numel(), dtype=tdt, device="cuda")
     yy = y.clone()
     for m in range(M):
         sol.step(yy, yy, H, 1)
@@ -623,12 +629,12 @@ def run_adjoint(args):
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e = {"value": upd * args.steps / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": hy.numel() * 4 + hk.numel() * 4 + hd.numel() * 4, "d2h_bytes_per_step": hg.numel() * 8}
+           "h2d_bytes_per_step": (hy.numel() + hk.numel() + hd.numel()) * esz, "d2h_bytes_per_step": hg.numel() * 8}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": {4: "f32"}.get(esz, "f32x2" if args.f32x2 else "f64"), "data": "synthetic",
             "config": {"workload": (f"misfit gradient: 2D acoustics {n}x{n}, 4th-order FD, rho = 1, 64 receivers, "
-                                    f"GBS_8,6 FP32, {M} macro-steps, {ckpt_desc}; one step = forward + "
+                                    f"GBS_8,6 {prec_name}, {M} macro-steps, {ckpt_desc}; one step = forward + "
                                     f"checkpointed backward; updates counted: {M} forward + {M} adjoint macro-steps"),
                        "shapes": [[n, n]], "scheme": "GBS_8,6", "updates_per_step_per_gpu": upd,
                        "macro_steps": M, "checkpoint_every": None if SN else C, "snapshots": SN, "misfit_J": J,

@@ -250,7 +250,9 @@ gbs_status gbs_step_host_stream(gbs_handle h, const void* const* y_in_host, void
  * rcv_resid[i] to field 0 at flat point index rcv_idx[i] (device arrays;
  * indices per problem 0, i.e. batch must be 1 when n_rcv > 0); n_rcv may be 0.
  * An index outside [0, points) is skipped and latches GBS_ERR_INVALID, which
- * gbs_sync() reports.  Requires enable_adjoint and GBS_ACOUSTIC. */
+ * gbs_sync() reports.  Requires enable_adjoint and GBS_ACOUSTIC.  GBS_F32X2 handles run
+ * the adjoint kernels in FP32-pair arithmetic, like their forward steps (y_in, the media and
+ * lam_out converted to pairs; lam_in written and grad_kappa accumulated in FP64). */
 gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out, void* lam_in,
                             double* grad_kappa, double H, const int64_t* rcv_idx, int n_rcv,
                             const void* rcv_resid);

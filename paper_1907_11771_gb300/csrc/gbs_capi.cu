@@ -1077,7 +1077,11 @@ gbs_status gbs_adjoint_step(gbs_handle h, const void* y_in, const void* lam_out,
   a.max_steps = h->levels_steps;
   a.rcv_pts = h->probs[0].pts;
   a.err = h->d_err;
-  const int n = plain_adjoint_step(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, h->stream);
+  // FP64 states in FP32 pairs: the adjoint in pair arithmetic, with the second staging state
+  // (idle outside gbs_step_host_stream) as the pair copy of lam_out
+  const int n = h->ds ? plain_adjoint_step_pairs(a, h->stage2, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv,
+                                                 rcv_resid, h->stream)
+                      : plain_adjoint_step(a, y_in, lam_out, lam_in, grad_kappa, rcv_idx, n_rcv, rcv_resid, h->stream);
   if (n < 0) return fail(h, GBS_ERR_CUDA, "adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
   h->launches += n;
   return GBS_OK;

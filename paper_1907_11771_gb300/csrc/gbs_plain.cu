@@ -1630,10 +1630,12 @@ int adjoint_step_t(const AdjPlan& a, const void* y_in_v, const void* lam_out_v, 
   k_adj_finish<T, DIM, R><<<grid, block, 0, st>>>(p, y_in, shared, lam_in, grad,
                                                   (DIM >= 2 && sizeof(T) == 4) ? a.gpair : nullptr);
   ++launches;
-  if (n_rcv > 0) {
-    k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid),
-                                                     a.rcv_pts, a.err);
-    ++launches;
+  if constexpr (!std::is_same<T, dsf>::value) {   // pairs: the caller injects into the FP64 lam_in
+    if (n_rcv > 0) {
+      k_inject<T><<<(n_rcv + 127) / 128, 128, 0, st>>>(lam_in, rcv_idx, n_rcv, static_cast<const T*>(rcv_resid),
+                                                       a.rcv_pts, a.err);
+      ++launches;
+    }
   }
   if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return launches;
@@ -1755,6 +1757,41 @@ int inject(int f64, void* lam, const int64_t* idx, int n, const void* values, in
     k_inject<float><<<(n + 127) / 128, 128, 0, s>>>(static_cast<float*>(lam), idx, n,
                                                      static_cast<const float*>(values), n_valid, err);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+namespace {
+// FP32 pairs -> FP64 (exact: a pair's value is the FP64 sum of its parts)
+__global__ void k_from_ds(const dsf* __restrict__ a, double* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = double(a[i]);
+}
+}  // namespace
+
+int plain_adjoint_step_pairs(const AdjPlan& a, void* lam_pairs, const void* y_in, const void* lam_out, void* lam_in,
+                             double* grad_kappa, const int64_t* rcv_idx, int n_rcv, const void* rcv_resid,
+                             cudaStream_t s) {
+  const StepPlan& p = a.fw;
+  if (p.system != GBS_ACOUSTIC || !p.ds || !lam_pairs) return -1;
+  // y_in, kappa, b and lam_out as FP32 pairs; the adjoint macro-step in pair arithmetic with
+  // lam_in written over the pair copy of lam_out (read only by the reverse steps before it)
+  const int64_t E = p.state_elems, M = p.probs_media_elems;
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(y_in), static_cast<dsf*>(p.ds_y0), E);
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.kappa), static_cast<dsf*>(p.ds_kappa), M);
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(p.b), static_cast<dsf*>(p.ds_b), M);
+  k_to_ds<<<1024, 256, 0, s>>>(static_cast<const double*>(lam_out), static_cast<dsf*>(lam_pairs), E);
+  AdjPlan b = a;
+  b.fw.kappa = p.ds_kappa;
+  b.fw.b = p.ds_b;
+  const int l = adjoint_sys<dsf>(b, p.ds_y0, lam_pairs, lam_pairs, grad_kappa, nullptr, 0, nullptr, s);
+  if (l < 0) return -1;
+  k_from_ds<<<1024, 256, 0, s>>>(static_cast<const dsf*>(lam_pairs), static_cast<double*>(lam_in), E);
+  int extra = 5;
+  if (n_rcv > 0) {
+    if (inject(1, lam_in, rcv_idx, n_rcv, rcv_resid, a.rcv_pts, a.err, s) < 0) return -1;
+    ++extra;
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  return l + extra;
 }
 
 int plain_adjoint_step(const AdjPlan& a, const void* y_in, const void* lam_out, void* lam_in,

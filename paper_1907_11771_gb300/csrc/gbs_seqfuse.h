@@ -26,4 +26,12 @@ struct SeqLevels {
 // lv.base set), otherwise plain_macro_step.  Returns the number of kernels launched, or -1.
 int plain_macro_step_seqfused(const StepPlan& p, const SeqLevels& lv, const void* y_in, void* y_out, cudaStream_t s);
 
+// The adjoint macro-step of a GBS_F32X2 handle in FP32-pair arithmetic (the adjoint kernels
+// instantiated for pairs): y_in, kappa, b and lam_out (FP64) are converted to pairs, lam_in is
+// written in FP64 and the gradient accumulated in FP64 as on the FP64 path.  lam_pairs: a
+// scratch state of pairs (8 bytes per element).  Returns the number of kernels launched, or -1.
+int plain_adjoint_step_pairs(const AdjPlan& a, void* lam_pairs, const void* y_in, const void* lam_out, void* lam_in,
+                             double* grad_kappa, const int64_t* rcv_idx, int n_rcv, const void* rcv_resid,
+                             cudaStream_t s);
+
 }  // namespace gbs

@@ -19,7 +19,7 @@ from paper_1907_11771_gb300.autograd import GBSMisfitFn, GBSStepFn, gbs_misfit_a
 from tests.gpu_common import AcousticCase, oracle_scheme, rel_l2
 
 pytestmark = pytest.mark.gpu
-F32, F64 = B.GBS_F32_STATE_F64_COMBINE, B.GBS_F64
+F32, F64, X2 = B.GBS_F32_STATE_F64_COMBINE, B.GBS_F64, B.GBS_F32X2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,6 +58,52 @@ def test_misfit_gradient_with_checkpointing_matches_oracle(precision, ckpt, snap
     tol = 1e-10 if precision == F64 else 2e-5
     assert J == pytest.approx(oJ, rel=tol)
     assert rel_l2(g.cpu().numpy(), og.ravel()) <= (1e-10 if precision == F64 else 1e-4)
+    sol.close()
+
+
+@pytest.mark.parametrize("ckpt,snaps", [(3, None), (None, 2)])
+def test_pair_adjoint_matches_the_oracle_and_the_fp64_adjoint(ckpt, snaps):
+    # FP64 states in FP32 pairs: the adjoint kernels run in pair arithmetic (about 2^-44 per
+    # operation against FP64's 2^-53): the gradient agrees with the oracle's FP64 gradient and
+    # with the FP64 handle's to the pair rounding level
+    n_macro = 7
+    case, sol, H, rcv, data, t = _setup(X2, n_macro=n_macro)
+    J, g = gbs_misfit_and_grad(sol, t["y0"], H, n_macro, t["rcv"], t["data"], checkpoint_every=ckpt or 1,
+                               snapshots=snaps)
+    steps, c = oracle_scheme(S.GBS_8_6)
+    oJ, og = OG.misfit_and_gradient(case.f, case.fT, case.pair, case.y0, H, steps, c, n_macro, rcv, data)
+    assert J == pytest.approx(oJ, rel=1e-10)
+    assert rel_l2(g.cpu().numpy(), og.ravel()) <= 1e-9
+    case64, sol64, H64, _, _, t64 = _setup(F64, n_macro=n_macro)
+    _, g64 = gbs_misfit_and_grad(sol64, t64["y0"], H64, n_macro, t64["rcv"], t64["data"],
+                                 checkpoint_every=ckpt or 1, snapshots=snaps)
+    assert rel_l2(g.cpu().numpy(), g64.cpu().numpy()) <= 1e-9
+    sol.close()
+    sol64.close()
+
+
+def test_pair_adjoint_step_in_place_and_receivers():
+    # lam_in written over lam_out, receiver residuals injected into the FP64 result
+    case, sol, H, rcv, data, t = _setup(X2, n_macro=1)
+    rng = np.random.default_rng(7)
+    lam = torch.tensor(rng.standard_normal(case.y0.size), device="cuda")
+    y = t["y0"]
+    ref_in = torch.empty_like(lam)
+    g1 = torch.zeros(case.kappa.size, dtype=torch.float64, device="cuda")
+    g2 = torch.zeros_like(g1)
+    resid = torch.tensor(rng.standard_normal(rcv.size), device="cuda")
+    B.gbs_adjoint_step(sol.h, y, lam, ref_in, g1, H, t["rcv"], resid)
+    lam2 = lam.clone()
+    B.gbs_adjoint_step(sol.h, y, lam2, lam2, g2, H, t["rcv"], resid)
+    sol.sync()
+    assert torch.equal(lam2, ref_in) and torch.equal(g1, g2)
+    steps, c = oracle_scheme(S.GBS_8_6)
+    olam, og = OG.gbs_macro_step_adjoint(case.f, case.fT, case.pair, case.y0, lam.cpu().numpy().reshape(case.y0.shape),
+                                         H, steps, c)
+    olam = olam.ravel().copy()
+    olam[rcv] += resid.cpu().numpy()
+    assert rel_l2(ref_in.cpu().numpy(), olam) <= 1e-10
+    assert rel_l2(g1.cpu().numpy(), og.ravel()) <= 1e-9
     sol.close()
 
 
