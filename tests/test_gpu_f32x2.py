@@ -120,7 +120,9 @@ def test_pairs_remove_the_fp32_floor():
     assert e_32 > 1e3 * e_x2, (e_32, e_x2)
 
 
-def test_adjoint_of_a_pair_handle_is_the_fp64_adjoint():
+def test_adjoint_of_a_pair_handle_matches_the_fp64_adjoint():
+    # the pair handle's adjoint runs in FP32-pair arithmetic (about 2^-44 per operation): one
+    # adjoint macro-step agrees with the FP64 handle's to that rounding level
     res = []
     for prec in (F64, X2):
         case = AcousticCase((20, 24), 4, prec, seed=12, const_rho=True)
@@ -135,7 +137,9 @@ def test_adjoint_of_a_pair_handle_is_the_fp64_adjoint():
         sol.sync()
         res.append((li.cpu().numpy(), g.cpu().numpy()))
         sol.close()
-    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(res[1][0], res[0][0]) <= 1e-10
+    assert rel(res[1][1], res[0][1]) <= 1e-9
 
 
 def test_time_blocked_kernel_refused_for_fp64_states_and_3d_pairs():
