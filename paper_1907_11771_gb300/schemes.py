@@ -12,12 +12,12 @@ no free part (Sec. 3.2).
 * GBS_12_8  -- Sec. 3.8.3 (order 12, eight cores, ISB_n 0.7116)
 * SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1 -- Table 1 (fully determined)
 * SQ8_2468  -- classical Richardson extrapolation with N = 2, 4, 6, 8 (order 8)
-* GBS_6_6   -- order 6 on six cores (all even counts up to N_max = 22): a genuinely order-6
-               scheme with positive imaginary-axis coverage, from an earlier penalty-method run
-               of the App. B optimisation, rounded to rationals with denominators below 2^16 (as
-               Sec. 3.8 does for its schemes); exact ISB 15.00302 (ISB_n 0.65231).  It is not the
-               order-6 optimum: on these counts that coincides with the order-8 optimum (ISB_n
-               0.7695), whose order-7 error term vanishes.  The paper prints no order-6 scheme:
+* GBS_6_6   -- order 6 on six cores (all even counts up to N_max = 22): the App. B optimum at
+               order 6 kept 1e-4 inside the unit circle, rounded to rationals with denominators
+               below 2^16 (as Sec. 3.8 does for its schemes; optimize.gbs_6_6_free_weights
+               regenerates them); exact ISB 17.65602 (ISB_n 0.76765), order-7 error term
+               nonzero.  Without the margin the order-6 optimum coincides with the order-8 one
+               (ISB_n 0.7695), whose order-7 term vanishes.  The paper prints no order-6 scheme:
                square order-6 schemes have ISB 0 (Sec. 2.2).
 """
 from dataclasses import dataclass
@@ -75,7 +75,7 @@ SQ16_TABLE1 = Scheme("SQ16{2,8,...,22}", 16, (2, 8, 10, 12, 14, 16, 18, 22))
 SQ8_2468 = Scheme("SQ8{2,4,6,8}", 8, (2, 4, 6, 8))
 
 GBS_6_6 = Scheme("GBS_6,6", 6, (2, 4, 6), (8, 10, 12, 14, 16, 18, 20, 22),
-                 ("269/59612", "197/13930", "1486/33929", "11883/63743", "19127/15572", "-162418/33125",
-                  "-20111/27925", "197282/38345"))
+                 ("188/59023", "124/13615", "1361/56815", "4025/60943", "6469/28645", "90535/24952",
+                  "-1002769/65522", "508409/41177"))
 
 ALL = {s.name: s for s in (GBS_8_6, GBS_8_8, GBS_12_8, SQ8_TABLE1, SQ12_TABLE1, SQ16_TABLE1, SQ8_2468, GBS_6_6)}

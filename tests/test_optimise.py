@@ -10,7 +10,7 @@
   the origin drives the leading error terms to zero.
 * GBS_6,6 is a genuinely order-6 scheme with positive ISB (the paper prints none; square order-6
   schemes have ISB 0, Sec. 2.2), pinned by exact arithmetic: order constraints, order exactly 6,
-  and its recorded ISB.
+  and its recorded ISB; the optimiser regenerates its rationals.
 """
 import math
 from fractions import Fraction
@@ -37,11 +37,23 @@ def test_order6_scheme_constraints_order_and_isb():
         assert R[k] == Fraction(1, math.factorial(k))
     assert R[7] != Fraction(1, math.factorial(7))
     isb = W.isb_exact(R)
-    assert isb == pytest.approx(15.00302, abs=2e-5)
-    assert round(isb / sc.evals_per_core, 5) == 0.65231
+    assert isb == pytest.approx(17.65602, abs=2e-5)
+    assert round(isb / sc.evals_per_core, 5) == 0.76765
     # versus the square order-6 scheme on the dependent counts: no imaginary-axis coverage
     sq = W.square_weights([2, 4, 6], 6)
     assert W.isb_exact(W.stability_poly([2, 4, 6], sq)) == 0.0
+
+
+def test_order6_scheme_is_regenerated_by_the_optimiser():
+    # the committed rationals are the optimiser's order-6 optimum (margin 1e-4) rounded to
+    # denominators below 2^16; compared as values, since the last digits of an LP solution may
+    # differ between solver builds, then as the rounded rationals themselves
+    got = O.gbs_6_6_free_weights()
+    ref = [Fraction(t) for t in S.GBS_6_6.c_free_text]
+    assert (S.GBS_6_6.steps_dep, S.GBS_6_6.steps_free) == O.GBS_6_6_STEPS
+    scale = max(abs(float(v)) for v in ref)
+    assert max(abs(float(a) - float(b)) for a, b in zip(got, ref)) <= 1e-6 * scale
+    assert got == ref
 
 
 def _exact_isb_n(order, dep, free, c_free):
