@@ -2,7 +2,8 @@
 
 * ``GBSStepFn``: y_out = M(kappa)^n y_in for n macro-steps; its backward calls
   ``gbs_adjoint_step`` once per macro-step (recomputing the intermediate states
-  from y_in), returning d/dy_in and d/dkappa.
+  from y_in: all n of them, or with ``snapshots=s`` at most s held at once on a
+  binomial schedule), returning d/dy_in and d/dkappa.
 * ``gbs_misfit_and_grad``: the receiver misfit
       J = 1/2 sum_m sum_r (p(x_r, t_m) - d_r(t_m))^2,  m = 1..n_macro,
   and dJ/dkappa, with two-level checkpointing: the forward sweep keeps every
@@ -34,12 +35,12 @@ class GBSStepFn(torch.autograd.Function):
     kappa tensor is the ``kappa`` argument (the library reads it in place)."""
 
     @staticmethod
-    def forward(ctx, y_in, kappa, solver, H, n_macro):
+    def forward(ctx, y_in, kappa, solver, H, n_macro, snapshots=None):
         if kappa.data_ptr() != solver._media[0].data_ptr():
             raise ValueError("kappa must be the tensor the solver was created with")
         y_out = torch.empty_like(y_in)
         solver.step(y_in.detach(), y_out, H, n_macro)
-        ctx.solver, ctx.H, ctx.n_macro = solver, H, n_macro
+        ctx.solver, ctx.H, ctx.n_macro, ctx.snapshots = solver, H, n_macro, snapshots
         ctx.save_for_backward(y_in.detach())
         return y_out
 
@@ -47,16 +48,36 @@ class GBSStepFn(torch.autograd.Function):
     def backward(ctx, lam_out):
         (y_in,) = ctx.saved_tensors
         sol, H, n = ctx.solver, ctx.H, ctx.n_macro
-        states = [y_in]
-        for _ in range(n - 1):
-            nxt = torch.empty_like(y_in)
-            sol.step(states[-1], nxt, H, 1)
-            states.append(nxt)
         lam = lam_out.detach().contiguous().clone()
         grad = torch.zeros(sol.state_elems // sol.F, dtype=torch.float64, device=y_in.device)
-        for m in range(n - 1, -1, -1):
-            sol.adjoint_step(states[m], lam, lam, grad, H)
-        return lam, grad.to(y_in.dtype), None, None, None
+        if ctx.snapshots is None:
+            states = [y_in]
+            for _ in range(n - 1):
+                nxt = torch.empty_like(y_in)
+                sol.step(states[-1], nxt, H, 1)
+                states.append(nxt)
+            for m in range(n - 1, -1, -1):
+                sol.adjoint_step(states[m], lam, lam, grad, H)
+        else:
+            # binomial schedule: the first descent's states stored by a forward sweep, then the
+            # plan's advances and adjoint macro-steps (checkpoint.revolve_plan)
+            plan = revolve_plan(n, int(ctx.snapshots))
+            slots = [y_in.clone()] + [torch.empty_like(y_in) for _ in range(plan.max_slots - 1)]
+            work = y_in.clone()
+            buf = lambda k: work if k == WORK else slots[k]
+            stores = dict(plan.forward_stores)
+            for m in range(max(stores, default=0)):
+                sol.step(work, work, H, 1)
+                if (m + 1) in stores:
+                    slots[stores[m + 1]].copy_(work)
+            for act in plan.actions:
+                if act[0] == "advance":
+                    _, src, dst, a, m = act
+                    sol.step(buf(src), buf(dst), H, m - a)
+                else:
+                    _, k, m = act
+                    sol.adjoint_step(buf(k), lam, lam, grad, H)
+        return lam, grad.to(y_in.dtype), None, None, None, None
 
 
 def gbs_misfit_and_grad(solver, y0, H, n_macro, rcv_idx, data, checkpoint_every=50, snapshots=None):

@@ -9,7 +9,8 @@
 * ``gbs_misfit_and_grad`` with a fake solver (a small linear map on CPU
   tensors whose adjoint and kappa-derivative are exact) gives the same J and
   gradient with two-level and binomial checkpointing, and both match central
-  finite differences of J.
+  finite differences of J; ``GBSStepFn``'s backward, with every state or a
+  binomial schedule, matches torch's autograd through the same map.
 """
 from functools import lru_cache
 
@@ -173,3 +174,29 @@ def test_revolve_recomputes_no_more_than_the_schedule_says():
     sol.steps = 0
     gbs_misfit_and_grad(sol, y0, 0.1, n, rcv, data, snapshots=s)
     assert sol.steps == n + revolve_plan(n, s).advances
+
+
+@pytest.mark.parametrize("n,s", [(1, 1), (5, 1), (9, 2), (17, 3), (6, 10)])
+def test_step_function_backward_with_and_without_checkpoints(n, s):
+    # GBSStepFn's backward on the fake solver: every state (None) and a binomial schedule of s
+    # states give the gradients of torch's own autograd through the dense map A(kappa)^n
+    from paper_1907_11771_gb300.autograd import GBSStepFn
+    sol = FakeLinearSolver(16, seed=3)
+    sol.kappa.requires_grad_(True)
+    sol._media = (sol.kappa,)
+    rng = np.random.default_rng(11)
+    y0 = torch.tensor(rng.standard_normal(16))
+    w = torch.tensor(rng.standard_normal(16))
+    yr = y0.clone().requires_grad_(True)
+    kr = sol.kappa.detach().clone().requires_grad_(True)
+    out = yr
+    for _ in range(n):
+        out = (sol.A0 + torch.diag(kr) @ sol.B) @ out
+    (w * out).sum().backward()
+    for snaps in (None, s):
+        y = y0.clone().requires_grad_(True)
+        sol.kappa.grad = None
+        res = GBSStepFn.apply(y, sol.kappa, sol, 0.1, n, snaps)
+        (w * res).sum().backward()
+        assert torch.allclose(y.grad, yr.grad, rtol=1e-12, atol=1e-13)
+        assert torch.allclose(sol.kappa.grad, kr.grad, rtol=1e-12, atol=1e-13)

@@ -131,6 +131,27 @@ def test_misfit_gradient_central_differences_on_16_directions(precision):
     sol.close()
 
 
+@pytest.mark.parametrize("snaps", [1, 2, 3])
+def test_autograd_step_with_binomial_checkpointing_equals_all_states(snaps):
+    # the same adjoint macro-steps on the same (recomputed) states: identical gradients
+    case, sol, H, rcv, data, t = _setup(F64, n_macro=3)
+    kappa = case.t_kappa
+    rng = np.random.default_rng(9)
+    w = None
+    grads = []
+    for s in (None, snaps):
+        y = t["y0"].clone().requires_grad_(True)
+        kappa.grad = None
+        kappa.requires_grad_(True)
+        out = GBSStepFn.apply(y, kappa, sol, H, 6, s)
+        if w is None:
+            w = torch.tensor(rng.standard_normal(out.numel()), device="cuda")
+        (out * w).sum().backward()
+        grads.append((y.grad.clone(), kappa.grad.clone()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    sol.close()
+
+
 def test_autograd_step_and_misfit_functions():
     case, sol, H, rcv, data, t = _setup(F64, n_macro=3)
     # GBSStepFn: d<w, y_out>/dy_in and d/dkappa against the oracle adjoint of 2 macro-steps
