@@ -338,7 +338,8 @@ struct Vec16<dsf> {
 };
 
 // resident blocks per SM the register budget of k_lf_tiled aims at, each measured best against
-// its neighbours: FP32 2D 6, FP32 3D 5; 8-byte states 3 in 2D and 2 in 3D
+// its neighbours: FP32 2D 5, FP32 3D 4 (the increment form's f0 and scaled-media operands need
+// the registers of one block more than the earlier 6 and 5); 8-byte states 3 in 2D and 2 in 3D
 template <typename T, int DIM, int R>
 constexpr int lf_min_blocks() {
   return sizeof(T) == 4 ? (DIM == 2 ? 5 : 4) : (DIM == 2 ? 3 : 2);
