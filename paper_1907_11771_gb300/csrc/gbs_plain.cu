@@ -338,11 +338,18 @@ struct Vec16<dsf> {
 };
 
 // resident blocks per SM the register budget of k_lf_tiled aims at, each measured best against
-// its neighbours: FP32 2D 5, FP32 3D 4 (the increment form's f0 and scaled-media operands need
-// the registers of one block more than the earlier 6 and 5); 8-byte states 3 in 2D and 2 in 3D
+// its neighbours: FP32 2D 5, FP32 3D 4 (one fewer than before the increment form, whose f0 and
+// scaled-media operands take registers); 8-byte states 3 in 2D and 2 in 3D.  The FP32 values can
+// be set at build time for such measurements.
+#ifndef GBS_LF_BLOCKS_F32_2D
+#define GBS_LF_BLOCKS_F32_2D 5
+#endif
+#ifndef GBS_LF_BLOCKS_F32_3D
+#define GBS_LF_BLOCKS_F32_3D 4
+#endif
 template <typename T, int DIM, int R>
 constexpr int lf_min_blocks() {
-  return sizeof(T) == 4 ? (DIM == 2 ? 5 : 4) : (DIM == 2 ? 3 : 2);
+  return sizeof(T) == 4 ? (DIM == 2 ? GBS_LF_BLOCKS_F32_2D : GBS_LF_BLOCKS_F32_3D) : (DIM == 2 ? 3 : 2);
 }
 
 // TMA staging helpers (inline PTX): shared-window address, mbarrier, 4D tensor copy
