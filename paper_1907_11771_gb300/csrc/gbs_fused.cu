@@ -673,26 +673,6 @@ __device__ __forceinline__ int problem_of(const ProbDev* probs, int batch, int64
   return lo;
 }
 
-// Exact FP32 -> FP64 promotion on the integer pipe, bit for bit the hardware conversion (all 2^32
-// inputs checked on the host): a normal float's sign, exponent (re-biased by 1023 - 127 = 896)
-// and 23 mantissa bits placed into the double's fields; infinities and NaNs keep exponent 2047
-// and their payload; a subnormal m 2^-149 is normalised (its leading bit found by clz); zero
-// keeps its sign.  GB300's conversion instruction shares the slow FP64 pipe with the combine's
-// FMAs, so a converted operand per FMA would double that pipe's work.
-__device__ __forceinline__ double promote(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu, ex = mag >> 23;
-  unsigned hi = sign | ((mag >> 3) + (ex == 0xffu ? (1792u << 20) : (896u << 20)));
-  unsigned lo = b << 29;
-  if (ex == 0u) {
-    const int sh = __clz(mag) - 8;                     // mag << sh has bit 23 set (mag != 0)
-    const unsigned fr = (mag << sh) & 0x7fffffu;
-    hi = mag ? (sign | ((897u - (unsigned)sh) << 20) | (fr >> 3)) : sign;
-    lo = mag ? (fr << 29) : 0u;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // y_out = y_0 + sum_k c_k d*_k (per problem, its slot's weights): the increment form's combine
 // (y*_k = y_0 + d*_k, sum_k c_k = 1; Sec. 2.1, Sec. 3.2), in ascending k.  kF64: the averages and
 // y_0 are promoted to FP64 exactly and summed with FP64 FMAs, rounded to FP32 once (GB300's FP64

@@ -697,7 +697,7 @@ __device__ __forceinline__ bool lf_tile_level(const StepPlan& p, const T* y_in, 
         const int64_t e = fl * P + o;
         const T yc = fl == 0 ? sh[0][r][cc] : fl == 1 ? sh[1][r][cc] : fl == 2 ? sh[2][r][cc] : ldg(cur + e);
         const T yp = lf_update(fl, pg[fl], f[fl]);
-        combine_last(acc, e, first, last, c, gragg_avg(pv[fl], yc, yp), yo,
+        combine_last<T, typename out_of<T>::type, DIM == 3>(acc, e, first, last, c, gragg_avg(pv[fl], yc, yp), yo,
                      kInc && first && !p.partial ? y_in[q.state_off + e] : T(0));
       }
     }

@@ -93,15 +93,46 @@ __device__ __forceinline__ float2 mul_split2(float2 hi, float2 lo, float2 f) {
   return __fadd2_rn(p, __ffma2_rn(lo, f, e));
 }
 
+// Exact FP32 -> FP64 promotion on the integer pipe, bit for bit the hardware conversion (all 2^32
+// inputs checked on the host): a normal float's sign, exponent (re-biased by 1023 - 127 = 896)
+// and 23 mantissa bits placed into the double's fields; infinities and NaNs keep exponent 2047
+// and their payload; a subnormal m 2^-149 is normalised (its leading bit found by clz); zero
+// keeps its sign.  GB300's conversion instruction shares the slow FP64 pipe with the combine's
+// FMAs, so a converted operand per FMA would double that pipe's work.
+__device__ __forceinline__ double promote(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu, ex = mag >> 23;
+  unsigned hi = sign | ((mag >> 3) + (ex == 0xffu ? (1792u << 20) : (896u << 20)));
+  unsigned lo = b << 29;
+  if (ex == 0u) {
+    const int sh = __clz(mag) - 8;                     // mag << sh has bit 23 set (mag != 0)
+    const unsigned fr = (mag << sh) & 0x7fffffu;
+    hi = mag ? (sign | ((897u - (unsigned)sh) << 20) | (fr >> 3)) : sign;
+    lo = mag ? (fr << 29) : 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double to_f64(float f) { return promote(f); }
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) { return (double)v; }
+
 // The combine of the plain path's last leap-frog step of sequence k: y_out (+)= c_k y*_k in FP64.
 // FP32 states are in increment form (y*_k = y_0 + d*_k): the first sequence starts the
 // accumulator at y_0, each adds c_k d*_k (d*_k promoted exactly), the last rounds once to FP32.
-template <typename T, typename O>
+// kIntPromote: FP32 inputs promoted on the integer pipe (promote) instead of by the conversion
+// instruction on the FP64 pipe; measured faster in the 3D kernels (1.4% per 3D macro-step) and
+// slower in the 2D ones (0.6%), whose issue slots are the scarcer resource.
+template <typename T, typename O, bool kIntPromote = false>
 __device__ __forceinline__ void combine_last(double* acc, int64_t e, bool first, bool last, double c, T ystar,
                                              O* yo, T y0 = T(0)) {
-  const double ys = (double)ystar;
+  auto f64 = [](T v) -> double {
+    if constexpr (kIntPromote) return to_f64(v);
+    else return (double)v;
+  };
+  const double ys = f64(ystar);
   double a2;
-  if constexpr (sizeof(T) == 4 && sizeof(O) == 4) a2 = fma(c, ys, first ? (double)y0 : acc[e]);
+  if constexpr (sizeof(T) == 4 && sizeof(O) == 4) a2 = fma(c, ys, first ? f64(y0) : acc[e]);
   else a2 = first ? c * ys : fma(c, ys, acc[e]);
   if (last) yo[e] = static_cast<O>(a2);
   else acc[e] = a2;

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               b0[e] = l1[fl];
               b1[e] = d2;
             } else {
-              combine_last(p.acc + q.state_off, e, first, last, c, gragg_avg(pv2[fl], l1[fl], d2),
+              combine_last<float, float, true>(p.acc + q.state_off, e, first, last, c, gragg_avg(pv2[fl], l1[fl], d2),
                            y_out + q.state_off, first && !p.partial ? y_in[q.state_off + e] : 0.f);
             }
           }
