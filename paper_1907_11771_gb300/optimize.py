@@ -210,17 +210,18 @@ def _excess(d):
     return (2.0 * d.real + np.abs(d) ** 2) / (np.abs(1.0 + d) + 1.0)
 
 
-def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8, rounds=60):
+def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8, rounds=60, slack=0.0):
     """Free weights with |1 + delta_j| <= 1 - mu_j on the samples and the lead term negative, by
     cutting planes around x0: the half-planes Re(e^(-i psi) delta_j) <= 1 - cos psi - mu_j, cut
     at psi = arg(1 + delta_j), each row scaled by its own sensitivity to the free weights;
     converged when every sample's excess is below tol times its sensitivity.  (x, column
-    scales), or None if the LP proves that none exists or the cuts do not settle."""
+    scales), or None if the LP proves that none exists or the cuts do not settle.  slack: |R| may
+    exceed 1 by that much; lead None: no constraint at the origin."""
     d, B = rows_model.at(h, ys, x0)
     Dc = 1.0 / np.maximum(np.abs(B).max(axis=0), 1e-300)     # column scaling: x = x0 + Dc z
     Bs = B * Dc[None, :]
     sens = np.maximum(np.abs(Bs).max(axis=1), 1e-300)
-    mu = _margin(h, ys, margin, order)
+    mu = _margin(h, ys, margin, order) - slack
     nf = Bs.shape[1]
     rows, rhs = [], []
 
@@ -234,16 +235,18 @@ def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8
     for j in range(d.size):
         for k in range(angles):
             cut(j, 2 * np.pi * k / angles)
-    lg, lr = lead
-    eps = 1e-8 * abs(lr)
-    ls = 1.0 / max(np.abs(lg * Dc).max(), 1e-300)
-    lead_row = np.concatenate([lg * Dc * ls, [0.0]])
-    lead_rhs = -(lr + lg @ x0 + eps) * ls
+    extra_rows, extra_rhs = [], []
+    if lead is not None:
+        lg, lr = lead
+        eps = 1e-8 * abs(lr)
+        ls = 1.0 / max(np.abs(lg * Dc).max(), 1e-300)
+        extra_rows.append(np.concatenate([lg * Dc * ls, [0.0]]))
+        extra_rhs.append(-(lr + lg @ x0 + eps) * ls)
     cost = np.zeros(nf + 1)
     cost[-1] = 1.0
     bounds = [(None, None)] * nf + [(-1.0, None)]
     for _ in range(rounds):
-        A_ub, b_ub = np.array(rows + [lead_row]), np.array(rhs + [lead_rhs])
+        A_ub, b_ub = np.array(rows + extra_rows), np.array(rhs + extra_rhs)
         res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=bounds, method="highs-ds")
         if res.status == 4:   # numerical trouble in the simplex: try the interior-point method
             res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=bounds, method="highs-ipm")
@@ -259,17 +262,17 @@ def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8
     return None
 
 
-def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, rounds=8):
+def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, rounds=8, slack=0.0):
     """Exchange loop around the LP: weights stable on the fine grid (half the margin), or None."""
     pts = ys
     for _ in range(rounds):
-        r = _lp_feasible(h, rows_model, lead, order, pts, margin, x0)
+        r = _lp_feasible(h, rows_model, lead, order, pts, margin, x0, slack=slack)
         if r is None:
             return None
         x, Dc = r
         d, B = rows_model.at(h, fine, x)
         sens = np.maximum(np.abs(B * Dc[None, :]).max(axis=1), 1e-300)
-        v = (_excess(d) + 0.5 * _margin(h, fine, margin, order)) / sens
+        v = (_excess(d) + 0.5 * _margin(h, fine, margin, order) - slack) / sens
         bad = np.where(v > tol)[0]
         if bad.size == 0:
             return x
@@ -277,17 +280,21 @@ def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, round
     return None
 
 
-def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9, rel_tol=1e-7, h_hi=None):
+def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9, rel_tol=1e-7, h_hi=None,
+             slack=0.0, origin=True):
     """Maximise the imaginary stability boundary over the free weights (App. B): bisection over
     h in (0, N_max + 1] with the LP feasibility test above.  The dependent/free split only fixes
     the parametrisation (every split spans the same weights); small dependent counts keep it
-    well conditioned."""
+    well conditioned.  slack > 0 accepts |R| up to 1 + slack on the contour, and origin=False
+    drops the constraint at the origin: the looser criterion under which a sampled FP64
+    solver at its tolerance counts a polynomial as stable (strictly stable optima need the
+    defaults)."""
     steps_dep, steps_free = tuple(steps_dep), tuple(steps_free)
     steps = steps_dep + steps_free
     c0x, Gx = affine_weights_exact(order, steps_dep, steps_free)
     c0 = np.array([float(v) for v in c0x])
     G = np.array([[float(v) for v in row] for row in Gx])
-    lead = _lead_constraint(order, steps, c0, G)
+    lead = _lead_constraint(order, steps, c0, G) if origin else None
     rows_model = _DeltaRows(order, steps, c0x, Gx)
     nmax = max(steps)
     ys = np.arange(1, n_samples + 1) / n_samples
@@ -297,7 +304,7 @@ def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9
     found = False
     while hi - lo > rel_tol * hi:
         mid = 0.5 * (lo + hi)
-        x = _feasible(mid, rows_model, lead, order, ys, fine, margin, best)
+        x = _feasible(mid, rows_model, lead, order, ys, fine, margin, best, slack=slack)
         if x is not None:
             lo, best, found = mid, x, True
         else:
