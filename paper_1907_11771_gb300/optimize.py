@@ -51,7 +51,7 @@ ISB_n the paper prints for order 4 up to 28 and order 8 up to 22, 30 and 40
 of the paper's GBS_12,8 (0.7128).  On all counts up to 36 (order 12) and 32
 (order 16) its strictly stable optima, 0.677 and 0.42, stay below the printed
 0.7504 and 0.6075; allowing |R| up to 1 + 1e-12 on the contour and dropping the
-constraint at the origin, order 16 reaches 0.625.
+constraint at the origin (slack=1e-12, origin=False), order 16 reaches 0.625.
 """
 from dataclasses import dataclass
 from fractions import Fraction
