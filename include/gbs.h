@@ -405,6 +405,19 @@ gbs_status gbs_step_noalloc(const gbs_problem* pb, const void* kappa, const void
                             const double* c_free, const void* y_in, void* y_out, double H,
                             int n_macro, void* cuda_stream);
 
+/* Self-test of the library's exact FP32 -> FP64 promotion, which the FP64 combines use
+ * instead of the conversion instruction (GB300 runs that instruction on its slow FP64 pipe):
+ * for the float bit patterns first .. first + count - 1 (a range within [0, 2^32)), compares
+ * the promotion's bits with the conversion instruction's on the current device and writes to
+ * mismatches (host, 3 entries) the number of inputs that are not NaN and whose doubles differ
+ * [0], of NaN inputs whose doubles differ in more than the quiet bit (bit 51) [1], and of NaN
+ * inputs whose doubles differ in the quiet bit alone [2] (the conversion quiets a signalling
+ * NaN; the promotion keeps its bits).  Synchronises the device; allocates nothing (the counters
+ * are a static device array, so concurrent calls race).  No counterpart in the paper (a check
+ * of an implementation detail).  Errors: GBS_ERR_INVALID (NULL mismatches, range outside
+ * [0, 2^32)), GBS_ERR_CUDA. */
+gbs_status gbs_selftest_f32_to_f64(uint64_t first, uint64_t count, uint64_t* mismatches);
+
 /* Message of the last failed gbs_step_noalloc call on this thread ("" if none).
  * No counterpart in the paper. */
 const char* gbs_noalloc_last_error(void);

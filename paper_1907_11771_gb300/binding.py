@@ -68,6 +68,7 @@ _SIGS = {
     "gbs_destroy": (_I, [_P]),
     "gbs_last_error": (ctypes.c_char_p, [_P]),
     "gbs_kernel_launches": (_I64, [_P]),
+    "gbs_selftest_f32_to_f64": (_I, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "gbs_step_noalloc": (_I, [ctypes.POINTER(gbs_problem), _P, _P, _I, _I, ctypes.POINTER(_I), _I,
                               ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P, _D, _I, _P]),
     "gbs_noalloc_last_error": (ctypes.c_char_p, []),
@@ -272,6 +273,17 @@ def gbs_step_noalloc(pb, kappa, rho, order, steps_dep, steps_free, c_free, y_in,
     if st != GBS_OK:
         msg = lib().gbs_noalloc_last_error()
         raise GbsError(st, msg.decode() if msg else "")
+
+
+def gbs_selftest_f32_to_f64(first, count):
+    """(non-NaN differences, NaN differences beyond the quiet bit, NaN differences in the quiet
+    bit alone) of the exact FP32 -> FP64 promotion against the conversion instruction over the
+    float bit patterns [first, first + count)."""
+    out = (ctypes.c_uint64 * 3)()
+    st = lib().gbs_selftest_f32_to_f64(int(first), int(count), out)
+    if st != GBS_OK:
+        raise GbsError(st, "self-test of the FP32 -> FP64 promotion failed")
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def gbs_noalloc_last_error():

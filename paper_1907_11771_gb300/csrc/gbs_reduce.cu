@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "gbs_internal.h"
+#include "gbs_stencil.cuh"
 
 namespace gbs {
 namespace {
@@ -177,3 +178,59 @@ int misfit(int f64, const void* y, const int64_t* idx, int n_rcv, const void* da
 }
 
 }  // namespace gbs
+
+// ---------------------------------------------------------------------------
+// Self-test of the exact FP32 -> FP64 promotion used by the FP64 combines (promote, in
+// gbs_stencil.cuh): its bits against the conversion instruction's for a range of float bit
+// patterns.  Counters live in a small static device array (the call allocates nothing).
+// ---------------------------------------------------------------------------
+namespace gbs {
+namespace {
+
+// [0] inputs that are not NaN and whose doubles differ; [1] NaN inputs whose doubles differ in
+// more than the quiet bit (bit 51); [2] NaN inputs whose doubles differ in the quiet bit alone
+__device__ unsigned long long g_promote_mismatch[3];
+
+__global__ void __launch_bounds__(256) k_selftest_promote(unsigned long long first, unsigned long long count) {
+  unsigned long long bad = 0, badnan = 0, quiet = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned b = (unsigned)(first + i);
+    const float f = __uint_as_float(b);
+    const unsigned long long x = (unsigned long long)__double_as_longlong(promote(f)) ^
+                                 (unsigned long long)__double_as_longlong((double)f);
+    if (x) {
+      if ((b & 0x7fffffffu) <= 0x7f800000u) ++bad;
+      else if (x == (1ull << 51)) ++quiet;
+      else ++badnan;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+    badnan += __shfl_down_sync(0xffffffffu, badnan, o);
+    quiet += __shfl_down_sync(0xffffffffu, quiet, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (bad | badnan | quiet)) {
+    atomicAdd(&g_promote_mismatch[0], bad);
+    atomicAdd(&g_promote_mismatch[1], badnan);
+    atomicAdd(&g_promote_mismatch[2], quiet);
+  }
+}
+
+}  // namespace
+}  // namespace gbs
+
+extern "C" gbs_status gbs_selftest_f32_to_f64(uint64_t first, uint64_t count, uint64_t* mismatches) {
+  if (!mismatches || first > (1ull << 32) || count > (1ull << 32) - first) return GBS_ERR_INVALID;
+  const unsigned long long zero[3] = {0, 0, 0};
+  if (cudaMemcpyToSymbol(gbs::g_promote_mismatch, zero, sizeof zero) != cudaSuccess) return GBS_ERR_CUDA;
+  if (count) {
+    gbs::k_selftest_promote<<<4096, 256>>>(first, count);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return GBS_ERR_CUDA;
+  }
+  unsigned long long out[3];
+  if (cudaMemcpyFromSymbol(out, gbs::g_promote_mismatch, sizeof out) != cudaSuccess) return GBS_ERR_CUDA;
+  for (int i = 0; i < 3; ++i) mismatches[i] = out[i];
+  return GBS_OK;
+}

@@ -93,12 +93,14 @@ __device__ __forceinline__ float2 mul_split2(float2 hi, float2 lo, float2 f) {
   return __fadd2_rn(p, __ffma2_rn(lo, f, e));
 }
 
-// Exact FP32 -> FP64 promotion on the integer pipe, bit for bit the hardware conversion (all 2^32
-// inputs checked on the host): a normal float's sign, exponent (re-biased by 1023 - 127 = 896)
-// and 23 mantissa bits placed into the double's fields; infinities and NaNs keep exponent 2047
-// and their payload; a subnormal m 2^-149 is normalised (its leading bit found by clz); zero
-// keeps its sign.  GB300's conversion instruction shares the slow FP64 pipe with the combine's
-// FMAs, so a converted operand per FMA would double that pipe's work.
+// Exact FP32 -> FP64 promotion on the integer pipe, bit for bit the hardware conversion for every
+// float but the signalling NaNs (all 2^32 inputs compared with it on the device by
+// gbs_selftest_f32_to_f64): a normal float's sign, exponent (re-biased by 1023 - 127 = 896) and
+// 23 mantissa bits placed into the double's fields; infinities and NaNs keep exponent 2047 and
+// their payload (the conversion also sets a signalling NaN's quiet bit; an FMA on either gives a
+// NaN); a subnormal m 2^-149 is normalised (its leading bit found by clz); zero keeps its sign.
+// GB300's conversion instruction shares the slow FP64 pipe with the combine's FMAs, so a
+// converted operand per FMA would double that pipe's work.
 __device__ __forceinline__ double promote(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu, ex = mag >> 23;
