@@ -55,11 +55,11 @@ FUSED_SOURCES = ("paper_1907_11771_gb300/csrc/gbs_fused.cu", "paper_1907_11771_g
 # kernel on the 2D 2048^2 FP32 workload, from one ncu capture per schedule (hseg, tmax, schedule),
 # keyed by the hash of FUSED_SOURCES they were measured on: another build reports no traffic.
 PASSES_2D2048_TRAFFIC = {
-    ("53de5eb70980", 256, 4, 0): 5.325961984e9 + 3.071086336e9,
-    ("53de5eb70980", 192, 4, 0): 5.198048256e9 + 3.074904832e9,
-    ("53de5eb70980", 192, 4, 1): 5.235100672e9 + 3.072640768e9,
-    ("53de5eb70980", 384, 4, 0): 5.075866880e9 + 3.076349440e9,
-    ("53de5eb70980", 128, 4, 0): 6.117917440e9 + 3.075159552e9,
+    ("58541fb99eeb", 256, 4, 0): 5.325961984e9 + 3.071086336e9,
+    ("58541fb99eeb", 192, 4, 0): 5.198048256e9 + 3.074904832e9,
+    ("58541fb99eeb", 192, 4, 1): 5.235100672e9 + 3.072640768e9,
+    ("58541fb99eeb", 384, 4, 0): 5.075866880e9 + 3.076349440e9,
+    ("58541fb99eeb", 128, 4, 0): 6.117917440e9 + 3.075159552e9,
 }
 
 # Algorithmic minimum bytes per grid point per macro-step (FP32 states): the method must read
@@ -67,13 +67,27 @@ PASSES_2D2048_TRAFFIC = {
 ALG_MIN_BYTES_PER_POINT = {2: 32.0, 3: 40.0}
 
 
-def fused_source_hash():
-    """First 12 hex digits of the SHA-256 of the time-blocked kernel's sources."""
+def strip_comments(src):
+    """C/CUDA source without its comments, trailing blanks and empty lines (the code a
+    comment-only edit leaves unchanged)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip()) + "\n"
+
+
+def fused_source_hash(read=None):
+    """First 12 hex digits of the SHA-256 of the time-blocked kernel's sources, comments
+    stripped.  read(rel) -> text overrides reading the working tree."""
     import hashlib
     h = hashlib.sha256()
     for rel in FUSED_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, rel)) as f:
+                text = f.read()
+        else:
+            text = read(rel)
+        h.update(strip_comments(text).encode())
     return h.hexdigest()[:12]
 
 

@@ -43,3 +43,16 @@ def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(monkeypatch, tmp_
     assert bench.peaks() == (6753.8, "measured")
     os.unlink(tmp_path / "MEASURED_PEAKS.json")
     assert bench.peaks() == (pytest.approx(6800.0), "fallback")
+
+
+def test_traffic_key_ignores_comments_but_not_code():
+    src = {rel: open(os.path.join(bench.ROOT, rel)).read() for rel in bench.FUSED_SOURCES}
+    base = bench.fused_source_hash(src.__getitem__)
+    assert base == bench.fused_source_hash()
+    first = bench.FUSED_SOURCES[0]
+    commented = dict(src)
+    commented[first] = "// a note\n/* a block\n   comment */\n" + src[first].replace("\n", "  // tail\n", 3)
+    assert bench.fused_source_hash(commented.__getitem__) == base
+    edited = dict(src)
+    edited[first] = src[first] + "\nstatic const int k_extra = 1;\n"
+    assert bench.fused_source_hash(edited.__getitem__) != base
