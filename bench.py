@@ -101,37 +101,70 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 25 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 25 ms during the timed region, and
+    in a second nvidia-smi process (so that a field the driver lacks cannot cost the SM record)
+    the HBM clock and temperature."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    MEM_FIELDS = "clocks.mem,clocks.max.mem,temperature.memory"
 
     def __init__(self, index):
         self.index = index
-        self.proc = None
-        self.path = None
+        self.proc = self.mem_proc = None
+        self.path = self.mem_path = None
+
+    def _start(self, fields):
+        fd, path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        out = open(path, "w")
+        proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={fields}",
+                                 "--format=csv,noheader,nounits", "-lms", "25"],
+                                stdout=out, stderr=subprocess.DEVNULL)
+        return proc, path, out
 
     def __enter__(self):
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.out = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "25"],
-                                         stdout=self.out, stderr=subprocess.DEVNULL)
+            self.proc, self.path, self.out = self._start(self.FIELDS)
         except Exception:
             self.proc = None
+        try:
+            self.mem_proc, self.mem_path, self.mem_out = self._start(self.MEM_FIELDS)
+        except Exception:
+            self.mem_proc = None
         return self
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            self.out.close()
+        for proc, out in ((self.proc, getattr(self, "out", None)), (self.mem_proc, getattr(self, "mem_out", None))):
+            if proc:
+                proc.terminate()
+                try:
+                    proc.wait(timeout=5)
+                except Exception:
+                    proc.kill()
+                out.close()
+
+    def mem_summary(self):
+        """Median HBM clock, its maximum and the hottest HBM reading (None where unavailable)."""
+        mem, mmax, temp = [], None, []
+        if self.mem_proc and self.mem_path and os.path.exists(self.mem_path):
+            for line in open(self.mem_path):
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 3:
+                    continue
+                try:
+                    mem.append(float(parts[0]))
+                    mmax = float(parts[1])
+                except ValueError:
+                    continue
+                try:
+                    temp.append(float(parts[2]))
+                except ValueError:
+                    pass
+            os.unlink(self.mem_path)
+        return {"mem_mhz": statistics.median(mem) if mem else None, "mem_max_mhz": mmax,
+                "mem_temp_c_max": max(temp) if temp else None}
 
     def summary(self):
         if not self.proc or not self.path:
@@ -152,7 +185,7 @@ class ClockSampler:
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "reasons": sorted(reasons), **self.mem_summary()}
 
 
 def max_over_ranks(value, ws, device):

@@ -32,6 +32,22 @@ def test_clock_summary_reports_thermal_and_hw_slowdown(tmp_path):
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
 
 
+def test_clock_summary_reads_the_hbm_clock_and_temperature(tmp_path):
+    ok = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    mem = tmp_path / "mem.csv"
+    mem.write_text("3996, 3996, 51\n3200, 3996, 58\n3996, 3996, N/A\nbad line\n")
+    path = tmp_path / "clocks.csv"
+    path.write_text(ok + "\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = object(), str(path)
+    s.mem_proc, s.mem_path = object(), str(mem)
+    r = s.summary()
+    assert r["sm_mhz"] == 2070 and r["mem_mhz"] == 3996 and r["mem_max_mhz"] == 3996
+    assert r["mem_temp_c_max"] == 58
+    # no memory record: the SM record stands alone
+    assert _summary_of(tmp_path, [ok])["mem_mhz"] is None
+
+
 def test_clock_summary_without_nvidia_smi():
     s = bench.ClockSampler(0).summary()
     assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
