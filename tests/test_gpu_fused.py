@@ -1,9 +1,9 @@
 """GPU parity of the time-blocked FP32 path (2D acoustics): against the FP64 oracle
 (relative L2 <= 1e-5) and against the point-parallel path on the same inputs.
 
-Grids span several strips and row segments with ragged edges, every pass length
-T in {2, 4, 6, 8} occurs (GBS_{8,6} has N = 2..22, GBS_{8,8} N = 2..30), and a
-batch mixes problem sizes and schemes.
+Grids span several strips and row segments with ragged edges, both pass lengths of the
+default build occur (T = 4, and T = 2 for the first pass of every N = 2 mod 4: GBS_{8,6} has
+N = 2..22, GBS_{8,8} N = 2..30), and a batch mixes problem sizes and schemes.
 """
 import numpy as np
 import pytest
