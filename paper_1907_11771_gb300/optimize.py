@@ -210,6 +210,27 @@ def _excess(d):
     return (2.0 * d.real + np.abs(d) ** 2) / (np.abs(1.0 + d) + 1.0)
 
 
+def _max_excess(h, rows_model, x, grid, zooms=2, pts=201):
+    """Largest |R(i h y)| - 1 over y in (0, 1] for the weights x: on the grid, then around every
+    local maximum within 1e-6 of the unit circle on windows of pts samples spanning two grid
+    steps, zooming twice (|R| oscillates in y, and a peak between grid samples can exceed the
+    circle while every sample stays inside)."""
+    e = _excess(rows_model.at(h, grid, x)[0])
+    best = float(e.max())
+    inner = np.arange(1, e.size - 1)
+    peaks = inner[(e[inner] >= e[inner - 1]) & (e[inner] >= e[inner + 1]) & (e[inner] > -1e-6)]
+    if peaks.size == 0:
+        return best
+    ys, width = grid[peaks], float(grid[1] - grid[0])
+    for _ in range(zooms):
+        win = np.clip(ys[:, None] + np.linspace(-width, width, pts)[None, :], grid[0], grid[-1])
+        ee = _excess(rows_model.at(h, win.ravel(), x)[0]).reshape(win.shape)
+        best = max(best, float(ee.max()))
+        ys = win[np.arange(win.shape[0]), ee.argmax(axis=1)]
+        width *= 2.0 / (pts - 1)
+    return best
+
+
 def _lp_feasible(h, rows_model, lead, order, ys, margin, x0, tol=1e-10, angles=8, rounds=60, slack=0.0):
     """Free weights with |1 + delta_j| <= 1 - mu_j on the samples and the lead term negative, by
     cutting planes around x0: the half-planes Re(e^(-i psi) delta_j) <= 1 - cos psi - mu_j, cut
@@ -281,14 +302,19 @@ def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, round
 
 
 def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9, rel_tol=1e-7, h_hi=None,
-             slack=0.0, origin=True):
+             slack=0.0, origin=True, continuation=False):
     """Maximise the imaginary stability boundary over the free weights (App. B): bisection over
     h in (0, N_max + 1] with the LP feasibility test above.  The dependent/free split only fixes
     the parametrisation (every split spans the same weights); small dependent counts keep it
     well conditioned.  slack > 0 accepts |R| up to 1 + slack on the contour, and origin=False
     drops the constraint at the origin: the looser criterion under which a sampled FP64
     solver at its tolerance counts a polynomial as stable (strictly stable optima need the
-    defaults)."""
+    defaults).  continuation: after the bisection, raise h in small steps from the weights found,
+    each feasibility test started from the last feasible weights and kept only if |R| - 1 stays
+    within slack + 1e-12 on the fine grid and around its local maxima (_max_excess; halving the
+    step on a failure down to rel_tol): at
+    orders 12 and 16 the LP is so badly conditioned that a test started far from a solution can
+    miss one, and from nearby it succeeds."""
     steps_dep, steps_free = tuple(steps_dep), tuple(steps_free)
     steps = steps_dep + steps_free
     c0x, Gx = affine_weights_exact(order, steps_dep, steps_free)
@@ -311,6 +337,16 @@ def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9
             hi = mid
     if not found:
         raise ValueError("no stable free weights found")
+    if continuation:
+        step = 2e-3 * lo
+        while step > rel_tol * lo:
+            x = _feasible(lo + step, rows_model, lead, order, ys, fine, margin, best, slack=slack)
+            # the LP's tolerance is relative to each sample's sensitivity, which is large far out
+            # on the contour: a step is kept only if |R| - 1 <= slack + 1e-12 on the fine grid
+            if x is not None and _max_excess(lo + step, rows_model, x, fine) <= slack + 1e-12:
+                lo, best = lo + step, x
+            else:
+                step *= 0.5
     return OptResult(steps_dep, steps_free, best, lo, lo / (nmax + 1))
 
 

@@ -113,3 +113,27 @@ def test_order16_reaches_table2_when_rounding_level_excess_is_accepted():
     P = np.stack([O.gbs_poly_values(n, ys) for n in dep + free], axis=1)
     c0, G = O.affine_weights(16, dep, free)
     assert np.abs(P @ (c0 + G @ r.c_free)).max() - 1.0 <= 2e-12
+
+
+def test_order12_continuation_narrows_the_gap_to_table2():
+    # Table 2 prints ISB_n 0.7504 for order 12 on all even counts up to 36.  There the LP is so
+    # badly conditioned that the bisection's feasibility tests, started far from a solution,
+    # stop at 0.6875 (no constraint at the origin, the criterion of the order-16 case above);
+    # continuing in small steps from the weights found, each test started from the last
+    # feasible weights, reaches 0.7075, with |R| <= 1 up to rounding on the whole [0, ISB].
+    import numpy as np
+    from fractions import Fraction
+    dep, free = tuple(range(2, 13, 2)), tuple(range(14, 37, 2))
+    r0 = O.optimise(12, dep, free, margin=0.0, origin=False, rel_tol=1e-5)
+    r = O.optimise(12, dep, free, margin=0.0, origin=False, continuation=True, rel_tol=1e-5)
+    assert r0.isb_n < 0.69 and r.isb_n >= 0.7075
+    c0x, Gx = O.affine_weights_exact(12, dep, free)
+    # |R| - 1 from the exact elimination, refined around every local maximum of the grid
+    rows = O._DeltaRows(12, dep + free, c0x, Gx)
+    assert O._max_excess(r.isb, rows, r.c_free, np.arange(1, 100001) / 100000) <= 1e-12
+    # and from the weights as plain polynomial values (no delta form) on a grid of its own
+    c = np.array([float(c0x[i] + sum(Gx[i][j] * Fraction(float(r.c_free[j])) for j in range(len(free))))
+                  for i in range(len(dep) + len(free))])
+    ys = 1j * np.linspace(1e-3, r.isb, 200001)
+    P = np.stack([O.gbs_poly_values(n, ys) for n in dep + free], axis=1)
+    assert np.abs(P @ c).max() - 1.0 <= 1e-12
