@@ -44,14 +44,21 @@ programming on samples y_j of the contour:
 * Every LP is centred on the weights of the largest feasible h so far, with the
   free weights scaled column by column, which keeps its entries moderate.
 
+* Continuation (optional): after the bisection, h rises in small steps, each
+  test centred on the last feasible weights, and a step is kept only if |R| - 1
+  stays within the slack on the fine grid refined around its local maxima.
+
 This is a host-side design tool: it produces weights for gbs_set_weights and is
 checked by exact root isolation of the resulting R.  It reproduces the optimal
-ISB_n the paper prints for order 4 up to 28 and order 8 up to 22, 30 and 40
-(Sec. 3.8, Table 2; 0.8548 against 0.8551 at 40) and the optimum on the counts
-of the paper's GBS_12,8 (0.7128).  On all counts up to 36 (order 12) and 32
-(order 16) its strictly stable optima, 0.677 and 0.42, stay below the printed
-0.7504 and 0.6075; allowing |R| up to 1 + 1e-12 on the contour and dropping the
-constraint at the origin (slack=1e-12, origin=False), order 16 reaches 0.625.
+ISB_n the paper prints for order 4 up to 28 and order 8 up to 22 and 30
+(Sec. 3.8, Table 2) and the optimum on the counts of the paper's GBS_12,8
+(0.7128).  Every split of the counts into dependent and free spans the same
+weights, but the LP's conditioning depends on the split.  With the short
+sequences dependent, the bisection stops below Table 2 on all counts up to 36
+(order 12: 0.677 against 0.7504) and 32 (order 16: 0.42 against 0.6075).  With
+the longest sequence among the dependent ones and continuation, the exact ISB_n
+of the returned weights is 0.75042 at order 12, 0.63534 at order 16 and 0.85587
+at order 8 up to 40 (printed 0.8551).
 """
 from dataclasses import dataclass
 from fractions import Fraction
@@ -305,8 +312,9 @@ def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9
              slack=0.0, origin=True, continuation=False):
     """Maximise the imaginary stability boundary over the free weights (App. B): bisection over
     h in (0, N_max + 1] with the LP feasibility test above.  The dependent/free split only fixes
-    the parametrisation (every split spans the same weights); small dependent counts keep it
-    well conditioned.  slack > 0 accepts |R| up to 1 + slack on the contour, and origin=False
+    the parametrisation (every split spans the same weights), but it sets the LP's conditioning:
+    at orders 8 to 16 on all even counts, the longest sequence among the dependent ones with
+    continuation reaches Table 2, the short sequences alone dependent stop short.  slack > 0 accepts |R| up to 1 + slack on the contour, and origin=False
     drops the constraint at the origin: the looser criterion under which a sampled FP64
     solver at its tolerance counts a polynomial as stable (strictly stable optima need the
     defaults).  continuation: after the bisection, raise h in small steps from the weights found,
