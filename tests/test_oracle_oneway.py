@@ -8,7 +8,10 @@ Pins:
   single excited mode (xi = -2 pi i dt) to FP64 rounding, and the error converges with order
   p (8 for GBS_8,6, 12 for GBS_12,8) until it meets the FP64 rounding floor of the whole run,
   FFTs included, about 1e-16 sum|c_k| per macro-step: 1e-13 for GBS_8,6 and 1e-12 for GBS_12,8
-  at the finest levels (the paper reports coefficient-truncation floors of 1e-14 and 1e-12).
+  at the finest levels (the paper reports coefficient-truncation floors of 1e-14 and 1e-12);
+* those coefficient-truncation floors themselves, at 60 digits with everything exact but the
+  weights: the error levels off at M |sum_k c~_k - 1| / 2, and with the weights chopped to FP64
+  it sits at the paper's 1e-14 (GBS_8,6) and 1e-12 (GBS_12,8).
 """
 from fractions import Fraction
 
@@ -85,3 +88,42 @@ def test_section4_run_matches_a_high_precision_single_mode_evaluation(scheme):
         assert abs(rate - 8) < 0.6, rate
     # the finest level sits on the rounding floor, far above its own time error
     assert rows[-1][2] < 1e-18 and rows[-1][1] < 1e-11
+
+
+@pytest.mark.parametrize("scheme,n,paper_floor", [(S.GBS_8_6, 1024, 1e-14), (S.GBS_12_8, 2048, 1e-12)])
+def test_section4_coefficient_truncation_floors(scheme, n, paper_floor):
+    """Sec. 4: with the weights truncated to FP64 the error stops converging, at 1e-14 (order 8)
+    and 1e-12 (order 12); twenty significant digits of the weights reach 1e-16.  On the single
+    excited mode of Sec. 4's run the error after one trip is |R(xi)^M - e^(-2 pi i)| / 2,
+    evaluated here at 60 digits with everything exact but the weights.  With exact weights it
+    keeps converging.  With FP64 weights it levels off at M |sum_k c~_k - 1| / 2, which grows
+    with M: the weights' sum misses 1 by their rounding, and P_k(0) = 1.  Chopped toward zero,
+    as "truncation" says, the weights put it at the paper's levels at these resolutions (within
+    a factor of 3); rounded to nearest, as this library does, it is lower for GBS_12,8."""
+    import math
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    steps, c = _weights(scheme)
+    chop = []
+    for v in c:
+        f = float(v)
+        if abs(Fraction(f)) > abs(v):
+            f = math.nextafter(f, 0.0)
+        chop.append(Fraction(f))
+    near = [Fraction(float(v)) for v in c]
+    lam = 0.99 * ISB[scheme.name] / math.pi
+    M = math.ceil(n / lam)
+    xi = mpmath.mpc(0, -2) * mpmath.pi / M
+    target = mpmath.exp(mpmath.mpc(0, -2) * mpmath.pi)
+
+    def err(cw):
+        acc = mpmath.mpc(0)
+        for a in reversed(OW.stability_poly(steps, cw)):
+            acc = acc * xi + mpmath.mpf(a.numerator) / a.denominator
+        return float(abs(acc ** M - target) / 2)
+
+    assert err(c) <= 1e-4 * paper_floor                     # exact weights: still converging
+    for cw in (chop, near):
+        drift = M * abs(float(sum(cw) - 1)) / 2
+        assert abs(err(cw) - drift) <= 0.05 * drift         # the floor is the weights' sum
+    assert paper_floor / 3 <= err(chop) <= 3 * paper_floor
