@@ -119,9 +119,14 @@ class ClockSampler:
         fd, path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         out = open(path, "w")
-        proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={fields}",
-                                 "--format=csv,noheader,nounits", "-lms", "25"],
-                                stdout=out, stderr=subprocess.DEVNULL)
+        try:
+            proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={fields}",
+                                     "--format=csv,noheader,nounits", "-lms", "25"],
+                                    stdout=out, stderr=subprocess.DEVNULL)
+        except Exception:
+            out.close()
+            os.unlink(path)
+            raise
         return proc, path, out
 
     def __enter__(self):

@@ -48,9 +48,21 @@ def test_clock_summary_reads_the_hbm_clock_and_temperature(tmp_path):
     assert _summary_of(tmp_path, [ok])["mem_mhz"] is None
 
 
-def test_clock_summary_without_nvidia_smi():
+def test_clock_summary_without_nvidia_smi(monkeypatch, tmp_path):
     s = bench.ClockSampler(0).summary()
     assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
+    # a sampler whose nvidia-smi cannot start leaves no record file behind
+    import subprocess
+    import tempfile
+
+    def no_smi(*a, **k):
+        raise FileNotFoundError("nvidia-smi")
+    monkeypatch.setattr(subprocess, "Popen", no_smi)
+    monkeypatch.setattr(tempfile, "tempdir", str(tmp_path))
+    with bench.ClockSampler(0) as cs:
+        pass
+    assert cs.summary()["reasons"] == ["nvidia-smi unavailable"]
+    assert list(tmp_path.iterdir()) == []
 
 
 def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(monkeypatch, tmp_path):
