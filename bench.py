@@ -701,8 +701,9 @@ def run_oneway(args):
     """Sec. 4's test problem on the GPU: the one-way wave u_t + u_x = 0 with spectral derivatives.
     Throughput: a batch of 256 problems of n = 1024, GBS_8,6 at 0.99 x the stability limit.  The
     FFTs run in FP64, so the kernel is bound by GB300's FP64 rate: its roofline counts
-    algorithmic FP64 flops (per right-hand side two radix-2 FFTs, 10 flops per butterfly, n/2
-    log2 n butterflies each, plus 2 n for the -i k multiply) against the nominal FP64 rate
+    algorithmic FP64 flops (per right-hand side two radix-2 FFTs of length n/2, the real signal
+    packed as a half-length complex one, 10 flops per butterfly, plus the bins' pairing and the
+    scaling) against the nominal FP64 rate
     (1.25 TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz).  The config also
     carries Sec. 4's convergence study: the error after one trip around the interval at
     lambda = dt/dx = 0.99 ISB / pi for GBS_8,6 and GBS_12,8, n = 16 .. 1024."""
@@ -752,8 +753,11 @@ def run_oneway(args):
     launches = sol.kernel_launches - l0
     ms = sum(a.elapsed_time(b) for a, b in evs)
     value = upd * args.steps / (ms / 1e3) / 1e9
-    logn = int(np.log2(n))
-    rhs_flops = 2 * (n // 2) * logn * 10 + 2 * n
+    m, logm = n // 2, int(np.log2(n)) - 1
+    # per right-hand side: two FFTs of length n/2 (the real signal as a half-length complex one;
+    # 10 flops per butterfly), the pairing of bins k, m - k with the -i k multiply (46 flops per
+    # pair) and the scaling of the n samples
+    rhs_flops = 2 * (m // 2) * logm * 10 + (m // 2) * 46 + 2 * n
     evals = 1 + sum(S.GBS_8_6.steps)                     # shared f0 plus one per leap-frog step
     flops = nb * evals * rhs_flops * args.steps
     peak_tf = 152 * 2 * 2 * 2.07e9 / 1e12

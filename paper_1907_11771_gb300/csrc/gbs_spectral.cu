@@ -3,9 +3,10 @@
 // A problem has n <= 2048 points, so one block holds a whole macro-step in shared memory: the
 // state y_0, the shared first evaluation f0 = f(y_0) (Sec. 3.6), the two leap-frog levels of
 // the current sequence, the evaluation scratch and the FP64 combine accumulator.  Every right-
-// hand-side evaluation is a radix-2 FFT of the level, a multiplication of mode m by
-// -i k_m (k_m = 2 pi m / (n dx), m = -n/2+1 .. n/2-1; the Nyquist mode, whose derivative the
-// grid cannot represent, set to zero) and an inverse FFT (Sec. 4: spectral derivatives, so the
+// hand-side evaluation is a radix-2 FFT of the level (a real signal, as one complex FFT of half
+// the length), a multiplication of mode m by -i k_m (k_m = 2 pi m / (n dx),
+// m = -n/2+1 .. n/2-1; the Nyquist mode, whose derivative the grid cannot represent, set to
+// zero) and an inverse FFT (Sec. 4: spectral derivatives, so the
 // errors are the time stepper's).  Then, per sequence k with h = H / N_k (eq. "GBS"): Forward
 // Euler from f0, N_k leap-frog steps, the average (y_(N-1) + 2 y_N + y_(N+1)) / 4, and
 // y_out = sum_k c_k y*_k accumulated in FP64 (Sec. 2.1, Sec. 3.2).  One block per problem.
@@ -24,12 +25,13 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// In-place radix-2 decimation-in-time FFT of z[0..n) (n = 2^logn): bit-reversal permutation,
-// then logn butterfly stages.  tw[m] = exp(-2 pi i m / n), m < n/2; inverse = conjugate
-// twiddles, unscaled.  Ends with a barrier.
-__device__ void fft(double2* z, const double2* tw, int n, int logn, bool inverse) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int j = (int)(__brev((unsigned)i) >> (32 - logn));
+// In-place radix-2 decimation-in-time FFT of z[0..m) (m = 2^logm): bit-reversal permutation,
+// then logm butterfly stages.  tw[q] = exp(-2 pi i q / n), q < n/2, is the table of a length-n
+// transform, n = tmul m: stage s takes exp(-2 pi i pos / 2^s) = tw[pos (m >> s) tmul].  Inverse =
+// conjugate twiddles, unscaled.  Ends with a barrier.
+__device__ void fft(double2* z, const double2* tw, int m, int logm, int tmul, bool inverse) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int j = (int)(__brev((unsigned)i) >> (32 - logm));
     if (i < j) {
       const double2 t = z[i];
       z[i] = z[j];
@@ -37,10 +39,10 @@ __device__ void fft(double2* z, const double2* tw, int n, int logn, bool inverse
     }
   }
   __syncthreads();
-  for (int s = 1; s <= logn; ++s) {
+  for (int s = 1; s <= logm; ++s) {
     const int half = 1 << (s - 1);
-    const int tstride = n >> s;
-    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+    const int tstride = (m >> s) * tmul;
+    for (int b = threadIdx.x; b < m / 2; b += blockDim.x) {
       const int pos = b & (half - 1);
       const int i = ((b >> (s - 1)) << s) + pos;
       double2 w = tw[pos * tstride];
@@ -54,22 +56,50 @@ __device__ void fft(double2* z, const double2* tw, int n, int logn, bool inverse
   }
 }
 
-// f = -u_x spectrally (the header above); u and f in shared memory, z scratch.  Ends with a barrier.
+// f = -u_x spectrally (the header above), u real of length n: the transform of a real signal as
+// one complex transform of half the length (the even samples as real parts, the odd ones as
+// imaginary parts), so each derivative costs two length-n/2 FFTs.  With m = n/2, Z = FFT_m(z)
+// and W = exp(-2 pi i / n), the real signal's bins are U_k = E_k + W^k O_k and
+// U_(m-k) = conj(E_k - W^k O_k), where E_k = (Z_k + conj Z_(m-k)) / 2 and
+// O_k = (Z_k - conj Z_(m-k)) / (2i); the derivative's bins F = -i k_m U (zero at k = 0 and at the
+// Nyquist bin m) go back the same way, Z'_k = (F_k + conj F_(m-k)) / 2 +
+// i (F_k - conj F_(m-k)) conj(W^k) / 2 and Z'_(m-k) from the conjugates, and the inverse
+// FFT_m of Z' holds f's even and odd samples, times m.  One thread takes the bins k and m - k
+// together, so the update is in place.  u and f in shared memory, z scratch (n/2 entries).
+// Ends with a barrier.
 __device__ void spectral_rhs(const double* u, double* f, double2* z, const double2* tw, int n, int logn,
                              double kscale) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = make_double2(u[i], 0.0);
+  const int m = n >> 1, logm = logn - 1;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) z[j] = make_double2(u[2 * j], u[2 * j + 1]);
   __syncthreads();
-  fft(z, tw, n, logn, false);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int m = i < n / 2 ? i : (i == n / 2 ? 0 : i - n);
-    const double k = kscale * (double)m;
-    const double2 a = z[i];
-    z[i] = make_double2(k * a.y, -k * a.x);   // (a.x + i a.y) * (-i k)
+  fft(z, tw, m, logm, 2, false);
+  for (int k = threadIdx.x; k <= m / 2; k += blockDim.x) {
+    if (k == 0) {
+      z[0] = make_double2(0.0, 0.0);   // the mean and the Nyquist mode have derivative zero
+      continue;
+    }
+    const int kp = m - k;
+    const double2 a = z[k], b = z[kp], w = tw[k];
+    const double2 e = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    const double2 o = make_double2(0.5 * (a.y + b.y), -0.5 * (a.x - b.x));
+    const double2 wo = cmul(w, o);
+    const double2 uk = make_double2(e.x + wo.x, e.y + wo.y);
+    const double2 ukp = make_double2(e.x - wo.x, -(e.y - wo.y));
+    const double sk = kscale * (double)k, skp = kscale * (double)kp;
+    const double2 fk = make_double2(sk * uk.y, -sk * uk.x);        // -i k U
+    const double2 fkp = make_double2(skp * ukp.y, -skp * ukp.x);
+    const double2 ef = make_double2(0.5 * (fk.x + fkp.x), 0.5 * (fk.y - fkp.y));
+    const double2 of = cmul(make_double2(0.5 * (fk.x - fkp.x), 0.5 * (fk.y + fkp.y)), make_double2(w.x, -w.y));
+    z[k] = make_double2(ef.x - of.y, ef.y + of.x);
+    if (kp != k) z[kp] = make_double2(ef.x + of.y, -ef.y + of.x);
   }
   __syncthreads();
-  fft(z, tw, n, logn, true);
-  const double inv_n = 1.0 / (double)n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = z[i].x * inv_n;
+  fft(z, tw, m, logm, 2, true);
+  const double inv_m = 1.0 / (double)m;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    f[2 * j] = z[j].x * inv_m;
+    f[2 * j + 1] = z[j].y * inv_m;
+  }
   __syncthreads();
 }
 
