@@ -11,6 +11,8 @@ The work of sequence k is N_k leap-frog levels plus its Forward-Euler level (the
 right-hand side is evaluated once per rank).  partition() folds the pairs as Sec. 3.6 does
 and assigns the groups to ranks longest-first onto the least loaded rank, so any rank count
 and any scheme (not only the even counts up to 4 g - 2) get a balanced, disjoint cover.
+min_ranks() gives the fewest ranks that keep every rank within the longest sequence's time,
+the core counts that Tables 1 and 2 print.
 This module holds host logic only: the arithmetic runs in the CUDA library, the exchange in
 torch.distributed (NCCL between GPUs; gloo in the CPU tests).
 """
@@ -36,6 +38,41 @@ def fold_pairs(steps):
         else:
             groups.append([k])
     return groups
+
+
+def min_ranks(steps):
+    """The fewest ranks (cores, in Sec. 3.6) that run the sequences in the time of the longest
+    one: each rank evaluates the first right-hand side and then the leap-frog levels of its
+    sequences, at most N_max + 1 evaluations, so the counts N_k are packed into bins of
+    capacity N_max.  Exact (backtracking over the sequences, longest first, for the at most
+    16 sequences of a scheme).  For the even counts 2 .. 4g - 2 it is g (Sec. 3.6's folded
+    pairs)."""
+    items = sorted((int(n) for n in steps), reverse=True)
+    if not items:
+        return 0
+    cap = items[0]
+
+    def fits(k):
+        bins = [0] * k
+
+        def place(i):
+            if i == len(items):
+                return True
+            seen = set()
+            for b in range(k):
+                if bins[b] + items[i] <= cap and bins[b] not in seen:
+                    seen.add(bins[b])          # bins with equal loads are interchangeable
+                    bins[b] += items[i]
+                    if place(i + 1):
+                        return True
+                    bins[b] -= items[i]
+            return False
+        return place(0)
+
+    k = -(-sum(items) // cap)
+    while not fits(k):
+        k += 1
+    return k
 
 
 def _place(groups, steps, n_ranks):

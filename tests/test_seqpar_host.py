@@ -118,3 +118,21 @@ def test_two_gloo_ranks_complete_the_macro_step(split):
         assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 1e-14
         assert calls == ([masks[rank]] * 3 if masks[rank] else [])
     assert np.array_equal(res[0][0], res[1][0])      # every rank holds the same completed state
+
+
+def test_min_ranks_reproduces_the_papers_core_counts():
+    from paper_1907_11771_gb300.seqpar import min_ranks
+    # Table 1: the fully determined schemes on three, four and five cores
+    assert min_ranks((2, 16, 18, 20)) == 3
+    assert min_ranks((2, 8, 12, 14, 16, 20)) == 4
+    assert min_ranks((2, 8, 10, 12, 14, 16, 18, 22)) == 5
+    # Table 2: all even counts up to N_opt on 8, 11, 10 and 9 cores
+    for n_opt, cores in ((28, 8), (40, 11), (36, 10), (32, 9)):
+        assert min_ranks(range(2, n_opt + 1, 2)) == cores, n_opt
+    # Sec. 3.6: the even counts up to 4g - 2 fill g cores; Sec. 3.8's six- and eight-core schemes
+    for g in range(1, 9):
+        assert min_ranks(range(2, 4 * g - 1, 2)) == g
+    assert min_ranks(S.GBS_8_6.steps) == 6
+    assert min_ranks(S.GBS_8_8.steps) == 8
+    assert min_ranks(S.GBS_12_8.steps) == 8
+    assert min_ranks((2, 4, 6, 8)) == 3 and min_ranks(()) == 0     # 8 | 6 + 2 | 4
