@@ -142,3 +142,19 @@ def test_table2_reached_with_the_longest_sequence_dependent(order, dep, free, or
     isb_n = W.isb_exact(W.stability_poly(steps, c)) / (max(steps) + 1)
     assert isb_n >= printed, isb_n
     assert abs(isb_n - r.isb_n) <= 1e-4 * isb_n
+
+
+def test_max_excess_finds_a_peak_narrower_than_its_grid():
+    # |R| - 1 = e(y) on a grid of spacing 1e-4 with a peak of 1e-7 and width 2e-5 halfway between
+    # two samples: every grid sample lies near -1e-3, the refinement around the grid's local
+    # maxima finds it
+    import numpy as np
+
+    class Bump:
+        def at(self, h, ys, x):
+            e = -1e-3 - 1e-4 * ys + (1e-3 + 0.70005e-4 + 1e-7) * np.exp(-((ys - 0.70005) / 2e-5) ** 2)
+            return e.astype(complex), None      # |1 + e| - 1 = e for real e > -1
+
+    grid = np.arange(1, 10001) / 10000
+    assert Bump().at(1.0, grid, None)[0].real.max() < -9e-4
+    assert abs(O._max_excess(1.0, Bump(), None, grid) - 1e-7) <= 1e-9
