@@ -309,6 +309,18 @@ def _feasible(h, rows_model, lead, order, ys, fine, margin, x0, tol=1e-10, round
     return None
 
 
+def longest_dependent_split(order, steps):
+    """(steps_dep, steps_free) with the order/2 - 1 shortest counts and the longest one dependent,
+    the rest free: the parametrisation with which the LP, with continuation, reaches Table 2
+    (orders 8 to 16 on all even counts; see optimise)."""
+    s = sorted(int(n) for n in steps)
+    q = order // 2
+    if len(s) <= q or len(set(s)) != len(s):
+        raise ValueError("need more than order/2 distinct step counts")
+    dep = tuple(s[:q - 1]) + (s[-1],)
+    return dep, tuple(n for n in s if n not in dep)
+
+
 def optimise(order, steps_dep, steps_free, n_samples=600, refine=60, margin=1e-9, rel_tol=1e-7, h_hi=None,
              slack=0.0, origin=True, continuation=False):
     """Maximise the imaginary stability boundary over the free weights (App. B): bisection over

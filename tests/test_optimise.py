@@ -133,6 +133,7 @@ def test_table2_reached_with_the_longest_sequence_dependent(order, dep, free, or
     # optimiser reaches all three.  The ISB is that of the returned weights by exact root
     # isolation (the oracle): the free weights taken as their FP64 values, the dependent ones
     # solved exactly from them, |R(iy)| <= 1 on the whole [0, ISB] with no tolerance.
+    assert O.longest_dependent_split(order, range(2, max(dep) + 1, 2)) == (tuple(dep), tuple(free))
     r = O.optimise(order, dep, free, margin=0.0 if not origin else 1e-9, origin=origin, continuation=True,
                    rel_tol=1e-5)
     cf = [Fraction(float(v)) for v in r.c_free]
