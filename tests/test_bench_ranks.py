@@ -52,3 +52,22 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         assert bench.run_reference(A()) == 0
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_on_rank_zero_uses_every_core(monkeypatch):
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "pick_oracle_side", lambda budget: 128)
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.run_reference(A()) == 0
+    line = json.loads(buf.getvalue())
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["grid"] == [128, 128]
+    assert "FP64 CPU oracle" in line["config"]["workload"] and "FP32" not in line["config"]["workload"]
+    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    assert line["e2e"]["value"] == line["value"]
