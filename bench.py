@@ -266,6 +266,14 @@ def pick_oracle_side(budget_s):
     return max(128, min(N_GRID, s))
 
 
+def host_cores():
+    """CPUs this process may run on (its affinity set), else the host's count."""
+    try:
+        return len(os.sched_getaffinity(0)) or 1
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def _oracle_worker(side):
     return oracle_macro_step_timing(side)
 
@@ -278,7 +286,7 @@ def cpu_baseline(budget_s=15.0):
     side = pick_oracle_side(budget_s)
     dt, upd = oracle_macro_step_timing(side)
     single = {"value": upd / dt / 1e9, "cores": 1, "seconds": dt}
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     side_all = pick_oracle_side(budget_s / 2)     # memory bandwidth is shared by the processes
     try:
         t0 = time.perf_counter()
@@ -302,14 +310,14 @@ def cpu_baseline(budget_s=15.0):
 
 def run_reference(args):
     """The oracle on the host cores: every step runs one macro-step of the same sample in each of
-    os.cpu_count() concurrent processes (the oracle is single-threaded numpy; the processes are
+    host_cores() concurrent processes (the oracle is single-threaded numpy; the processes are
     started once, with spawn), or in this process alone where no process pool can start."""
     import multiprocessing as mp
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     budget = 100.0 / max(1, args.steps + args.warmup)
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     pool = None
     if cores > 1:
         try:

@@ -69,5 +69,5 @@ def test_reference_arm_on_rank_zero_uses_every_core(monkeypatch):
     line = json.loads(buf.getvalue())
     assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["grid"] == [128, 128]
     assert "FP64 CPU oracle" in line["config"]["workload"] and "FP32" not in line["config"]["workload"]
-    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    assert line["cpu_baseline"]["cores"] == bench.host_cores()
     assert line["e2e"]["value"] == line["value"]
